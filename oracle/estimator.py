@@ -1,0 +1,156 @@
+"""The hierarchical-probing trace estimator (oracle, test infrastructure only).
+
+Section 1 of arXiv:1302.4018 writes the estimator as (1/s) sum_k z_k^T f(A) z_k;
+Section 2.2 makes the vectors nested so that every prefix s reuses the
+quadratures of the shorter prefixes; Section 4 multiplies every vector by one
+Z_2 vector z_0 (Eq. removebias); Section 5.3 dilutes the 12 spin-colour
+components fully, so probe m of the space-time sequence stands for 12 right
+hand sides  v_{m,a} = (z_0 (.) z_m) (x) e_a,  a = 0..11, and
+    q_m = sum_a v_{m,a}^H A^-1 v_{m,a},     T_s = (1/s) sum_{m<s} q_m.
+For the (scalar) Laplacian there is one right-hand side per probe.
+
+The derivative of T_s with respect to a real per-site mass mu(x) (the
+diagonal term) follows from d(A^-1) = -A^-1 (dA) A^-1:
+    dT_s / dmu(x) = -(1/s) sum_{m,a} sum_c conj(y_{m,a}(x, c)) x_{m,a}(x, c),
+with x = A^-1 v and y = A^-H v.  This oracle solves the adjoint system
+explicitly (it does not use gamma_5-hermiticity).
+"""
+from __future__ import annotations
+
+from typing import Sequence
+
+import numpy as np
+
+from . import operators as ops
+from . import solvers
+from .probing import probe_phases, probe_values
+
+
+def probe_vectors(dims: Sequence[int], first: int, count: int, z0_seed: int,
+                  loc: Sequence[int] | None = None) -> np.ndarray:
+    """v_m = z_0 (.) z_m as complex [count, V] (correctly rounded entries)."""
+    ph, P = probe_phases(dims, first, count, z0_seed, loc=loc)
+    return probe_values(ph, P)
+
+
+# ------------------------------------------------------------------ prefix
+def trace_prefix(q: Sequence[complex]) -> np.ndarray:
+    """T_s = (1/s) sum_{m<s} q_m, s = 1..len(q), plain sequential FP64 sums."""
+    out = np.empty(len(q), dtype=complex)
+    acc = 0.0 + 0.0j
+    for s in range(1, len(q) + 1):
+        acc = acc + q[s - 1]
+        out[s - 1] = acc / s
+    return out
+
+
+def trace_prefix_kahan(q: Sequence[complex]) -> np.ndarray:
+    """The same prefix with Kahan-compensated sums (cross-check of rounding)."""
+    out = np.empty(len(q), dtype=complex)
+    sr = cr = si = ci = 0.0
+    for s in range(1, len(q) + 1):
+        for part in (0, 1):
+            v = q[s - 1].real if part == 0 else q[s - 1].imag
+            if part == 0:
+                y = v - cr
+                t = sr + y
+                cr = (t - sr) - y
+                sr = t
+            else:
+                y = v - ci
+                t = si + y
+                ci = (t - si) - y
+                si = t
+        out[s - 1] = complex(sr, si) / s
+    return out
+
+
+# ------------------------------------------------------------------ Laplacian
+def laplacian_solutions(dims, mass, W, tol=1e-13, mass_field=None, method="cg"):
+    """x_m = A^-1 v_m for the rows v_m of W."""
+    if method == "dense":
+        A = ops.laplacian_dense(dims, mass, mass_field)
+        return solvers.dense_solve(A, W.T).T
+    X = np.empty_like(W)
+    for m in range(W.shape[0]):
+        X[m], _ = solvers.cg(lambda v: ops.laplacian_apply(v, dims, mass, mass_field), W[m], tol=tol)
+    return X
+
+
+def laplacian_quadratures(dims, mass, first, count, z0_seed, tol=1e-13, mass_field=None,
+                          method="cg", loc=None):
+    """q_m = v_m^H A^-1 v_m, m = first..first+count-1."""
+    W = probe_vectors(dims, first, count, z0_seed, loc=loc)
+    if np.all(W.imag == 0):
+        W = W.real
+    X = laplacian_solutions(dims, mass, W, tol, mass_field, method)
+    return np.array([np.vdot(W[m], X[m]) for m in range(count)])
+
+
+def laplacian_grad_mass_field(dims, mass, s, z0_seed, tol=1e-13, mass_field=None, method="cg"):
+    """dT_s/dmu(x); A is real symmetric (its stencil is symmetric), so A^-H v = A^-1 v = x."""
+    W = probe_vectors(dims, 0, s, z0_seed)
+    if np.all(W.imag == 0):
+        W = W.real
+    X = laplacian_solutions(dims, mass, W, tol, mass_field, method)
+    Y = X
+    return -(np.sum(np.conj(Y) * X, axis=0)) / s
+
+
+# ------------------------------------------------------------------ Wilson
+def _dilute(w: np.ndarray, a: int) -> np.ndarray:
+    V = w.shape[0]
+    b = np.zeros((V, 12), dtype=complex)
+    b[:, a] = w
+    return b.reshape(V, 4, 3)
+
+
+def wilson_solutions(dims, U, kappa, W, tol=1e-13, mass=0.0, mass_field=None, method="bicgstab",
+                     dagger=False):
+    """x_{m,a} = D^-1 v_{m,a} (or D^-H v_{m,a}); returns complex [count, 12, V, 4, 3]."""
+    count, V = W.shape
+    X = np.empty((count, 12, V, 4, 3), dtype=complex)
+    if method == "dense":
+        D = ops.wilson_dense(U, dims, kappa, mass, mass_field)
+        if dagger:
+            D = np.conj(D).T
+        B = np.zeros((12 * V, 12 * count), dtype=complex)
+        for m in range(count):
+            for a in range(12):
+                B[:, 12 * m + a] = _dilute(W[m], a).reshape(-1)
+        Xs = solvers.dense_solve(D, B)
+        for m in range(count):
+            for a in range(12):
+                X[m, a] = Xs[:, 12 * m + a].reshape(V, 4, 3)
+        return X
+
+    def apply(v):
+        return ops.wilson_apply(v, U, dims, kappa, mass, mass_field, dagger=dagger)
+
+    for m in range(count):
+        for a in range(12):
+            X[m, a], _ = solvers.bicgstab(apply, _dilute(W[m], a), tol=tol)
+    return X
+
+
+def wilson_quadratures(dims, U, kappa, first, count, z0_seed, tol=1e-13, mass=0.0,
+                       mass_field=None, method="bicgstab", loc=None):
+    """q_m = sum_a v_{m,a}^H D^-1 v_{m,a} with full spin-colour dilution."""
+    W = probe_vectors(dims, first, count, z0_seed, loc=loc)
+    X = wilson_solutions(dims, U, kappa, W, tol, mass, mass_field, method)
+    V = W.shape[1]
+    q = np.zeros(count, dtype=complex)
+    for m in range(count):
+        for a in range(12):
+            q[m] += np.vdot(_dilute(W[m], a), X[m, a])
+    return q
+
+
+def wilson_grad_mass_field(dims, U, kappa, s, z0_seed, tol=1e-13, mass=0.0, mass_field=None,
+                           method="bicgstab"):
+    """dT_s/dmu(x) = -(1/s) sum_{m<s,a} sum_c conj(y(x,c)) x(x,c), y = D^-H v solved explicitly."""
+    W = probe_vectors(dims, 0, s, z0_seed)
+    X = wilson_solutions(dims, U, kappa, W, tol, mass, mass_field, method)
+    Y = wilson_solutions(dims, U, kappa, W, tol, mass, mass_field, method, dagger=True)
+    g = np.sum(np.conj(Y) * X, axis=(0, 1, 3, 4))
+    return -g / s

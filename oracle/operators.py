@@ -1,0 +1,150 @@
+"""Lattice operators of arXiv:1302.4018, written out plainly in FP64.
+
+Oracle (test infrastructure only).
+
+* Shifted periodic Laplacian (Section 5 control problem; BASELINE form for
+  d = 4):  A = (2d + m) I - sum_mu (S_mu + S_mu^T), plus an optional
+  per-site mass field mu(x) on the diagonal.
+* Wilson-Dirac matrix (Section 1.1.1: a sparse matrix on a periodic 4-D
+  lattice with 12 = 4 spin x 3 colour unknowns per site; Section 5.3 uses its
+  clover variant).  Plain Wilson form in kappa normalisation:
+      (D psi)(x) = (1 + m + mu(x)) psi(x)
+                   - kappa sum_mu [ (1 - g_mu) U_mu(x)        psi(x + mu)
+                                  + (1 + g_mu) U_mu(x - mu)^H psi(x - mu) ]
+  with explicit 4x4 gamma matrices (chiral basis, gamma_5 diagonal) and full
+  3x3 link products: no spin projection, no link reconstruction.
+
+Field layout: arrays indexed by the lexicographic site (x_1 fastest); a spinor
+is complex128 [V, 4, 3] (spin, colour); a gauge field is complex128
+[V, 4, 3, 3] (site, direction mu = 1..4 along x_1..x_4, row, column).
+Unknown number (spin s, colour c) of site x is 12 x + 3 s + c.
+"""
+from __future__ import annotations
+
+from typing import Sequence
+
+import numpy as np
+
+
+def _shape(dims: Sequence[int]) -> tuple:
+    return tuple(reversed([int(v) for v in dims]))
+
+
+def _axis(dims: Sequence[int], mu: int) -> int:
+    """numpy axis of lattice direction mu (0-based) in the reversed-dims shape."""
+    return len(dims) - 1 - mu
+
+
+def shift_field(f: np.ndarray, dims: Sequence[int], mu: int, sign: int) -> np.ndarray:
+    """g(x) = f(x + sign * mu_hat) on the torus (f indexed by site first)."""
+    V = f.shape[0]
+    g = f.reshape(_shape(dims) + f.shape[1:])
+    g = np.roll(g, -sign, axis=_axis(dims, mu))
+    return g.reshape((V,) + f.shape[1:])
+
+
+# ------------------------------------------------------------------ Laplacian
+def laplacian_apply(x: np.ndarray, dims: Sequence[int], mass: float,
+                    mass_field: np.ndarray | None = None) -> np.ndarray:
+    """A x for x of shape [V] or [V, n] (real or complex)."""
+    d = len(dims)
+    diag = 2 * d + mass
+    y = diag * x
+    if mass_field is not None:
+        y = y + (mass_field.reshape((-1,) + (1,) * (x.ndim - 1))) * x
+    for mu in range(d):
+        y = y - shift_field(x, dims, mu, +1) - shift_field(x, dims, mu, -1)
+    return y
+
+
+def laplacian_dense(dims: Sequence[int], mass: float, mass_field: np.ndarray | None = None) -> np.ndarray:
+    """The Laplacian as a dense matrix, row by row from the stencil definition."""
+    d = len(dims)
+    V = int(np.prod(dims))
+    A = np.zeros((V, V))
+    strides = [int(np.prod(dims[:j])) for j in range(d)]
+    for i in range(V):
+        A[i, i] += 2 * d + mass + (0.0 if mass_field is None else mass_field[i])
+        x = [(i // strides[j]) % dims[j] for j in range(d)]
+        for mu in range(d):
+            for sgn in (+1, -1):
+                y = list(x)
+                y[mu] = (y[mu] + sgn) % dims[mu]
+                A[i, sum(y[j] * strides[j] for j in range(d))] -= 1.0
+    return A
+
+
+# ------------------------------------------------------------------ gammas
+def pauli() -> list:
+    return [np.array([[0, 1], [1, 0]], dtype=complex),
+            np.array([[0, -1j], [1j, 0]], dtype=complex),
+            np.array([[1, 0], [0, -1]], dtype=complex)]
+
+
+def gamma_matrices() -> list:
+    """Euclidean chiral basis: g_k = [[0, -i s_k], [i s_k, 0]] (k = 1..3), g_4 = [[0, 1], [1, 0]],
+    g_5 = g_1 g_2 g_3 g_4 = diag(1, 1, -1, -1).  Returns [g_1, g_2, g_3, g_4, g_5]."""
+    Z = np.zeros((2, 2), dtype=complex)
+    I2 = np.eye(2, dtype=complex)
+    g = []
+    for s in pauli():
+        g.append(np.block([[Z, -1j * s], [1j * s, Z]]))
+    g.append(np.block([[Z, I2], [I2, Z]]))
+    g.append(g[0] @ g[1] @ g[2] @ g[3])
+    return g
+
+
+# ------------------------------------------------------------------ Wilson
+def wilson_apply(psi: np.ndarray, U: np.ndarray, dims: Sequence[int], kappa: float,
+                 mass: float = 0.0, mass_field: np.ndarray | None = None,
+                 dagger: bool = False) -> np.ndarray:
+    """D psi (or D^H psi when ``dagger``) for psi [V, 4, 3] complex.
+
+    D^H follows from transposing the blocks of D: the hopping term to x + mu
+    becomes (1 + g_mu) U_mu(x) and the one to x - mu becomes
+    (1 - g_mu) U_mu(x - mu)^H (the projectors are Hermitian).
+    """
+    g = gamma_matrices()
+    I4 = np.eye(4, dtype=complex)
+    diag = 1.0 + mass
+    out = diag * psi
+    if mass_field is not None:
+        out = out + mass_field[:, None, None] * psi
+    hop = np.zeros_like(psi)
+    for mu in range(4):
+        P_fwd = I4 - g[mu] if not dagger else I4 + g[mu]
+        P_bwd = I4 + g[mu] if not dagger else I4 - g[mu]
+        U_mu = U[:, mu]
+        psi_f = shift_field(psi, dims, mu, +1)
+        col = np.einsum("xab,xsb->xsa", U_mu, psi_f)
+        hop = hop + np.einsum("st,xta->xsa", P_fwd, col)
+        psi_b = shift_field(psi, dims, mu, -1)
+        U_b = shift_field(U_mu, dims, mu, -1)
+        col = np.einsum("xba,xsb->xsa", np.conj(U_b), psi_b)
+        hop = hop + np.einsum("st,xta->xsa", P_bwd, col)
+    return out - kappa * hop
+
+
+def wilson_dense(U: np.ndarray, dims: Sequence[int], kappa: float, mass: float = 0.0,
+                 mass_field: np.ndarray | None = None) -> np.ndarray:
+    """D as a dense 12V x 12V matrix, block by block from its definition."""
+    g = gamma_matrices()
+    I4 = np.eye(4, dtype=complex)
+    d = 4
+    V = int(np.prod(dims))
+    D = np.zeros((12 * V, 12 * V), dtype=complex)
+    strides = [int(np.prod(dims[:j])) for j in range(d)]
+    for i in range(V):
+        m_i = mass + (0.0 if mass_field is None else mass_field[i])
+        D[12 * i:12 * i + 12, 12 * i:12 * i + 12] += (1.0 + m_i) * np.eye(12)
+        x = [(i // strides[j]) % dims[j] for j in range(d)]
+        for mu in range(d):
+            y = list(x)
+            y[mu] = (y[mu] + 1) % dims[mu]
+            jf = sum(y[k] * strides[k] for k in range(d))
+            D[12 * i:12 * i + 12, 12 * jf:12 * jf + 12] += -kappa * np.kron(I4 - g[mu], U[i, mu])
+            y = list(x)
+            y[mu] = (y[mu] - 1) % dims[mu]
+            jb = sum(y[k] * strides[k] for k in range(d))
+            D[12 * i:12 * i + 12, 12 * jb:12 * jb + 12] += -kappa * np.kron(I4 + g[mu], np.conj(U[jb, mu]).T)
+    return D

@@ -1,0 +1,119 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+This module holds no arithmetic of the probing method: it only draws the
+inputs the method is applied to (gauge links, mass fields, random spinors,
+the uneven batch of lattices).  It imports nothing else from this package,
+so the oracle can use it without touching the CUDA library.
+
+Gauge links (stand-in for the missing 32^3x64 ensemble of Section 5.3):
+  U_mu(x) = exp(i eps H),  H = (G + G^H)/2 - tr(...)/3 I,
+  G_ij = (a + i b)/sqrt(2),  a, b ~ N(0, 1) from numpy PCG64(seed), drawn in
+  the order (site, mu, i, j, re/im).  The exponential is a degree-24 Taylor
+  series (||eps H|| < 3 for every config used, so the series is converged
+  far below FP64 rounding), followed by re-unitarisation: Gram-Schmidt on
+  rows 1-2 and row 3 = conj(row1 x row2), which makes every link exactly
+  special-unitary up to rounding.  Layout complex128 [V, 4, 3, 3].
+"""
+from __future__ import annotations
+
+import math
+from typing import Sequence
+
+import numpy as np
+
+
+def volume(dims: Sequence[int]) -> int:
+    v = 1
+    for L in dims:
+        v *= int(L)
+    return v
+
+
+def _taylor_expm_i(H: np.ndarray, eps: float, degree: int = 24) -> np.ndarray:
+    n = H.shape[-1]
+    X = (1j * eps) * H
+    out = np.broadcast_to(np.eye(n, dtype=complex), H.shape).copy()
+    term = out.copy()
+    for k in range(1, degree + 1):
+        term = np.matmul(term, X) / k
+        out += term
+    return out
+
+
+def reunitarize(U: np.ndarray) -> np.ndarray:
+    r1 = U[..., 0, :]
+    r1 = r1 / np.sqrt(np.sum(np.abs(r1) ** 2, axis=-1, keepdims=True))
+    r2 = U[..., 1, :]
+    r2 = r2 - np.sum(np.conj(r1) * r2, axis=-1, keepdims=True) * r1
+    r2 = r2 / np.sqrt(np.sum(np.abs(r2) ** 2, axis=-1, keepdims=True))
+    r3 = np.conj(np.cross(r1, r2))
+    return np.stack([r1, r2, r3], axis=-2)
+
+
+def gauge_links(dims: Sequence[int], eps: float, seed: int, chunk_sites: int = 1 << 18) -> np.ndarray:
+    """SU(3) links U = exp(i eps H) on every site and direction; complex128 [V, 4, 3, 3]."""
+    V = volume(dims)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = np.empty((V, 4, 3, 3), dtype=complex)
+    for s0 in range(0, V, chunk_sites):
+        n = min(chunk_sites, V - s0)
+        ab = rng.standard_normal((n, 4, 3, 3, 2))
+        G = (ab[..., 0] + 1j * ab[..., 1]) / math.sqrt(2.0)
+        H = 0.5 * (G + np.conj(np.swapaxes(G, -1, -2)))
+        tr = np.trace(H, axis1=-2, axis2=-1).real
+        H = H - (tr / 3.0)[..., None, None] * np.eye(3)
+        if eps == 0.0:
+            U = np.broadcast_to(np.eye(3, dtype=complex), (n, 4, 3, 3)).copy()
+        else:
+            U = reunitarize(_taylor_expm_i(H, eps))
+        out[s0:s0 + n] = U
+    return out
+
+
+def gauge_transform(U: np.ndarray, dims: Sequence[int], seed: int) -> tuple[np.ndarray, np.ndarray]:
+    """Random SU(3) gauge transformation g(x); returns (U', g) with
+    U'_mu(x) = g(x) U_mu(x) g(x + mu)^H."""
+    V = volume(dims)
+    g = gauge_links([V], 1.0, seed)[:, 0]
+    shape = tuple(reversed([int(v) for v in dims]))
+    Up = np.empty_like(U)
+    for mu in range(4):
+        axis = len(dims) - 1 - mu
+        gf = np.roll(g.reshape(shape + (3, 3)), -1, axis=axis).reshape(V, 3, 3)
+        Up[:, mu] = g @ U[:, mu] @ np.conj(np.swapaxes(gf, -1, -2))
+    return Up, g
+
+
+def mass_field(dims: Sequence[int], sigma: float, seed: int) -> np.ndarray:
+    """Per-site additive mass mu(x) ~ N(0, sigma^2) (sigma is the standard deviation)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return sigma * rng.standard_normal(volume(dims))
+
+
+def random_spinors(dims: Sequence[int], nrhs: int, seed: int) -> np.ndarray:
+    """Gaussian complex spinor fields, complex128 [nrhs, V, 4, 3]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    V = volume(dims)
+    a = rng.standard_normal((nrhs, V, 4, 3, 2))
+    return a[..., 0] + 1j * a[..., 1]
+
+
+def random_real_fields(dims: Sequence[int], nrhs: int, seed: int) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.standard_normal((nrhs, volume(dims)))
+
+
+BATCH_LATTICES = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32), (24, 24, 24, 48)]
+
+
+def batch_config(seed: int = 3000, lattices=BATCH_LATTICES) -> list[dict]:
+    """The uneven batch: per lattice kappa ~ U[0.10, 0.12], eps ~ U[0.2, 0.4],
+    s uniform in {64, 128, 256, 512}, link seed 1100 + i, all from PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i, dims in enumerate(lattices):
+        kappa = float(rng.uniform(0.10, 0.12))
+        eps = float(rng.uniform(0.2, 0.4))
+        s = int(rng.choice([64, 128, 256, 512]))
+        out.append({"dims": tuple(dims), "kappa": kappa, "eps": eps, "s": s, "link_seed": 1100 + i})
+    return out

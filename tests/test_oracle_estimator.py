@@ -1,0 +1,140 @@
+"""Pins of the oracle's estimator: exactness, closed forms, unbiasedness, gradients."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import estimator as E
+from oracle import operators as O
+from oracle import permutation as P
+from oracle import probing as Pr
+from paper_1302_4018_gb300 import synth
+from pins import free_wilson_trace_inverse, laplacian_eigenvalues, laplacian_trace_inverse
+
+
+def test_prefix_sequential_vs_kahan():
+    rng = np.random.default_rng(0)
+    q = rng.standard_normal(1000) * 1e3 + 1j * rng.standard_normal(1000)
+    a = E.trace_prefix(q)
+    b = E.trace_prefix_kahan(q)
+    assert np.allclose(a, b, rtol=1e-13)
+    assert np.isclose(a[-1], np.mean(q))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_laplacian_full_sequence_is_exact_4x4x4x4(seed):
+    dims = (4, 4, 4, 4)
+    q = E.laplacian_quadratures(dims, 0.05, 0, 256, seed, tol=1e-13)
+    T = E.trace_prefix(q)
+    assert np.isclose(T[-1].real, laplacian_trace_inverse(dims, 0.05), rtol=1e-11)
+
+
+def test_laplacian_8x8x8x8_dense_full_sequence():
+    # the 8^4, m = 0.05 control problem: T_N = Tr(A^-1) = closed form = dense LU
+    dims = (8, 8, 8, 8)
+    q = E.laplacian_quadratures(dims, 0.05, 0, 4096, 1, method="dense")
+    T = E.trace_prefix(q)
+    assert np.isclose(T[-1].real, laplacian_trace_inverse(dims, 0.05), rtol=1e-11)
+    # first vector without bias removal: h_0 = 1 is the lowest eigenvector: T_1 = V / m
+    q0 = E.laplacian_quadratures(dims, 0.05, 0, 2, 0, tol=1e-13)
+    assert np.isclose(q0[0].real, 4096 / 0.05, rtol=1e-12)
+
+
+@pytest.mark.parametrize("dims,seed", [((8, 8, 8, 8), 0), ((4, 8, 4, 8), 3)])
+def test_powers_exact_at_completion(dims, seed):
+    """Tr(A^k), k <= 2^{m+1} - 1, is exact at the completion point s = 2^{dm+1}
+    (same-colour sites are >= 2^{m+1} apart, Section 3.3), matvec only."""
+    d = 4
+    lam = laplacian_eigenvalues(dims, 0.05)
+    for m in (0, 1):
+        s = 2 ** (d * m + 1)
+        W = E.probe_vectors(dims, 0, s, seed).real
+        for k in range(1, 2 ** (m + 1)):
+            X = W.T.copy()
+            for _ in range(k):
+                X = O.laplacian_apply(X, dims, 0.05)
+            est = np.sum(W.T * X) / s
+            assert np.isclose(est, np.sum(lam ** k), rtol=1e-12)
+
+
+def test_unbiased_over_all_z0_2x2x2x2():
+    """Section 4: with v = z0 (.) z, E_{z0}[T_s] = Tr(A^-1) for every s (all 2^16 z0 on 2^4)."""
+    dims = (2, 2, 2, 2)
+    V = 16
+    Ainv = np.linalg.inv(O.laplacian_dense(dims, 0.05))
+    Z = np.where(Pr.LatticeBasis(dims).matrix()[np.array(P.hierarchical_loc(dims))] == 0, 1.0, -1.0)
+    signs = np.array(list(itertools.product([1.0, -1.0], repeat=V)))      # all z0
+    exact = np.trace(Ainv)
+    for s in (1, 2, 3, 5, 16):
+        Ts = np.zeros(len(signs))
+        for m in range(s):
+            Vm = signs * Z[:, m][None, :]
+            Ts += np.einsum("ni,ij,nj->n", Vm, Ainv, Vm)
+        assert np.isclose(Ts.mean() / s, exact, rtol=1e-12)
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 4), (3, 2, 2, 2)])
+def test_wilson_full_sequence_equals_dense_trace(dims):
+    U = synth.gauge_links(dims, 0.3, 11)
+    V = int(np.prod(dims))
+    q = E.wilson_quadratures(dims, U, 0.12, 0, V, 5, method="dense")
+    T = E.trace_prefix(q)
+    D = O.wilson_dense(U, dims, 0.12)
+    assert np.isclose(T[-1], np.trace(np.linalg.inv(D)), rtol=1e-11)
+    # gamma_5-hermiticity: every q_m (hence every T_s) is real
+    assert np.max(np.abs(T.imag)) <= 1e-11 * np.max(np.abs(T.real))
+    # BiCGStab oracle agrees with dense on a prefix
+    qb = E.wilson_quadratures(dims, U, 0.12, 0, 3, 5, tol=1e-13)
+    assert np.allclose(qb, q[:3], rtol=1e-11)
+
+
+def test_wilson_free_field_full_sequence_4x4x4x4():
+    dims = (4, 4, 4, 4)
+    V = 256
+    U = np.broadcast_to(np.eye(3, dtype=complex), (V, 4, 3, 3)).copy()
+    Ug, _ = synth.gauge_transform(U, dims, 5)
+    q = E.wilson_quadratures(dims, Ug, 0.115, 0, V, 9, method="dense")
+    T = E.trace_prefix(q)
+    assert np.isclose(T[-1].real, free_wilson_trace_inverse(dims, 0.115), rtol=1e-10)
+
+
+def test_laplacian_gradient_closed_form_and_fd():
+    dims = (4, 4, 2, 2)
+    V = 64
+    m = 0.3
+    # at s = N: dT/dm = sum_x dT/dmu(x) = -sum_k 1/lambda_k^2
+    g = E.laplacian_grad_mass_field(dims, m, V, 2, tol=1e-14)
+    lam = laplacian_eigenvalues(dims, m)
+    assert np.isclose(np.sum(g).real, -np.sum(1.0 / lam ** 2), rtol=1e-10)
+    # central differences of the estimate at s = 5 in a few site directions
+    s = 5
+    g5 = E.laplacian_grad_mass_field(dims, m, s, 2, method="dense").real
+    h = 1e-5
+    for site in (0, 7, 33):
+        e = np.zeros(V)
+        e[site] = h
+        tp = E.trace_prefix(E.laplacian_quadratures(dims, m, 0, s, 2, mass_field=e, method="dense"))[-1]
+        tm = E.trace_prefix(E.laplacian_quadratures(dims, m, 0, s, 2, mass_field=-e, method="dense"))[-1]
+        assert np.isclose((tp - tm).real / (2 * h), g5[site], rtol=1e-6, atol=1e-9)
+
+
+def test_wilson_gradient_fd():
+    dims = (2, 2, 2, 4)
+    V = 32
+    U = synth.gauge_links(dims, 0.3, 21)
+    mf = synth.mass_field(dims, 0.01, 5000)
+    s = 3
+    g = E.wilson_grad_mass_field(dims, U, 0.12, s, 7, mass_field=mf, method="dense")
+    assert np.max(np.abs(g.imag)) < 1e-10 * np.max(np.abs(g.real))
+    h = 1e-5
+    for site in (0, 13, 31):
+        e = mf.copy()
+        e[site] += h
+        tp = E.trace_prefix(E.wilson_quadratures(dims, U, 0.12, 0, s, 7, mass_field=e, method="dense"))[-1]
+        e[site] -= 2 * h
+        tm = E.trace_prefix(E.wilson_quadratures(dims, U, 0.12, 0, s, 7, mass_field=e, method="dense"))[-1]
+        assert np.isclose(((tp - tm) / (2 * h)).real, g[site].real, rtol=1e-6, atol=1e-9)
+    # uniform direction d/dm = sum_x dT/dmu(x)
+    tp = E.trace_prefix(E.wilson_quadratures(dims, U, 0.12, 0, s, 7, mass=h, mass_field=mf, method="dense"))[-1]
+    tm = E.trace_prefix(E.wilson_quadratures(dims, U, 0.12, 0, s, 7, mass=-h, mass_field=mf, method="dense"))[-1]
+    assert np.isclose(((tp - tm) / (2 * h)).real, np.sum(g).real, rtol=1e-7)

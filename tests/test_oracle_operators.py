@@ -1,0 +1,91 @@
+"""Pins of the oracle's operators and solvers against closed forms and library routines."""
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from oracle import operators as O
+from oracle import solvers as S
+from paper_1302_4018_gb300 import synth
+from pins import free_wilson_trace_inverse, laplacian_eigenvalues, laplacian_trace_inverse
+
+
+def test_gamma_clifford_and_hermitian():
+    g = O.gamma_matrices()
+    for m in range(4):
+        assert np.allclose(g[m].conj().T, g[m])
+        for n in range(4):
+            assert np.allclose(g[m] @ g[n] + g[n] @ g[m], 2.0 * (m == n) * np.eye(4))
+    assert np.allclose(g[4], np.diag([1, 1, -1, -1]))
+
+
+def test_links_are_special_unitary():
+    U = synth.gauge_links((4, 4, 2, 2), 0.4, 17).reshape(-1, 3, 3)
+    assert np.allclose(U @ np.conj(np.swapaxes(U, -1, -2)), np.eye(3), atol=1e-13)
+    assert np.allclose(np.linalg.det(U), 1.0, atol=1e-13)
+    # eps -> 0: links approach the identity like 1 + i eps H
+    U0 = synth.gauge_links((2, 2, 2, 2), 1e-8, 3).reshape(-1, 3, 3)
+    assert np.allclose(U0, np.eye(3), atol=1e-6)
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 3, 4, 5), (8, 1, 2, 4)])
+def test_laplacian_apply_equals_dense(dims):
+    A = O.laplacian_dense(dims, 0.05)
+    x = synth.random_real_fields(dims, 1, 3)[0]
+    assert np.allclose(A @ x, O.laplacian_apply(x, dims, 0.05), atol=1e-12)
+    assert np.allclose(A, A.T)
+    # the constant vector (h_0) is the lowest eigenvector with eigenvalue m (Section 5.1 remark)
+    assert np.allclose(O.laplacian_apply(np.ones(A.shape[0]), dims, 0.05), 0.05)
+
+
+@pytest.mark.parametrize("dims,m", [((4, 4, 4, 4), 0.05), ((8, 8, 8, 8), 0.05), ((6, 4, 3, 2), 0.3)])
+def test_laplacian_trace_closed_form(dims, m):
+    A = O.laplacian_dense(dims, m)
+    assert np.isclose(np.trace(np.linalg.inv(A)), laplacian_trace_inverse(dims, m), rtol=1e-11)
+    assert np.allclose(np.sort(np.linalg.eigvalsh(A)), np.sort(laplacian_eigenvalues(dims, m)), atol=1e-10)
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 4), (4, 2, 2, 2), (3, 2, 2, 2)])
+def test_wilson_apply_equals_dense_and_adjoint(dims):
+    U = synth.gauge_links(dims, 0.3, 5)
+    mf = synth.mass_field(dims, 0.01, 9)
+    D = O.wilson_dense(U, dims, 0.12, 0.02, mf)
+    psi = synth.random_spinors(dims, 1, 3)[0]
+    assert np.allclose(D @ psi.reshape(-1), O.wilson_apply(psi, U, dims, 0.12, 0.02, mf).reshape(-1))
+    assert np.allclose(D.conj().T @ psi.reshape(-1),
+                       O.wilson_apply(psi, U, dims, 0.12, 0.02, mf, dagger=True).reshape(-1))
+    # gamma_5-hermiticity D^H = g5 D g5
+    g5 = np.kron(np.eye(int(np.prod(dims))), np.kron(O.gamma_matrices()[4], np.eye(3)))
+    assert np.allclose(D.conj().T, g5 @ D @ g5)
+
+
+@pytest.mark.parametrize("dims,kappa", [((4, 4, 4, 4), 0.115), ((2, 4, 2, 4), 0.12), ((3, 3, 2, 4), 0.1)])
+def test_free_wilson_trace_closed_form(dims, kappa):
+    V = int(np.prod(dims))
+    U = np.broadcast_to(np.eye(3, dtype=complex), (V, 4, 3, 3)).copy()
+    D = O.wilson_dense(U, dims, kappa)
+    assert np.isclose(np.trace(np.linalg.inv(D)), free_wilson_trace_inverse(dims, kappa), rtol=1e-11)
+    # a random gauge transformation of the free field leaves the trace unchanged
+    Ug, _ = synth.gauge_transform(U, dims, 77)
+    Dg = O.wilson_dense(Ug, dims, kappa)
+    assert np.isclose(np.trace(np.linalg.inv(Dg)), free_wilson_trace_inverse(dims, kappa), rtol=1e-11)
+
+
+def test_solvers_match_dense():
+    dims = (4, 4, 2, 2)
+    b = synth.random_real_fields(dims, 1, 1)[0]
+    x, _ = S.cg(lambda v: O.laplacian_apply(v, dims, 0.05), b, tol=1e-13)
+    A = O.laplacian_dense(dims, 0.05)
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-11, atol=1e-11)
+    dims = (2, 2, 2, 4)
+    U = synth.gauge_links(dims, 0.3, 2)
+    psi = synth.random_spinors(dims, 1, 4)[0]
+    y, _ = S.bicgstab(lambda v: O.wilson_apply(v, U, dims, 0.12), psi, tol=1e-13)
+    D = O.wilson_dense(U, dims, 0.12)
+    ref = np.linalg.solve(D, psi.reshape(-1))
+    assert np.linalg.norm(y.reshape(-1) - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+def test_problem_size_golden():
+    rows = {r[0]: int(r[1]) for r in read_golden("problem_size.txt")}
+    n = 3 * 4 * rows["Ls"] ** 3 * rows["Lt"]
+    assert n == 25165824 and round(n / 2 ** 20) == rows["approx_millions"]
