@@ -1,0 +1,235 @@
+/*
+ * hprobe.h - C ABI of the GB300 hierarchical-probing library.
+ *
+ * Estimates Tr(A^-1) for lattice operators A on 4-D tori with the nested
+ * Hadamard/Fourier probing vectors of Stathopoulos, Laeuchli and Orginos,
+ * "Hierarchical probing for estimating the trace of the matrix inverse on
+ * toroidal lattices" (arXiv:1302.4018).  Every step runs in CUDA kernels
+ * compiled for sm_103a; the host code only validates, schedules and copies.
+ *
+ * Conventions shared by every call
+ *   - Sites are numbered lexicographically, x_1 fastest:
+ *       site = x_1 + L_1 (x_2 + L_2 (x_3 + L_3 x_4)).
+ *   - Unknown (spin s, colour c) of a Wilson site is 12 * site + 3 s + c.
+ *   - Buffers marked "host or device" may be either: the library asks the
+ *     CUDA driver which one it is and copies host data itself.  Buffers
+ *     marked "device" must be device memory of the context's GPU.
+ *   - The caller owns and allocates every input and output; the library
+ *     never frees caller memory.  Workspace belongs to the context.
+ *   - Work is ordered on the context's stream.  Calls that return host
+ *     results synchronise that stream before returning.
+ *   - No call aborts, throws or exits: each returns an hp_status and, on
+ *     failure, hp_last_error() describes the cause (per calling thread).
+ */
+#ifndef HPROBE_H
+#define HPROBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HP_OK = 0,
+    HP_EINVAL = 1,        /* an argument is out of range or inconsistent          */
+    HP_EUNSUPPORTED = 2,  /* valid request the method cannot serve (see below)   */
+    HP_ENOMEM = 3,        /* device or pinned-host allocation failed             */
+    HP_ECUDA = 4,         /* a CUDA runtime call failed                          */
+    HP_ENOCONV = 5,       /* some right-hand side missed tol within maxiter      */
+    HP_ETIMEOUT = 6       /* a bounded device wait gave up                       */
+} hp_status;
+
+typedef struct hp_ctx hp_ctx;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to run on (NULL: the context creates its own non-blocking stream).
+ * On success *out owns device workspace until hp_ctx_destroy. */
+hp_status hp_ctx_create(int device, void* cuda_stream, hp_ctx** out);
+void hp_ctx_destroy(hp_ctx* ctx);
+/* Message of the last failed call on this thread (never NULL). */
+const char* hp_last_error(void);
+/* Wait for all work queued on the context's stream. */
+hp_status hp_ctx_synchronize(hp_ctx* ctx);
+
+/* A lattice: ndim in [1, 8] sizes; operators need ndim <= 4 (missing
+ * dimensions are size 1).  The volume must be at most 2^31. */
+typedef struct {
+    int32_t ndim;
+    int64_t dims[8];
+} hp_lattice;
+
+/* Facts about the probing basis of a lattice (Sections 2.2, 3.3, 3.4).
+ * L_j = 2^{k_j} p_j with p_j odd; K = sum k_j binary levels; Q = prod p_j.
+ * When Q > 1 the three-colour level (theorem of Section 3.4) follows the
+ * binary levels; if its three classes are equal (R = Q / 3 each) a final
+ * dense Fourier level of size R completes the basis, otherwise only the
+ * first 2^K vectors exist (Section 2.2: no nested basis for unequal colour
+ * counts).  Entries of every vector are exp(2 pi i phase / period). */
+typedef struct {
+    int64_t volume;
+    int64_t n_vectors;       /* vectors of the nested sequence available        */
+    int32_t K, Q, R;         /* R = 0 when the odd classes are unequal          */
+    int32_t period;          /* P: common period of all phases (even)           */
+    int32_t kmax;
+    int32_t ks[8], ps[8];
+} hp_basis;
+
+hp_status hp_basis_info(const hp_lattice* lat, hp_basis* out);
+
+/* The value table of the phases: out[2k], out[2k+1] = cos, sin of 2 pi k / P
+ * for k = 0 .. P-1 (host array of 2P doubles), each rounded once to binary64
+ * from a double-double evaluation after an exact octant reduction.  These
+ * are the entries exp(2 pi i k / P) of the Fourier matrices of Eq.
+ * (FourierElements) used by the device.  Host-only; needs no GPU.
+ * Errors: HP_EINVAL for P < 1 or P > 65535 or out == NULL. */
+hp_status hp_phase_values(int32_t period, double* out);
+
+/* Hierarchical permutation (Section 3, Algorithm 5 with the closed form of
+ * the red-black table from the third lemma of Section 3.3, then the
+ * three-colour level of Section 3.4 for odd factors).
+ * loc_dev[site] (device, uint32[V]) receives the 0-based position of the
+ * site in the hierarchical order, i.e. the inverse permutation "iperm" of
+ * Section 2.1.  The binary levels give the most significant digits; inside
+ * a level dimension 1 gives the most significant bit.
+ * Errors: HP_EINVAL for ndim outside [1,8], a size < 1 or V > 2^31. */
+hp_status hp_permutation(hp_ctx* ctx, const hp_lattice* lat, uint32_t* loc_dev);
+
+/* Probing vectors v_m = z_0 (.) z_m for m = first .. first+count-1 (Section 2.2,
+ * Eq. row-col-permutation generalised to Eq. Hperm-general-recursive, and
+ * Section 4, Eq. removebias).  phase_dev (device, uint16[count][V]) receives
+ * phase[j * V + site] with v_{first+j}(site) = exp(2 pi i phase / P);
+ * *period_out (host) receives P.  z0_seed == 0 means z_0 = 1; otherwise
+ * z_0(site) = -1 iff the top bit of output number `site` (0-based) of
+ * Vigna's SplitMix64 generator seeded with z0_seed is set.
+ * Errors: HP_EINVAL for first < 0, count < 0 or first+count > V;
+ * HP_EUNSUPPORTED when first+count exceeds n_vectors (unequal odd classes). */
+hp_status hp_probe_vectors(hp_ctx* ctx, const hp_lattice* lat, int64_t first, int64_t count,
+                           uint64_t z0_seed, uint16_t* phase_dev, int32_t* period_out);
+
+typedef enum { HP_OP_LAPLACIAN = 0, HP_OP_WILSON = 1 } hp_op_kind;
+
+/* The operator A (Section 5: shifted periodic Laplacian; Section 1.1.1 and
+ * 5.3: Wilson-Dirac matrix, here without the clover term).
+ *   Laplacian:  (A x)(s) = (8 + mass + mu(s)) x(s) - sum_mu [x(s+mu) + x(s-mu)]
+ *   Wilson:     (D psi)(s) = (1 + mass + mu(s)) psi(s)
+ *                 - kappa sum_mu [(1 - g_mu) U_mu(s) psi(s+mu) + (1 + g_mu) U_mu(s-mu)^H psi(s-mu)]
+ *     chiral gamma basis: g_k = [[0, -i sigma_k], [i sigma_k, 0]] (k = 1..3),
+ *     g_4 = [[0, 1], [1, 0]], g_5 = diag(1, 1, -1, -1); direction mu = k runs along x_k.
+ * links: Wilson only, complex128 [V][4][3][3] (row-major 3x3 per site and
+ *        direction, real/imaginary interleaved), host or device, special unitary.
+ * mass_field: optional mu(s), double[V], host or device; NULL means 0. */
+typedef struct {
+    int32_t kind;
+    double mass;
+    double kappa;
+    const double* links;
+    const double* mass_field;
+} hp_operator;
+
+typedef enum {
+    HP_PREC_FP64 = 0,        /* everything in FP64                                       */
+    HP_PREC_MIXED_FP32 = 1,  /* FP32 iteration, FP64 reliable updates / true residual   */
+    HP_PREC_MIXED_FP16 = 2,  /* FP16 storage (per-site norm) with FP32 arithmetic inside */
+    HP_PREC_MIXED_BF16 = 3   /* BF16 storage (per-site norm) with FP32 arithmetic inside */
+} hp_precision;
+
+typedef struct {
+    int32_t precision;      /* hp_precision                                              */
+    int32_t rhs_block;      /* right-hand sides solved concurrently (0: automatic)       */
+    int32_t maxiter;        /* iterations per right-hand side (0: 10000)                 */
+    int32_t dilution;       /* 12 for Wilson (full spin-colour dilution), 1 for Laplacian; 0: default */
+    uint64_t z0_seed;       /* bias-removal vector, 0 = none (Section 4)                 */
+    int64_t first;          /* first probe to solve; q of probes < first come from q_inout */
+    double delta;           /* reliable-update threshold on ||r||/max||r|| (0: per precision) */
+    int32_t check_every;    /* iterations between host scheduling steps (0: automatic)   */
+    int32_t use_graph;      /* 1: replay the iteration chunk from a captured CUDA graph  */
+    int32_t block_threads;  /* threads per block of the stencil kernels (0: autotune)     */
+    int32_t reserved[5];
+} hp_solver_opts;
+
+typedef struct {
+    int64_t rhs_solved;
+    int64_t iterations_total;     /* sum over right-hand sides                         */
+    int32_t iterations_max;
+    int32_t iterations_min;
+    int64_t reliable_updates;     /* FP64 true-residual recomputations                 */
+    int64_t sloppy_matvecs;       /* per right-hand side, iteration precision          */
+    int64_t fp64_matvecs;         /* per right-hand side, FP64                         */
+    double max_true_residual;     /* max ||b - A x|| / ||b|| in FP64 at convergence    */
+    double seconds;               /* wall time of the call                             */
+    int32_t n_unconverged;
+    int32_t reserved;
+} hp_solve_stats;
+
+/* The incremental trace estimate (Section 1: (1/s) sum_k z_k^H A^-1 z_k;
+ * Section 1.1.2: each quadrature by a linear solve; Section 2.2: nested
+ * prefixes; Section 5.3: full spin-colour dilution for Wilson).
+ * For probe m and dilution index a the source is v_{m,a} = (z_0 (.) z_m) (x) e_a
+ * (Wilson; the Laplacian has one source per probe, split into real and
+ * imaginary parts when the probe is complex), solved to a TRUE relative
+ * residual ||b - A x||_2 / ||b||_2 <= tol computed in FP64.
+ *   q_m = sum_a v_{m,a}^H x_{m,a},   T_s = (1/s) sum_{m<s} q_m.
+ * q_inout (host, nullable): complex q[m] as (re, im) pairs for m < s_max;
+ *   entries m < opts->first are inputs (an earlier run), the others outputs.
+ * trace_prefix (host): (re, im) of T_s at [2 (s-1)], s = 1 .. s_max.
+ * stats (host, nullable).
+ * Errors: HP_EINVAL (s_max < 1, first outside [0, s_max), tol <= 0, bad
+ * operator fields, ndim > 4 for operators); HP_EUNSUPPORTED (s_max above
+ * n_vectors); HP_ENOCONV when a right-hand side misses tol in maxiter
+ * (outputs still filled from the last iterate). */
+hp_status hp_trace_inv(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t s_max,
+                       double tol, const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
+                       hp_solve_stats* stats);
+
+/* hp_trace_inv plus the derivative of Re T_{s_max} with respect to the
+ * per-site mass mu(s) (real):
+ *   dT/dmu(s) = -(1/s_max) sum_{m,a} sum_c conj(y_{m,a}(s,c)) x_{m,a}(s,c),  y = A^-H v.
+ * The adjoint solution comes from the forward one: the Laplacian is real
+ * symmetric (y = x) and the Wilson matrix is gamma_5-hermitian,
+ * D^-H = g_5 D^-1 g_5, so with full dilution y_{m,a} = g5_a g_5 x_{m,a}.
+ * dT_dmu: double[V], host or device.  dT_dm (host): the uniform-mass
+ * derivative sum_s dT/dmu(s).  opts->first must be 0. */
+hp_status hp_trace_inv_grad(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t s_max,
+                            double tol, const hp_solver_opts* opts, double* trace_prefix,
+                            double* dT_dmu, double* dT_dm, hp_solve_stats* stats);
+
+/* Many lattices (uneven sizes, masses, kappas) in one schedule: the
+ * right-hand sides of every lattice share one set of solver slots, so each
+ * kernel launch advances all lattices at once, and a slot that converges is
+ * refilled with the next right-hand side of any lattice.
+ * trace_prefix[i] (host) has 2 * s_max[i] doubles.  opts->first must be 0. */
+hp_status hp_trace_inv_batch(hp_ctx* ctx, int32_t nlat, const hp_operator* ops, const hp_lattice* lats,
+                             const int64_t* s_max, double tol, const hp_solver_opts* opts,
+                             double* const* trace_prefix, hp_solve_stats* stats);
+
+/* y = A x for nrhs fields in the canonical layout: Wilson complex128
+ * [nrhs][V][4][3], Laplacian double [nrhs][V]; host or device.  precision
+ * selects the stencil kernel used (the input is rounded to that storage,
+ * the result returned in FP64). */
+hp_status hp_operator_apply(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t nrhs,
+                            int32_t precision, const double* in, double* out);
+
+/* Times `iters` launches of the Wilson stencil kernel in `precision` on
+ * nrhs internal fields (CUDA events on the context stream) and reports the
+ * mean time per launch and the algorithmic bytes / flops of one launch:
+ * bytes = nrhs V (2 S + 4 L / nrhs) with S the bytes of one site's spinor
+ * and L those of one link in that precision (each spinor read and written
+ * once, the 4 links of a site read once for all right-hand sides),
+ * flops = 1368 nrhs V.  All outputs are host scalars. */
+hp_status hp_dslash_bench(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t precision,
+                          int32_t nrhs, int32_t iters, double* ms_per_launch, double* bytes_per_launch,
+                          double* flops_per_launch);
+
+/* Per-kernel timing of everything the context launches while enabled
+ * (CUDA events around each launch).  hp_profile_report writes a JSON
+ * object {"kernel": {"launches": n, "ms": t}, ...} into buf (host, size
+ * bytes, NUL-terminated, truncated if short) and clears the records. */
+hp_status hp_profile_enable(hp_ctx* ctx, int32_t on);
+hp_status hp_profile_report(hp_ctx* ctx, char* buf, int64_t size);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPROBE_H */

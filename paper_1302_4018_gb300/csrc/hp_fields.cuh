@@ -1,0 +1,418 @@
+// Device-side field storage and the Wilson stencil core.
+//
+// Spinor fields hold the right-hand sides of all solver slots:
+//   chunk k of site s of slot q lives at  base[(q * NCH + k) * Vmax + s]
+// so consecutive threads (consecutive sites) read consecutive 16-byte
+// chunks (fully coalesced 128-bit accesses).
+//   FP64: 12 chunks of double2 (one complex each)
+//   FP32:  6 chunks of float4  (two complex each)
+//   FP16 / BF16: 3 chunks of uint4 (four complex each, scaled by a per-site
+//         FP32 norm = max |component| so the stored values lie in [-1, 1])
+// Links of one lattice ([4][chunks][V], same coalescing):
+//   FP64: 9 double2 per link (full 3x3)
+//   FP32: 3 float4 per link (rows 1-2, 12 reals); row 3 = conj(row1 x row2)
+//   FP16: 3 uint2 per link (rows 1-2 in binary16), row 3 reconstructed
+#pragma once
+#include "hp_internal.h"
+
+template <int PR>
+struct Real_of {
+  typedef float T;
+};
+template <>
+struct Real_of<PR64> {
+  typedef double T;
+};
+
+struct FieldPtr {
+  void* p;
+  float* nrm;   // half precisions only
+};
+
+template <int PR>
+struct SpinorIO;
+
+template <>
+struct SpinorIO<PR64> {
+  static constexpr int NCH = 12;
+  static constexpr int BYTES = 192;
+  template <typename R>
+  __device__ static __forceinline__ void load(FieldPtr f, int Vmax, int slot, int site, cplx<R> (&s)[12]) {
+    const double2* b = (const double2*)f.p + (size_t)slot * 12 * Vmax + site;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double2 v = b[(size_t)k * Vmax];
+      s[k].x = (R)v.x;
+      s[k].y = (R)v.y;
+    }
+  }
+  template <typename R>
+  __device__ static __forceinline__ void load_nc(FieldPtr f, int Vmax, int slot, int site, cplx<R> (&s)[12]) {
+    const double2* b = (const double2*)f.p + (size_t)slot * 12 * Vmax + site;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double2 v = __ldg(b + (size_t)k * Vmax);
+      s[k].x = (R)v.x;
+      s[k].y = (R)v.y;
+    }
+  }
+  template <typename R>
+  __device__ static __forceinline__ void store(FieldPtr f, int Vmax, int slot, int site, const cplx<R> (&s)[12]) {
+    double2* b = (double2*)f.p + (size_t)slot * 12 * Vmax + site;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) b[(size_t)k * Vmax] = make_double2((double)s[k].x, (double)s[k].y);
+  }
+};
+
+template <>
+struct SpinorIO<PR32> {
+  static constexpr int NCH = 6;
+  static constexpr int BYTES = 96;
+  template <typename R>
+  __device__ static __forceinline__ void unpack(const float4 (&c)[6], cplx<R> (&s)[12]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      s[2 * k].x = c[k].x;
+      s[2 * k].y = c[k].y;
+      s[2 * k + 1].x = c[k].z;
+      s[2 * k + 1].y = c[k].w;
+    }
+  }
+  template <typename R>
+  __device__ static __forceinline__ void load(FieldPtr f, int Vmax, int slot, int site, cplx<R> (&s)[12]) {
+    const float4* b = (const float4*)f.p + (size_t)slot * 6 * Vmax + site;
+    float4 c[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) c[k] = b[(size_t)k * Vmax];
+    unpack(c, s);
+  }
+  template <typename R>
+  __device__ static __forceinline__ void load_nc(FieldPtr f, int Vmax, int slot, int site, cplx<R> (&s)[12]) {
+    const float4* b = (const float4*)f.p + (size_t)slot * 6 * Vmax + site;
+    float4 c[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) c[k] = __ldg(b + (size_t)k * Vmax);
+    unpack(c, s);
+  }
+  template <typename R>
+  __device__ static __forceinline__ void store(FieldPtr f, int Vmax, int slot, int site, const cplx<R> (&s)[12]) {
+    float4* b = (float4*)f.p + (size_t)slot * 6 * Vmax + site;
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      b[(size_t)k * Vmax] = make_float4((float)s[2 * k].x, (float)s[2 * k].y, (float)s[2 * k + 1].x, (float)s[2 * k + 1].y);
+  }
+};
+
+template <int PR>
+struct Half2Ops;
+template <>
+struct Half2Ops<PR16> {
+  __device__ static __forceinline__ float2 to_f2(unsigned int u) {
+    __half2 h = *reinterpret_cast<__half2*>(&u);
+    return __half22float2(h);
+  }
+  __device__ static __forceinline__ unsigned int from_f2(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<unsigned int*>(&h);
+  }
+};
+template <>
+struct Half2Ops<PRB16> {
+  __device__ static __forceinline__ float2 to_f2(unsigned int u) {
+    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&u);
+    return __bfloat1622float2(h);
+  }
+  __device__ static __forceinline__ unsigned int from_f2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<unsigned int*>(&h);
+  }
+};
+
+template <int PR>
+struct SpinorIOHalf {
+  static constexpr int NCH = 3;
+  static constexpr int BYTES = 52;   // 48 bytes of values + 4 bytes of norm
+  template <typename R>
+  __device__ static __forceinline__ void unpack(const uint4 (&c)[3], float n, cplx<R> (&s)[12]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float2 a = Half2Ops<PR>::to_f2(c[k].x), b = Half2Ops<PR>::to_f2(c[k].y);
+      float2 d = Half2Ops<PR>::to_f2(c[k].z), e = Half2Ops<PR>::to_f2(c[k].w);
+      s[4 * k + 0] = {a.x * n, a.y * n};
+      s[4 * k + 1] = {b.x * n, b.y * n};
+      s[4 * k + 2] = {d.x * n, d.y * n};
+      s[4 * k + 3] = {e.x * n, e.y * n};
+    }
+  }
+  template <typename R>
+  __device__ static __forceinline__ void load(FieldPtr f, int Vmax, int slot, int site, cplx<R> (&s)[12]) {
+    const uint4* b = (const uint4*)f.p + (size_t)slot * 3 * Vmax + site;
+    uint4 c[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[k] = b[(size_t)k * Vmax];
+    unpack(c, f.nrm[(size_t)slot * Vmax + site], s);
+  }
+  template <typename R>
+  __device__ static __forceinline__ void load_nc(FieldPtr f, int Vmax, int slot, int site, cplx<R> (&s)[12]) {
+    const uint4* b = (const uint4*)f.p + (size_t)slot * 3 * Vmax + site;
+    uint4 c[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[k] = __ldg(b + (size_t)k * Vmax);
+    unpack(c, __ldg(f.nrm + (size_t)slot * Vmax + site), s);
+  }
+  template <typename R>
+  __device__ static __forceinline__ void store(FieldPtr f, int Vmax, int slot, int site, const cplx<R> (&s)[12]) {
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf((float)s[k].x), fabsf((float)s[k].y)));
+    float inv = m > 0.f ? 1.0f / m : 0.f;
+    uint4* b = (uint4*)f.p + (size_t)slot * 3 * Vmax + site;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 c;
+      c.x = Half2Ops<PR>::from_f2((float)s[4 * k].x * inv, (float)s[4 * k].y * inv);
+      c.y = Half2Ops<PR>::from_f2((float)s[4 * k + 1].x * inv, (float)s[4 * k + 1].y * inv);
+      c.z = Half2Ops<PR>::from_f2((float)s[4 * k + 2].x * inv, (float)s[4 * k + 2].y * inv);
+      c.w = Half2Ops<PR>::from_f2((float)s[4 * k + 3].x * inv, (float)s[4 * k + 3].y * inv);
+      b[(size_t)k * Vmax] = c;
+    }
+    f.nrm[(size_t)slot * Vmax + site] = m;
+  }
+};
+template <>
+struct SpinorIO<PR16> : SpinorIOHalf<PR16> {};
+template <>
+struct SpinorIO<PRB16> : SpinorIOHalf<PRB16> {};
+
+// ------------------------------------------------------------------- links
+template <typename R>
+__device__ __forceinline__ void reconstruct_row3(cplx<R> (&u)[9]) {
+  // row 3 = conj(row1 x row2), exact for special-unitary links
+  cplx<R> a = cmul(u[1], u[5]), b = cmul(u[2], u[4]);
+  u[6] = {a.x - b.x, -(a.y - b.y)};
+  a = cmul(u[2], u[3]);
+  b = cmul(u[0], u[5]);
+  u[7] = {a.x - b.x, -(a.y - b.y)};
+  a = cmul(u[0], u[4]);
+  b = cmul(u[1], u[3]);
+  u[8] = {a.x - b.x, -(a.y - b.y)};
+}
+
+template <int LPR>
+struct LinkIO;
+
+template <>
+struct LinkIO<PR64> {
+  static constexpr int BYTES = 144;
+  template <typename R>
+  __device__ static __forceinline__ void load(const LatGeom& g, int mu, int site, cplx<R> (&u)[9]) {
+    const double2* b = g.U64 + (size_t)mu * 9 * g.V + site;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      double2 v = __ldg(b + (size_t)k * g.V);
+      u[k].x = (R)v.x;
+      u[k].y = (R)v.y;
+    }
+  }
+};
+
+template <>
+struct LinkIO<PR32> {
+  static constexpr int BYTES = 48;
+  template <typename R>
+  __device__ static __forceinline__ void load(const LatGeom& g, int mu, int site, cplx<R> (&u)[9]) {
+    const float4* b = g.U32 + (size_t)mu * 3 * g.V + site;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float4 v = __ldg(b + (size_t)k * g.V);
+      u[2 * k] = {v.x, v.y};
+      u[2 * k + 1] = {v.z, v.w};
+    }
+    reconstruct_row3(u);
+  }
+};
+
+template <>
+struct LinkIO<PR16> {
+  static constexpr int BYTES = 24;
+  template <typename R>
+  __device__ static __forceinline__ void load(const LatGeom& g, int mu, int site, cplx<R> (&u)[9]) {
+    const uint2* b = g.U16 + (size_t)mu * 3 * g.V + site;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint2 v = __ldg(b + (size_t)k * g.V);
+      float2 a = Half2Ops<PR16>::to_f2(v.x), c = Half2Ops<PR16>::to_f2(v.y);
+      u[2 * k] = {a.x, a.y};
+      u[2 * k + 1] = {c.x, c.y};
+    }
+    reconstruct_row3(u);
+  }
+};
+
+template <int SPR>
+struct LinkPrecOf {
+  static constexpr int v = (SPR == PR64) ? PR64 : (SPR == PR32 ? PR32 : PR16);
+};
+
+// ------------------------------------------------------------- stencil core
+// Spin projection in the chiral basis: g_mu = [[0, A], [A^H, 0]] with
+// A_1 = -i s_1, A_2 = -i s_2, A_3 = -i s_3, A_4 = 1.
+//   (1 - g_mu) psi = [h ; -A^H h],  h = psi_up - A psi_dn
+//   (1 + g_mu) psi = [h ;  A^H h],  h = psi_up + A psi_dn
+// Component index 3*spin + colour.
+template <typename R>
+__device__ __forceinline__ cplx<R> c_add(cplx<R> a, cplx<R> b) { return {a.x + b.x, a.y + b.y}; }
+template <typename R>
+__device__ __forceinline__ cplx<R> c_sub(cplx<R> a, cplx<R> b) { return {a.x - b.x, a.y - b.y}; }
+template <typename R>
+__device__ __forceinline__ cplx<R> c_addi(cplx<R> a, cplx<R> b) { return {a.x - b.y, a.y + b.x}; }  // a + i b
+template <typename R>
+__device__ __forceinline__ cplx<R> c_subi(cplx<R> a, cplx<R> b) { return {a.x + b.y, a.y - b.x}; }  // a - i b
+
+template <int MU, int SIGN, typename R>   // SIGN = -1: (1 - g), +1: (1 + g)
+__device__ __forceinline__ void project(const cplx<R> (&p)[12], cplx<R> (&h)[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    cplx<R> p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
+    if (MU == 0) {
+      h[c] = SIGN < 0 ? c_addi(p0, p3) : c_subi(p0, p3);
+      h[3 + c] = SIGN < 0 ? c_addi(p1, p2) : c_subi(p1, p2);
+    } else if (MU == 1) {
+      h[c] = SIGN < 0 ? c_add(p0, p3) : c_sub(p0, p3);
+      h[3 + c] = SIGN < 0 ? c_sub(p1, p2) : c_add(p1, p2);
+    } else if (MU == 2) {
+      h[c] = SIGN < 0 ? c_addi(p0, p2) : c_subi(p0, p2);
+      h[3 + c] = SIGN < 0 ? c_subi(p1, p3) : c_addi(p1, p3);
+    } else {
+      h[c] = SIGN < 0 ? c_sub(p0, p2) : c_add(p0, p2);
+      h[3 + c] = SIGN < 0 ? c_sub(p1, p3) : c_add(p1, p3);
+    }
+  }
+}
+
+template <int MU, int SIGN, typename R>
+__device__ __forceinline__ void accumulate(cplx<R> (&acc)[12], const cplx<R> (&w)[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    cplx<R> w0 = w[c], w1 = w[3 + c];
+    acc[c] = c_add(acc[c], w0);
+    acc[3 + c] = c_add(acc[3 + c], w1);
+    if (MU == 0) {   // -A^H v = (-i v1, -i v0);  A^H w = (i w1, i w0)
+      acc[6 + c] = SIGN < 0 ? c_subi(acc[6 + c], w1) : c_addi(acc[6 + c], w1);
+      acc[9 + c] = SIGN < 0 ? c_subi(acc[9 + c], w0) : c_addi(acc[9 + c], w0);
+    } else if (MU == 1) {   // -A^H v = (-v1, v0);  A^H w = (w1, -w0)
+      acc[6 + c] = SIGN < 0 ? c_sub(acc[6 + c], w1) : c_add(acc[6 + c], w1);
+      acc[9 + c] = SIGN < 0 ? c_add(acc[9 + c], w0) : c_sub(acc[9 + c], w0);
+    } else if (MU == 2) {   // -A^H v = (-i v0, i v1);  A^H w = (i w0, -i w1)
+      acc[6 + c] = SIGN < 0 ? c_subi(acc[6 + c], w0) : c_addi(acc[6 + c], w0);
+      acc[9 + c] = SIGN < 0 ? c_addi(acc[9 + c], w1) : c_subi(acc[9 + c], w1);
+    } else {   // -A^H v = -v;  A^H w = w
+      acc[6 + c] = SIGN < 0 ? c_sub(acc[6 + c], w0) : c_add(acc[6 + c], w0);
+      acc[9 + c] = SIGN < 0 ? c_sub(acc[9 + c], w1) : c_add(acc[9 + c], w1);
+    }
+  }
+}
+
+template <typename R, bool DAG>
+__device__ __forceinline__ void su3_mul(const cplx<R> (&u)[9], const cplx<R> (&h)[6], cplx<R> (&w)[6]) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      cplx<R> acc = {0, 0};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        cplx<R> a = DAG ? u[3 * c + r] : u[3 * r + c];
+        cplx<R> b = h[3 * s + c];
+        if (DAG) {   // conj(a) * b
+          acc.x = fma(a.x, b.x, acc.x);
+          acc.x = fma(a.y, b.y, acc.x);
+          acc.y = fma(a.x, b.y, acc.y);
+          acc.y = fma(-a.y, b.x, acc.y);
+        } else {
+          acc.x = fma(a.x, b.x, acc.x);
+          acc.x = fma(-a.y, b.y, acc.x);
+          acc.y = fma(a.x, b.y, acc.y);
+          acc.y = fma(a.y, b.x, acc.y);
+        }
+      }
+      w[3 * s + r] = acc;
+    }
+  }
+}
+
+struct SiteCoords {
+  int x[4];
+};
+
+__device__ __forceinline__ void site_coords(const LatGeom& g, int site, int (&x)[4], int (&st)[4]) {
+  int r = site;
+  int s = 1;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    x[j] = r % g.L[j];
+    r /= g.L[j];
+    st[j] = s;
+    s *= g.L[j];
+  }
+}
+
+// hop = sum_mu [(1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^H psi(x-mu)]
+template <int SPR, int LPR, typename R>
+__device__ __forceinline__ void wilson_hop(const LatGeom& g, FieldPtr in, int Vmax, int slot, int site,
+                                           const int (&x)[4], const int (&st)[4], cplx<R> (&acc)[12]) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = {0, 0};
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int L = g.L[mu];
+    const int fw = (x[mu] + 1 == L) ? site - (L - 1) * st[mu] : site + st[mu];
+    const int bw = (x[mu] == 0) ? site + (L - 1) * st[mu] : site - st[mu];
+    cplx<R> psi[12], h[6], w[6], u[9];
+    SpinorIO<SPR>::load_nc(in, Vmax, slot, fw, psi);
+    LinkIO<LPR>::load(g, mu, site, u);
+    if (mu == 0) project<0, -1>(psi, h);
+    if (mu == 1) project<1, -1>(psi, h);
+    if (mu == 2) project<2, -1>(psi, h);
+    if (mu == 3) project<3, -1>(psi, h);
+    su3_mul<R, false>(u, h, w);
+    if (mu == 0) accumulate<0, -1>(acc, w);
+    if (mu == 1) accumulate<1, -1>(acc, w);
+    if (mu == 2) accumulate<2, -1>(acc, w);
+    if (mu == 3) accumulate<3, -1>(acc, w);
+    SpinorIO<SPR>::load_nc(in, Vmax, slot, bw, psi);
+    LinkIO<LPR>::load(g, mu, bw, u);
+    if (mu == 0) project<0, 1>(psi, h);
+    if (mu == 1) project<1, 1>(psi, h);
+    if (mu == 2) project<2, 1>(psi, h);
+    if (mu == 3) project<3, 1>(psi, h);
+    su3_mul<R, true>(u, h, w);
+    if (mu == 0) accumulate<0, 1>(acc, w);
+    if (mu == 1) accumulate<1, 1>(acc, w);
+    if (mu == 2) accumulate<2, 1>(acc, w);
+    if (mu == 3) accumulate<3, 1>(acc, w);
+  }
+}
+
+// (D psi)(x) = (1 + m + mu(x)) psi(x) - kappa hop; psi(x) returned in `center`
+template <int SPR, int LPR, typename R>
+__device__ __forceinline__ void wilson_site(const LatGeom& g, FieldPtr in, int Vmax, int slot, int site,
+                                            cplx<R> (&out)[12], cplx<R> (&center)[12]) {
+  int x[4], st[4];
+  site_coords(g, site, x, st);
+  cplx<R> hop[12];
+  wilson_hop<SPR, LPR, R>(g, in, Vmax, slot, site, x, st, hop);
+  SpinorIO<SPR>::load_nc(in, Vmax, slot, site, center);
+  R diag = (R)(1.0 + g.mass + (g.mass_field ? g.mass_field[site] : 0.0));
+  R kap = (R)g.kappa;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    out[k].x = diag * center[k].x - kap * hop[k].x;
+    out[k].y = diag * center[k].y - kap * hop[k].y;
+  }
+}
+
+// the source v_{m,a}(site) = (z_0 (.) z_m)(site) e_a, value of its non-zero component
+__device__ __forceinline__ double2 source_value(const LatGeom& g, int site, int m) {
+  return g.ptab[probe_phase(g, (uint32_t)site, (uint32_t)m)];
+}

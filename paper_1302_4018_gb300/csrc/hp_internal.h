@@ -1,0 +1,275 @@
+// Internal declarations of the hierarchical-probing library (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/hprobe.h"
+
+// ------------------------------------------------------------------ errors
+void hp_set_error(const char* fmt, ...);
+
+#define HP_CUDA(call)                                                                       \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      hp_set_error("%s failed at %s:%d: %s", #call, __FILE__, __LINE__, cudaGetErrorString(e_)); \
+      return HP_ECUDA;                                                                      \
+    }                                                                                       \
+  } while (0)
+
+#define HP_TRY(expr)                     \
+  do {                                   \
+    hp_status s_ = (expr);               \
+    if (s_ != HP_OK) return s_;          \
+  } while (0)
+
+#define HP_LAUNCH_CHECK()                                                                   \
+  do {                                                                                      \
+    cudaError_t e_ = cudaGetLastError();                                                    \
+    if (e_ != cudaSuccess) {                                                                \
+      hp_set_error("kernel launch failed at %s:%d: %s", __FILE__, __LINE__, cudaGetErrorString(e_)); \
+      return HP_ECUDA;                                                                      \
+    }                                                                                       \
+  } while (0)
+
+// -------------------------------------------------------------- precisions
+enum { PR64 = 0, PR32 = 1, PR16 = 2, PRB16 = 3 };
+
+// ---------------------------------------------------------- lattice (device)
+// Everything a kernel needs about one lattice: geometry, probing basis and
+// operator.  Plain data, copied to device memory as an array (one entry per
+// lattice of a batch).
+struct LatGeom {
+  int nd;                 // number of dimensions (operators: padded to 4)
+  int L[8];
+  int V;
+  int ks[8];              // 2-adic valuation of each size
+  int kmax, K;            // binary levels
+  int Q, R, P;            // odd block size, final level size (0: unequal), period
+  int qstride[8];         // strides of the q-torus (sizes p_j)
+  unsigned long long z0_seed;
+  const uint32_t* loc;    // [V] hierarchical position of each site
+  const int32_t* wtab;    // [Q] position inside the odd block of each q point
+  const double2* ptab;    // [P] (cos, sin) of 2 pi k / P
+  // operator
+  int op_kind;
+  double kappa, mass;
+  const double* mass_field;   // [V] or nullptr
+  const double2* U64;         // [4][9][V]
+  const float4* U32;          // [4][3][V]  first two rows
+  const uint2* U16;           // [4][3][V]  first two rows, binary16
+  int dof;                    // unknowns per site that carry a source (12 Wilson, 1 Laplacian)
+  int parts;                  // Laplacian: 2 when probes are complex (re, im solved apart)
+};
+
+// ------------------------------------------------------------- slot state
+enum { SLOT_EMPTY = 0, SLOT_INIT = 1, SLOT_RUN = 2, SLOT_DONE = 3, SLOT_FAIL = 4 };
+
+struct SlotState {
+  double2 alpha, beta, omega, rho;   // BiCGStab scalars (CG uses .x)
+  double bnorm2, rnorm2, rmax2, true_res2;
+  double2 q;                         // quadrature v^H x at harvest
+  int status, need_update, restart, iters;
+  int updates, lat, a, m;            // lattice index, dilution index / part, probe index
+  int sloppy_mv, fp64_mv, pad0, pad1;
+};
+
+// ------------------------------------------------------------- the context
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct LatticeSetup {
+  std::vector<int64_t> dims;
+  LatGeom g;                // device pointers filled
+  DevBuf loc, wtab, ptab;
+  int64_t n_vectors = 0;
+  bool equal = false;
+};
+
+struct ProfRecord {
+  std::string name;
+  cudaEvent_t a, b;
+};
+
+struct hp_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  std::map<std::vector<int64_t>, std::unique_ptr<LatticeSetup>> lattices;
+  std::map<std::string, DevBuf> ws;          // named grow-only workspace
+  bool profiling = false;
+  std::vector<ProfRecord> prof;
+  std::vector<cudaEvent_t> event_pool;
+  std::map<std::string, int> autotune;       // key -> threads per block
+};
+
+// workspace
+hp_status hp_ws(hp_ctx* ctx, const char* name, size_t bytes, void** out);
+hp_status hp_ws_free_all(hp_ctx* ctx);
+
+// profiling around a launch
+void hp_prof_begin(hp_ctx* ctx, const char* name, cudaEvent_t* a);
+void hp_prof_end(hp_ctx* ctx, const char* name, cudaEvent_t a);
+struct ProfScope {
+  hp_ctx* ctx;
+  const char* name;
+  cudaEvent_t a = nullptr;
+  ProfScope(hp_ctx* c, const char* n) : ctx(c), name(n) { hp_prof_begin(ctx, name, &a); }
+  ~ProfScope() { hp_prof_end(ctx, name, a); }
+};
+
+// lattice setup (hp_core.cu)
+hp_status hp_validate_lattice(const hp_lattice* lat, int max_nd, std::vector<int64_t>* dims);
+hp_status hp_get_lattice(hp_ctx* ctx, const std::vector<int64_t>& dims, LatticeSetup** out);
+
+// host/device buffers: returns a device pointer to the data (copying host data
+// into workspace `name` when needed)
+hp_status hp_device_view(hp_ctx* ctx, const void* p, size_t bytes, const char* name, const void** out);
+bool hp_is_device_ptr(const void* p);
+
+// operator preparation (hp_wilson.cu): converts links to the internal
+// layouts of `geom` (allocated in workspace under `tag`)
+hp_status hp_prepare_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom* geom, const char* tag, int need_prec);
+hp_status hp_prepare_mass(hp_ctx* ctx, const hp_operator* op, LatGeom* geom, const char* tag);
+
+// ------------------------------------------------------------- solver API
+struct SolveProblem {
+  std::vector<LatGeom> lats;       // device pointers set
+  std::vector<int64_t> s_max;      // probes per lattice
+  std::vector<int64_t> first;      // first probe per lattice
+  double tol;
+  hp_solver_opts opts;
+  bool want_grad = false;
+  std::vector<double*> grad_dev;   // per lattice, [V] accumulators (device)
+};
+
+struct SolveResult {
+  std::vector<std::vector<double2>> qj;   // per lattice, per right-hand side (m*dof+a)
+  hp_solve_stats stats;
+  bool unconverged = false;
+};
+
+// implemented per operator family
+hp_status hp_solve_wilson(hp_ctx* ctx, SolveProblem& pb, SolveResult& res);
+hp_status hp_solve_laplace(hp_ctx* ctx, SolveProblem& pb, SolveResult& res);
+
+// -------------------------------------------------------- device helpers
+#ifdef __CUDACC__
+
+__device__ __forceinline__ int probe_phase(const LatGeom& g, uint32_t site, uint32_t m) {
+  uint32_t loc = g.loc[site];
+  uint32_t lb = loc, w = 0;
+  if (g.Q > 1) {
+    lb = loc / (uint32_t)g.Q;
+    w = loc - lb * (uint32_t)g.Q;
+  }
+  int ph = 0;
+  uint32_t hi = m;
+  if (g.K > 0) {
+    uint32_t ebin = m & ((1u << g.K) - 1u);
+    hi = m >> g.K;
+    uint32_t col = __brev(ebin) >> (32 - g.K);       // Hperm(m) = bit reversal over K bits
+    ph = (__popc(lb & col) & 1) * (g.P >> 1);
+  }
+  if (hi > 0 && g.R > 0) {                             // three-colour level and final Fourier level
+    uint32_t e3 = hi % 3u, ef = hi / 3u;
+    uint32_t C = w / (uint32_t)g.R, r = w - C * (uint32_t)g.R;
+    ph += (g.P / 3) * (int)((C * e3) % 3u);
+    ph += (g.P / g.R) * (int)((unsigned long long)r * ef % (unsigned long long)g.R);
+  }
+  if (g.z0_seed) {
+    unsigned long long z = g.z0_seed + (unsigned long long)(site + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    if (z >> 63) ph += g.P >> 1;
+  }
+  return ph % g.P;
+}
+
+template <typename T>
+struct cplx {
+  T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cconjmul(cplx<T> a, cplx<T> b) {  // conj(a) * b
+  return {a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x};
+}
+
+// block-level deterministic reduction helpers (fixed shuffle tree, fixed warp order)
+template <int NQ, int NTHREADS>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NQ], double* out_q0, size_t q_stride) {
+  __shared__ double sh[NQ][NTHREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double t = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) sh[q][warp] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double t = 0.0;
+      for (int w = 0; w < NTHREADS / 32; ++w) t += sh[q][w];
+      out_q0[q * q_stride] = t;
+    }
+  }
+}
+
+// returns true in every thread of the block that finishes last for this slot
+__device__ __forceinline__ bool last_block(unsigned int* counter, unsigned int nparts) {
+  __shared__ int am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int t = atomicAdd(counter, 1u);
+    am_last = (t == nparts - 1u);
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last != 0;
+}
+
+// sum of partials[q][0..nparts) in a fixed order by one block; result in every thread's out[q]
+template <int NQ, int NTHREADS>
+__device__ __forceinline__ void block_sum_partials(const double* part, size_t q_stride, int nparts, double (&out)[NQ]) {
+  __shared__ double sh2[NQ][NTHREADS];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += NTHREADS) t += __ldcg(part + q * q_stride + i);
+    sh2[q][threadIdx.x] = t;
+  }
+  __syncthreads();
+  for (int s = NTHREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) sh2[q][threadIdx.x] += sh2[q][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) out[q] = sh2[q][0];
+  __syncthreads();
+}
+
+#endif  // __CUDACC__

@@ -1,0 +1,281 @@
+"""Python binding of libhprobe.so (include/hprobe.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module only converts
+Python / torch arguments to the C structs and pointers of the ABI and turns
+error codes into exceptions.  Importing it loads the library and raises
+``HProbeLibraryMissing`` when it is absent: there is no fallback path.
+
+Device buffers are torch CUDA tensors (their ``data_ptr``); host buffers are
+numpy arrays.  Names follow the C ABI: ``permutation``, ``probe_vectors``,
+``trace_inv``, ``trace_inv_grad``, ``trace_inv_batch``, ``operator_apply``,
+``dslash_bench``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhprobe.so")
+
+
+class HProbeLibraryMissing(RuntimeError):
+    pass
+
+
+class HProbeError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("hprobe status %d: %s" % (status, msg))
+        self.status = status
+
+
+HP_OK, HP_EINVAL, HP_EUNSUPPORTED, HP_ENOMEM, HP_ECUDA, HP_ENOCONV, HP_ETIMEOUT = range(7)
+OP_LAPLACIAN, OP_WILSON = 0, 1
+PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
+
+EXPORTED = ["hp_ctx_create", "hp_ctx_destroy", "hp_last_error", "hp_ctx_synchronize", "hp_basis_info",
+            "hp_phase_values",
+            "hp_permutation", "hp_probe_vectors", "hp_trace_inv", "hp_trace_inv_grad", "hp_trace_inv_batch",
+            "hp_operator_apply", "hp_dslash_bench", "hp_profile_enable", "hp_profile_report"]
+
+
+class Lattice(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("dims", C.c_int64 * 8)]
+
+
+class Basis(C.Structure):
+    _fields_ = [("volume", C.c_int64), ("n_vectors", C.c_int64), ("K", C.c_int32), ("Q", C.c_int32),
+                ("R", C.c_int32), ("period", C.c_int32), ("kmax", C.c_int32), ("ks", C.c_int32 * 8),
+                ("ps", C.c_int32 * 8)]
+
+
+class Operator(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("mass", C.c_double), ("kappa", C.c_double),
+                ("links", C.c_void_p), ("mass_field", C.c_void_p)]
+
+
+class SolverOpts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("rhs_block", C.c_int32), ("maxiter", C.c_int32),
+                ("dilution", C.c_int32), ("z0_seed", C.c_uint64), ("first", C.c_int64), ("delta", C.c_double),
+                ("check_every", C.c_int32), ("use_graph", C.c_int32), ("block_threads", C.c_int32),
+                ("reserved", C.c_int32 * 5)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("rhs_solved", C.c_int64), ("iterations_total", C.c_int64), ("iterations_max", C.c_int32),
+                ("iterations_min", C.c_int32), ("reliable_updates", C.c_int64), ("sloppy_matvecs", C.c_int64),
+                ("fp64_matvecs", C.c_int64), ("max_true_residual", C.c_double), ("seconds", C.c_double),
+                ("n_unconverged", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise HProbeLibraryMissing("libhprobe.so not built (run __graft_entry__.build()): %s" % path)
+    lib = C.CDLL(path)
+    P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "hp_ctx_create": (C.c_int, [C.c_int, P, C.POINTER(P)]),
+        "hp_ctx_destroy": (None, [P]),
+        "hp_last_error": (C.c_char_p, []),
+        "hp_ctx_synchronize": (C.c_int, [P]),
+        "hp_basis_info": (C.c_int, [C.POINTER(Lattice), C.POINTER(Basis)]),
+        "hp_phase_values": (C.c_int, [I32, P]),
+        "hp_permutation": (C.c_int, [P, C.POINTER(Lattice), P]),
+        "hp_probe_vectors": (C.c_int, [P, C.POINTER(Lattice), I64, I64, C.c_uint64, P, C.POINTER(I32)]),
+        "hp_trace_inv": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I64, D, C.POINTER(SolverOpts),
+                                   P, P, C.POINTER(SolveStats)]),
+        "hp_trace_inv_grad": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I64, D,
+                                        C.POINTER(SolverOpts), P, P, P, C.POINTER(SolveStats)]),
+        "hp_trace_inv_batch": (C.c_int, [P, I32, P, P, P, D, C.POINTER(SolverOpts), P, C.POINTER(SolveStats)]),
+        "hp_operator_apply": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I64, I32, P, P]),
+        "hp_dslash_bench": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I32, I32, I32,
+                                      C.POINTER(D), C.POINTER(D), C.POINTER(D)]),
+        "hp_profile_enable": (C.c_int, [P, I32]),
+        "hp_profile_report": (C.c_int, [P, C.c_char_p, I64]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_LIB: Optional[C.CDLL] = None
+
+
+def lib() -> C.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = load_library()
+    return _LIB
+
+
+def _check(status: int):
+    if status != HP_OK:
+        raise HProbeError(status, lib().hp_last_error().decode())
+
+
+def make_lattice(dims: Sequence[int]) -> Lattice:
+    lat = Lattice()
+    lat.ndim = len(dims)
+    for j, v in enumerate(dims):
+        lat.dims[j] = int(v)
+    return lat
+
+
+def basis_info(dims: Sequence[int]) -> dict:
+    b = Basis()
+    _check(lib().hp_basis_info(C.byref(make_lattice(dims)), C.byref(b)))
+    return {"volume": b.volume, "n_vectors": b.n_vectors, "K": b.K, "Q": b.Q, "R": b.R, "period": b.period,
+            "kmax": b.kmax, "ks": list(b.ks)[:len(dims)], "ps": list(b.ps)[:len(dims)]}
+
+
+def phase_values(period: int) -> np.ndarray:
+    """(cos, sin) table of 2 pi k / P from the library (host code)."""
+    out = np.zeros((period, 2), dtype=np.float64)
+    _check(lib().hp_phase_values(int(period), out.ctypes.data))
+    return out
+
+
+def _ptr(x) -> Optional[int]:
+    """data pointer of a torch tensor or numpy array (None passes through)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    assert x.is_contiguous()
+    return x.data_ptr()
+
+
+class Context:
+    """hp_ctx on one CUDA device, optionally on an existing cudaStream_t (int handle)."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        h = C.c_void_p()
+        _check(lib().hp_ctx_create(int(device), C.c_void_p(stream) if stream else None, C.byref(h)))
+        self._h = h
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().hp_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def synchronize(self):
+        _check(lib().hp_ctx_synchronize(self._h))
+
+    # ---------------------------------------------------------------- integer path
+    def permutation(self, dims: Sequence[int], out):
+        """loc into ``out`` (device int32/uint32 tensor of V entries)."""
+        _check(lib().hp_permutation(self._h, C.byref(make_lattice(dims)), _ptr(out)))
+        return out
+
+    def probe_vectors(self, dims: Sequence[int], first: int, count: int, z0_seed: int, out) -> int:
+        """uint16 phases into ``out`` (device int16/uint16 tensor of count*V); returns the period."""
+        per = C.c_int32()
+        _check(lib().hp_probe_vectors(self._h, C.byref(make_lattice(dims)), int(first), int(count),
+                                      C.c_uint64(z0_seed), _ptr(out), C.byref(per)))
+        return per.value
+
+    # ---------------------------------------------------------------- operators
+    @staticmethod
+    def make_operator(kind: int, mass: float = 0.0, kappa: float = 0.0, links=None, mass_field=None) -> Operator:
+        op = Operator()
+        op.kind = kind
+        op.mass = float(mass)
+        op.kappa = float(kappa)
+        op.links = _ptr(links)
+        op.mass_field = _ptr(mass_field)
+        return op
+
+    @staticmethod
+    def make_opts(precision="fp64", rhs_block=0, maxiter=0, z0_seed=0, first=0, delta=0.0, check_every=0,
+                  use_graph=0, block_threads=0, dilution=0) -> SolverOpts:
+        o = SolverOpts()
+        o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+        o.rhs_block = rhs_block
+        o.maxiter = maxiter
+        o.dilution = dilution
+        o.z0_seed = z0_seed
+        o.first = first
+        o.delta = delta
+        o.check_every = check_every
+        o.use_graph = use_graph
+        o.block_threads = block_threads
+        return o
+
+    def operator_apply(self, op: Operator, dims, nrhs: int, precision, inp, out):
+        prec = PREC[precision] if isinstance(precision, str) else int(precision)
+        _check(lib().hp_operator_apply(self._h, C.byref(op), C.byref(make_lattice(dims)), int(nrhs), prec,
+                                       _ptr(inp), _ptr(out)))
+        return out
+
+    def trace_inv(self, op: Operator, dims, s_max: int, tol: float, opts: SolverOpts, q_inout=None):
+        """Returns (T [s_max] complex, q [s_max] complex or None, stats dict).  ``q_inout``: host
+        complex128 array of s_max (entries < opts.first are inputs)."""
+        T = np.zeros(s_max, dtype=np.complex128)
+        st = SolveStats()
+        if q_inout is not None:
+            assert q_inout.dtype == np.complex128 and q_inout.shape == (s_max,)
+        _check(lib().hp_trace_inv(self._h, C.byref(op), C.byref(make_lattice(dims)), int(s_max), float(tol),
+                                  C.byref(opts), _ptr(q_inout), _ptr(T), C.byref(st)))
+        return T, q_inout, st.as_dict()
+
+    def trace_inv_grad(self, op: Operator, dims, s_max: int, tol: float, opts: SolverOpts, grad_out):
+        """Returns (T, dT/dm, stats); dT/dmu(x) is written into ``grad_out`` (host float64 array or
+        device float64 tensor of V)."""
+        T = np.zeros(s_max, dtype=np.complex128)
+        dm = C.c_double()
+        st = SolveStats()
+        _check(lib().hp_trace_inv_grad(self._h, C.byref(op), C.byref(make_lattice(dims)), int(s_max), float(tol),
+                                       C.byref(opts), _ptr(T), _ptr(grad_out), C.byref(dm), C.byref(st)))
+        return T, dm.value, st.as_dict()
+
+    def trace_inv_batch(self, ops: Sequence[Operator], dims_list, s_max: Sequence[int], tol: float,
+                        opts: SolverOpts):
+        n = len(ops)
+        ops_arr = (Operator * n)(*ops)
+        lats = (Lattice * n)(*[make_lattice(d) for d in dims_list])
+        smax = (C.c_int64 * n)(*[int(s) for s in s_max])
+        outs = [np.zeros(int(s), dtype=np.complex128) for s in s_max]
+        ptrs = (C.c_void_p * n)(*[o.ctypes.data for o in outs])
+        st = SolveStats()
+        _check(lib().hp_trace_inv_batch(self._h, n, C.cast(ops_arr, C.c_void_p), C.cast(lats, C.c_void_p),
+                                        C.cast(smax, C.c_void_p), float(tol), C.byref(opts),
+                                        C.cast(ptrs, C.c_void_p), C.byref(st)))
+        return outs, st.as_dict()
+
+    def dslash_bench(self, op: Operator, dims, precision, nrhs: int, iters: int) -> dict:
+        ms, by, fl = C.c_double(), C.c_double(), C.c_double()
+        prec = PREC[precision] if isinstance(precision, str) else int(precision)
+        _check(lib().hp_dslash_bench(self._h, C.byref(op), C.byref(make_lattice(dims)), prec, int(nrhs),
+                                     int(iters), C.byref(ms), C.byref(by), C.byref(fl)))
+        return {"ms": ms.value, "bytes": by.value, "flops": fl.value}
+
+    # ---------------------------------------------------------------- profiling
+    def profile_enable(self, on: bool = True):
+        _check(lib().hp_profile_enable(self._h, 1 if on else 0))
+
+    def profile_report(self) -> dict:
+        buf = C.create_string_buffer(1 << 16)
+        _check(lib().hp_profile_report(self._h, buf, len(buf)))
+        return json.loads(buf.value.decode())

@@ -1,0 +1,354 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+Integer work (permutation, probe phases) is compared bit for bit; stencils
+within the rounding of their storage precision; trace estimates within
+1e-9 relative (the tolerance the solver residual 1e-10 supports: the error
+of q is |v^H D^-1 r| <= ||v|| ||D^-1|| ||r||, and ||D^-1|| < 10 here).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import estimator as E
+from oracle import operators as O
+from oracle import permutation as P
+from oracle import probing as Pr
+from paper_1302_4018_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TRACE_RTOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def hp():
+    from paper_1302_4018_gb300 import build as b
+
+    b.build()
+    from paper_1302_4018_gb300 import hprobe
+
+    return hprobe
+
+
+@pytest.fixture(scope="module")
+def ctx(hp):
+    assert torch.cuda.is_available()
+    c = hp.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+
+
+def links_dev(U):
+    return dev(U.view(np.float64).reshape(-1))
+
+
+# ------------------------------------------------------------------ integer path
+@pytest.mark.parametrize("dims", [(4, 4), (2, 4, 8), (8, 8, 8, 8), (4, 4, 4, 8), (12, 12), (6, 6, 6, 6),
+                                  (3, 3, 3, 3), (5, 4), (1, 4, 2, 8), (7,), (1024,), (2, 2, 2, 2, 2, 2, 2, 2),
+                                  (12, 6, 4, 2), (10, 6, 2)])
+def test_permutation_bit_exact(ctx, dims):
+    V = int(np.prod(dims))
+    loc = torch.empty(V, dtype=torch.int32, device="cuda:0")
+    ctx.permutation(dims, loc)
+    assert np.array_equal(loc.cpu().numpy(), np.array(P.hierarchical_loc(dims)))
+
+
+@pytest.mark.parametrize("dims", [(32, 32, 32, 64), (24, 24, 24, 48), (16, 16, 16, 32), (12, 12, 12, 12)])
+def test_permutation_full_size_sampled(ctx, dims):
+    V = int(np.prod(dims))
+    loc = torch.empty(V, dtype=torch.int32, device="cuda:0")
+    ctx.permutation(dims, loc)
+    l = loc.cpu().numpy()
+    assert np.array_equal(np.sort(l), np.arange(V))           # bijection at full size
+    rng = np.random.default_rng(1)
+    sites = rng.integers(0, V, 400)
+    assert np.array_equal(l[sites], np.array(P.hierarchical_loc(dims, sites)))
+
+
+@pytest.mark.parametrize("dims,seed", [((4, 4), 0), ((2, 4, 8), 5), ((4, 4, 4, 4), 2003), ((6, 6, 6, 6), 9),
+                                       ((3, 3, 3, 3), 1), ((12, 6), 0), ((5, 4), 3), ((6, 2, 6, 2), 4)])
+def test_probe_phases_bit_exact(ctx, hp, dims, seed):
+    V = int(np.prod(dims))
+    nvec = hp.basis_info(dims)["n_vectors"]
+    for first, count in [(0, min(nvec, 64)), (max(0, nvec - 7), min(7, nvec))]:
+        out = torch.empty(count * V, dtype=torch.int16, device="cuda:0")
+        per = ctx.probe_vectors(dims, first, count, seed, out)
+        ref, Pref = Pr.probe_phases(dims, first, count, seed)
+        got = out.cpu().numpy().astype(np.int64).reshape(count, V) & 0xFFFF
+        assert per == Pref
+        assert np.array_equal(got, ref)
+
+
+def test_probe_phases_full_size_sampled(ctx):
+    dims = (32, 32, 32, 64)
+    V = int(np.prod(dims))
+    for first in (0, 255, 1 << 20):
+        out = torch.empty(V, dtype=torch.int16, device="cuda:0")
+        ctx.probe_vectors(dims, first, 1, 2003, out)
+        got = out.cpu().numpy().astype(np.int64) & 0xFFFF
+        basis = Pr.LatticeBasis(dims)
+        col = basis.column(first)
+        sites = np.random.default_rng(first).integers(0, V, 300)
+        locs = np.array(P.hierarchical_loc(dims, sites))
+        z0 = np.array([1 - 2 * (Pr.splitmix64_output(2003, int(s)) >> 63) for s in sites])
+        ref = (col[locs] + np.where(z0 < 0, 1, 0)) % 2
+        assert np.array_equal(got[sites], ref)
+
+
+def test_probe_errors(ctx, hp):
+    out = torch.empty(64, dtype=torch.int16, device="cuda:0")
+    with pytest.raises(hp.HProbeError) as e:
+        ctx.probe_vectors((5, 4), 0, 5, 0, out)        # only 4 nested vectors exist
+    assert e.value.status == hp.HP_EUNSUPPORTED
+    with pytest.raises(hp.HProbeError) as e:
+        ctx.probe_vectors((4, 4), 10, 7, 0, out)
+    assert e.value.status == hp.HP_EINVAL
+
+
+# ------------------------------------------------------------------ stencils
+WILSON_TOL = {"fp64": 1e-13, "fp32": 3e-6, "fp16": 4e-3, "bf16": 3e-2}
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (3, 5, 4, 6), (2, 2, 2, 2), (8, 4, 6, 2), (1, 4, 1, 3)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+def test_wilson_apply_parity(ctx, hp, dims, prec):
+    U = synth.gauge_links(dims, 0.4, 7)
+    mf = synth.mass_field(dims, 0.01, 8)
+    nrhs = 3
+    psi = synth.random_spinors(dims, nrhs, 9)
+    op = ctx.make_operator(hp.OP_WILSON, 0.03, 0.12, links_dev(U), dev(mf))
+    out = torch.empty(psi.size * 2, dtype=torch.float64, device="cuda:0")
+    ctx.operator_apply(op, dims, nrhs, prec, dev(psi.view(np.float64).reshape(-1)), out)
+    got = out.cpu().numpy().view(np.complex128).reshape(psi.shape)
+    for r in range(nrhs):
+        ref = O.wilson_apply(psi[r], U, dims, 0.12, 0.03, mf)
+        err = np.linalg.norm(got[r] - ref) / np.linalg.norm(ref)
+        assert err <= WILSON_TOL[prec], err
+
+
+def test_wilson_apply_full_size_sampled(ctx, hp):
+    dims = (32, 32, 32, 64)
+    V = int(np.prod(dims))
+    U = synth.gauge_links(dims, 0.4, 1003)
+    psi = synth.random_spinors(dims, 1, 5)[0]
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.12, links_dev(U), None)
+    out = torch.empty(V * 24, dtype=torch.float64, device="cuda:0")
+    for prec in ("fp64", "fp32"):
+        ctx.operator_apply(op, dims, 1, prec, dev(psi.view(np.float64).reshape(-1)), out)
+        got = out.cpu().numpy().view(np.complex128).reshape(V, 4, 3)
+        ref = O.wilson_apply(psi, U, dims, 0.12)
+        sites = np.random.default_rng(0).integers(0, V, 2000)
+        err = np.linalg.norm(got[sites] - ref[sites]) / np.linalg.norm(ref[sites])
+        assert err <= WILSON_TOL[prec]
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (3, 5, 4, 6), (8, 8, 8, 8), (16, 1, 1, 1)])
+def test_laplacian_apply_parity(ctx, hp, dims):
+    x = synth.random_real_fields(dims, 2, 3)
+    mf = synth.mass_field(dims, 0.1, 4)
+    op = ctx.make_operator(hp.OP_LAPLACIAN, 0.05, 0.0, None, dev(mf))
+    out = torch.empty(x.size, dtype=torch.float64, device="cuda:0")
+    ctx.operator_apply(op, dims, 2, "fp64", dev(x.reshape(-1)), out)
+    got = out.cpu().numpy().reshape(x.shape)
+    pad = list(dims) + [1] * (4 - len(dims))
+    for r in range(2):
+        ref = O.laplacian_apply(x[r], pad, 0.05, mf)
+        assert np.allclose(got[r], ref, rtol=1e-14, atol=1e-13)
+
+
+# ------------------------------------------------------------------ trace estimates
+def rel(a, b):
+    return np.abs(a - b) / np.abs(b)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_laplacian_trace_config_8x8x8x8(ctx, hp, seed):
+    """8^4 Laplacian, m = 0.05, s = 1..256, CG to 1e-12."""
+    dims = (8, 8, 8, 8)
+    op = ctx.make_operator(hp.OP_LAPLACIAN, 0.05)
+    T, _, st = ctx.trace_inv(op, dims, 256, 1e-12, ctx.make_opts("fp64", z0_seed=seed))
+    q_ref = E.laplacian_quadratures(dims, 0.05, 0, 256, seed, method="dense")
+    T_ref = E.trace_prefix(q_ref)
+    assert np.all(rel(T, T_ref) <= TRACE_RTOL)
+    assert st["max_true_residual"] <= 1e-12
+    if seed == 0:   # h_0 = 1 is an eigenvector: CG converges in one step, T_1 = V / m
+        assert abs(T[0] - 4096 / 0.05) <= 1e-9 * 4096 / 0.05
+
+
+def test_laplacian_full_sequence_is_exact(ctx, hp):
+    from pins import laplacian_trace_inverse
+
+    dims = (4, 4, 4, 8)
+    op = ctx.make_operator(hp.OP_LAPLACIAN, 0.1)
+    T, _, _ = ctx.trace_inv(op, dims, 512, 1e-13, ctx.make_opts("fp64", z0_seed=3))
+    assert abs(T[-1].real - laplacian_trace_inverse(dims, 0.1)) <= 1e-10 * laplacian_trace_inverse(dims, 0.1)
+
+
+def test_laplacian_complex_probes(ctx, hp):
+    dims = (6, 6, 2, 3)
+    V = 216
+    op = ctx.make_operator(hp.OP_LAPLACIAN, 0.2)
+    T, _, _ = ctx.trace_inv(op, dims, V, 1e-13, ctx.make_opts("fp64", z0_seed=5))
+    T_ref = E.trace_prefix(E.laplacian_quadratures(dims, 0.2, 0, V, 5, method="dense"))
+    assert np.all(np.abs(T - T_ref) <= 1e-9 * np.abs(T_ref).max())
+    from pins import laplacian_trace_inverse
+    assert abs(T[-1].real - laplacian_trace_inverse(dims, 0.2)) <= 1e-9 * laplacian_trace_inverse(dims, 0.2)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+def test_wilson_trace_parity(ctx, hp, prec):
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_links(dims, 0.3, 1002)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.115, links_dev(U), None)
+    s = 6
+    T, _, st = ctx.trace_inv(op, dims, s, 1e-10, ctx.make_opts(prec, z0_seed=2002, rhs_block=24))
+    T_ref = E.trace_prefix(E.wilson_quadratures(dims, U, 0.115, 0, s, 2002, method="dense"))
+    assert np.all(rel(T, T_ref) <= TRACE_RTOL), (T, T_ref)
+    assert st["max_true_residual"] <= 1e-10
+    assert st["rhs_solved"] == 12 * s
+
+
+def test_wilson_full_sequence_exact_and_gauge_invariant(ctx, hp):
+    from pins import free_wilson_trace_inverse
+
+    dims = (4, 4, 2, 4)
+    V = 128
+    Ufree = np.broadcast_to(np.eye(3, dtype=complex), (V, 4, 3, 3)).copy()
+    Ug, _ = synth.gauge_transform(Ufree, dims, 77)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.12, links_dev(Ug), None)
+    T, _, _ = ctx.trace_inv(op, dims, V, 1e-11, ctx.make_opts("fp32", z0_seed=5))
+    exact = free_wilson_trace_inverse(dims, 0.12)
+    assert abs(T[-1].real - exact) <= 1e-9 * exact
+    assert np.max(np.abs(T.imag)) <= 1e-8 * np.max(np.abs(T.real))
+
+
+def test_wilson_config2_16x16x16x16_properties(ctx, hp):
+    """16^4, kappa 0.115, eps 0.3, BiCGStab 1e-10: FP64 and mixed agree, Im T = 0."""
+    dims = (16, 16, 16, 16)
+    U = synth.gauge_links(dims, 0.3, 1002)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.115, links_dev(U), None)
+    T64, _, s64 = ctx.trace_inv(op, dims, 2, 1e-10, ctx.make_opts("fp64", z0_seed=2002))
+    T32, _, s32 = ctx.trace_inv(op, dims, 2, 1e-10, ctx.make_opts("fp32", z0_seed=2002))
+    T16, _, _ = ctx.trace_inv(op, dims, 2, 1e-10, ctx.make_opts("fp16", z0_seed=2002))
+    assert np.all(rel(T32, T64) <= TRACE_RTOL) and np.all(rel(T16, T64) <= TRACE_RTOL)
+    assert np.max(np.abs(T64.imag)) <= 1e-9 * np.max(np.abs(T64.real))
+    assert s64["max_true_residual"] <= 1e-10 and s32["max_true_residual"] <= 1e-10
+
+
+def test_resume_gives_identical_prefix(ctx, hp):
+    """Checkpoint/resume: q of an earlier run plus first = 2 reproduces one long run bit for bit."""
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_links(dims, 0.3, 3)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.11, links_dev(U), None)
+    q_full = np.zeros(5, dtype=np.complex128)
+    T_full, _, _ = ctx.trace_inv(op, dims, 5, 1e-10, ctx.make_opts("fp64", z0_seed=9, rhs_block=12), q_inout=q_full)
+    q_part = np.zeros(2, dtype=np.complex128)
+    ctx.trace_inv(op, dims, 2, 1e-10, ctx.make_opts("fp64", z0_seed=9, rhs_block=12), q_inout=q_part)
+    q2 = np.zeros(5, dtype=np.complex128)
+    q2[:2] = q_part
+    T_res, _, _ = ctx.trace_inv(op, dims, 5, 1e-10, ctx.make_opts("fp64", z0_seed=9, first=2, rhs_block=12),
+                                q_inout=q2)
+    assert np.array_equal(q2, q_full) and np.array_equal(T_res, T_full)
+
+
+def test_nonconvergence_and_argument_errors(ctx, hp):
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_links(dims, 0.3, 3)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.12, links_dev(U), None)
+    with pytest.raises(hp.HProbeError) as e:
+        ctx.trace_inv(op, dims, 1, 1e-10, ctx.make_opts("fp64", maxiter=2))
+    assert e.value.status == hp.HP_ENOCONV
+    for bad in [dict(s_max=0), dict(tol=-1.0), dict(s_max=257)]:
+        kw = dict(s_max=2, tol=1e-10)
+        kw.update(bad)
+        with pytest.raises(hp.HProbeError) as e:
+            ctx.trace_inv(op, dims, kw["s_max"], kw["tol"], ctx.make_opts("fp64"))
+        assert e.value.status == hp.HP_EINVAL
+    op5 = ctx.make_operator(hp.OP_LAPLACIAN, 0.1)
+    with pytest.raises(hp.HProbeError) as e:
+        ctx.trace_inv(op5, (5, 4), 5, 1e-10, ctx.make_opts("fp64"))
+    assert e.value.status == hp.HP_EUNSUPPORTED
+
+
+# ------------------------------------------------------------------ gradient
+def test_laplacian_gradient(ctx, hp):
+    from pins import laplacian_eigenvalues
+
+    dims = (4, 4, 2, 2)
+    V = 64
+    op = ctx.make_operator(hp.OP_LAPLACIAN, 0.3)
+    g = np.zeros(V)
+    T, dTdm, _ = ctx.trace_inv_grad(op, dims, V, 1e-13, ctx.make_opts("fp64", z0_seed=2), g)
+    lam = laplacian_eigenvalues(dims, 0.3)
+    assert abs(dTdm + np.sum(1.0 / lam ** 2)) <= 1e-9 * np.sum(1.0 / lam ** 2)
+    g_ref = E.laplacian_grad_mass_field(dims, 0.3, 5, 2, method="dense").real
+    g5 = np.zeros(V)
+    ctx.trace_inv_grad(op, dims, 5, 1e-13, ctx.make_opts("fp64", z0_seed=2), g5)
+    assert np.allclose(g5, g_ref, rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_wilson_gradient_vs_oracle(ctx, hp, prec):
+    dims = (4, 4, 2, 4)
+    U = synth.gauge_links(dims, 0.3, 21)
+    mf = synth.mass_field(dims, 0.01, 5000)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.118, links_dev(U), dev(mf))
+    V = 128
+    g = torch.zeros(V, dtype=torch.float64, device="cuda:0")
+    T, dTdm, _ = ctx.trace_inv_grad(op, dims, 3, 1e-12, ctx.make_opts(prec, z0_seed=7), g)
+    g_ref = E.wilson_grad_mass_field(dims, U, 0.118, 3, 7, mass_field=mf, method="dense").real
+    assert np.allclose(g.cpu().numpy(), g_ref, rtol=1e-7, atol=1e-9)
+    assert abs(dTdm - g_ref.sum()) <= 1e-7 * abs(g_ref.sum())
+
+
+def test_autograd_function_and_finite_differences(ctx, hp):
+    from paper_1302_4018_gb300.autograd import trace_inv_estimate
+
+    dims = (4, 4, 4, 4)
+    V = 256
+    U = synth.gauge_links(dims, 0.3, 5)
+    mf = torch.tensor(synth.mass_field(dims, 0.01, 5000), device="cuda:0", requires_grad=True)
+    opts = ctx.make_opts("fp64", z0_seed=3)
+    links = links_dev(U)
+    T = trace_inv_estimate(mf, ctx, dims, 2, 1e-13, opts, kind=hp.OP_WILSON, kappa=0.118, links=links)
+    T.backward()
+    grad = mf.grad.cpu().numpy()
+    h = 1e-4
+    base = mf.detach().clone()
+    for site in (0, 77, 255):
+        e = torch.zeros(V, dtype=torch.float64, device="cuda:0")
+        e[site] = h
+        tp = trace_inv_estimate(base + e, ctx, dims, 2, 1e-13, opts, kind=hp.OP_WILSON, kappa=0.118, links=links)
+        tm = trace_inv_estimate(base - e, ctx, dims, 2, 1e-13, opts, kind=hp.OP_WILSON, kappa=0.118, links=links)
+        fd = (tp - tm).item() / (2 * h)
+        assert abs(fd - grad[site]) <= 1e-4 * max(1.0, abs(grad[site])), (site, fd, grad[site])
+    # uniform direction: dT/dm = sum_x dT/dmu(x)
+    one = torch.ones(V, dtype=torch.float64, device="cuda:0") * h
+    tp = trace_inv_estimate(base + one, ctx, dims, 2, 1e-13, opts, kind=hp.OP_WILSON, kappa=0.118, links=links)
+    tm = trace_inv_estimate(base - one, ctx, dims, 2, 1e-13, opts, kind=hp.OP_WILSON, kappa=0.118, links=links)
+    assert abs((tp - tm).item() / (2 * h) - grad.sum()) <= 1e-5 * abs(grad.sum())
+
+
+# ------------------------------------------------------------------ batching
+def test_batch_matches_single_lattice_oracle(ctx, hp):
+    cases = [((4, 4, 4, 4), 0.11, 0.2, 6), ((2, 2, 2, 4), 0.12, 0.4, 8), ((6, 2, 2, 2), 0.10, 0.3, 5)]
+    ops, dims_list, smax, refs, keep = [], [], [], [], []
+    for i, (dims, kappa, eps, s) in enumerate(cases):
+        U = synth.gauge_links(dims, eps, 1100 + i)
+        L = links_dev(U)
+        keep.append(L)
+        ops.append(ctx.make_operator(hp.OP_WILSON, 0.0, kappa, L, None))
+        dims_list.append(dims)
+        smax.append(s)
+        refs.append(E.trace_prefix(E.wilson_quadratures(dims, U, kappa, 0, s, 31, method="dense")))
+    for prec in ("fp64", "fp16"):
+        outs, st = ctx.trace_inv_batch(ops, dims_list, smax, 1e-10, ctx.make_opts(prec, z0_seed=31, rhs_block=16,
+                                                                                    use_graph=1))
+        for T, T_ref in zip(outs, refs):
+            assert np.all(rel(T, T_ref) <= TRACE_RTOL)
+        assert st["rhs_solved"] == 12 * sum(smax)
