@@ -1,0 +1,416 @@
+"""Throughput of hierarchical probing on the 32^3x64 Wilson-Dirac workload.
+
+One step = one pass of the whole path over one block of probing vectors:
+probe generation on the device, full spin-colour dilution (12 sources per
+probe), mixed-precision BiCGStab with FP64 reliable updates to a true
+relative residual 1e-10, the FP64 quadratures q_m = sum_a v^H x and the
+incremental prefix T_s (the next block resumes the nested sequence where the
+previous one stopped).  Metric: probing solves/s (one solve = one diluted
+right-hand side converged), whole job over all ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU: ranks take disjoint probe blocks (weak scaling, no collective on
+the data path); the timing is the max over ranks.  ``--impl reference`` times
+the CPU oracle (plain numpy BiCGStab) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (32, 32, 32, 64)
+KAPPA, EPS, LINK_SEED, Z0_SEED, TOL = 0.12, 0.4, 1003, 2003, 1e-10
+METRIC = "probing solves/s (32^3x64 Wilson, mixed precision, true residual 1e-10)"
+UNIT = "solves/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+HBM_FALLBACK = 6800.0
+# mean BiCGStab iterations per solve of this workload in FP64 (measured on the GPU)
+FP64_ITERS_PER_SOLVE = None
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in ("hp_fields.cuh", "hp_wilson.cu", "hp_internal.h"):
+        with open(os.path.join(ROOT, "paper_1302_4018_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+# DRAM traffic per launch from one ncu capture, valid only for the source it was taken on
+NCU_TRAFFIC = {}
+
+
+class Clocks:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        backend = "nccl"
+        try:
+            import torch
+
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(ws, value, device):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ algorithmic bytes
+def spinor_link_bytes(prec):
+    return {"fp64": (192, 144, 192), "fp32": (96, 48, 96), "fp16": (52, 24, 96), "bf16": (52, 24, 96)}[prec]
+
+
+def kernel_bytes(name, prec, V, rhs_iters, launches, updates):
+    """Algorithmic DRAM bytes of one solver kernel over the run (each vector read/written once,
+    links once per launch): rhs_iters = right-hand-side iterations, updates = FP64 reliable updates."""
+    S, L, E = spinor_link_bytes(prec)
+    if name.startswith("k_bicg_v"):
+        return V * (3 * S * rhs_iters + 4 * L * launches)
+    if name.startswith("k_bicg_t"):
+        return V * (2 * S * rhs_iters + 4 * L * launches)
+    if name == "k_bicg_s":
+        return V * 3 * S * rhs_iters
+    if name == "k_bicg_xr":
+        return V * (5 * S + 2 * E) * rhs_iters
+    if name == "k_bicg_p":
+        return V * 4 * S * rhs_iters
+    if name == "k_ru_accum":
+        return V * (2 * 192 + 2 * E) * updates
+    if name.startswith("k_ru_residual"):
+        return V * ((192 + 2 * S) * updates + 4 * 144 * launches)
+    return None
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+
+    from paper_1302_4018_gb300 import hprobe, synth
+
+    ws, rank, local = dist_setup()
+    device = "cuda:%d" % local
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    ctx = hprobe.Context(local, stream=stream.cuda_stream)
+    U = synth.gauge_links(DIMS, EPS, LINK_SEED, device=device)
+    V = U.shape[0]
+    links_dev = torch.from_numpy(U.view(np.float64).reshape(-1)).to(device)
+    links_host = torch.from_numpy(U.view(np.float64).reshape(-1)).pin_memory()
+    del U
+    prec = args.precision
+    P = args.probes_per_step
+    total_steps = args.warmup + args.steps
+    base = rank * (total_steps + 4) * P       # disjoint probe range per rank
+    q = np.zeros(base + (total_steps + 4) * P + 16, dtype=np.complex128)
+
+    def step(first, links, precision=prec, probes=P, rhs_block=args.rhs_block):
+        op = ctx.make_operator(hprobe.OP_WILSON, 0.0, KAPPA, links, None)
+        s_max = first + probes
+        opts = ctx.make_opts(precision, z0_seed=Z0_SEED, first=first, rhs_block=rhs_block)
+        qq = q[:s_max].copy()
+        T, qq, st = ctx.trace_inv(op, DIMS, s_max, TOL, opts, q_inout=qq)
+        q[:s_max] = qq
+        return st
+
+    first = base
+    # rank r owns probes [base, ...): its prefix below `base` is left at q = 0 here (the ranks'
+    # quadrature blocks are disjoint and concatenate into the nested sequence)
+    for _ in range(args.warmup):
+        step(first, links_dev)
+        first += P
+    ctx.profile_enable(True)
+    ctx.profile_report()
+    clocks = Clocks(local)
+    n0 = ctx.launch_count()
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(step(first, links_dev))
+        first += P
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(ws)
+    ms_dev = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - n0
+    prof = ctx.profile_report()
+    ctx.profile_enable(False)
+    ms_max = max_over_ranks(ws, ms_dev, device)
+    rhs = sum(s["rhs_solved"] for s in stats)
+    value = ws * rhs / (ms_max / 1e3)
+    iters = sum(s["iterations_total"] for s in stats)
+    updates = sum(s["reliable_updates"] for s in stats)
+    max_res = max(s["max_true_residual"] for s in stats)
+
+    # end to end through the C ABI with host buffers: links from pinned host memory, T back to host
+    e2e_steps = max(1, min(2, args.steps))
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_rhs = 0
+    h2d = d2h = 0
+    for _ in range(e2e_steps):
+        e2e_rhs += step(first, links_host)["rhs_solved"]
+        h2d += V * 72 * 8 + 16 * first          # links, earlier quadratures
+        d2h += 2 * 16 * (first + P)             # quadratures and prefix estimates
+        first += P
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(ws, time.perf_counter() - t0, device)
+    e2e = {"value": ws * e2e_rhs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d / e2e_steps),
+           "d2h_bytes_per_step": int(d2h / e2e_steps), "steps": e2e_steps}
+
+    # plain FP64 solver on the same GPU (one probe = 12 solves), for the mixed-vs-FP64 ratio
+    fp64 = None
+    if not args.no_fp64:
+        step(first, links_dev, precision="fp64", probes=1, rhs_block=12)   # warm-up (allocation)
+        first += 1
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st64 = step(first, links_dev, precision="fp64", probes=args.fp64_probes, rhs_block=12)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        first += args.fp64_probes
+        ms64 = max_over_ranks(ws, e0.elapsed_time(e1), device)
+        fp64 = {"solves_per_s": ws * st64["rhs_solved"] / (ms64 / 1e3), "rhs": st64["rhs_solved"],
+                "iters_per_solve": st64["iterations_total"] / max(1, st64["rhs_solved"]),
+                "max_true_residual": st64["max_true_residual"]}
+
+    # stencil alone (Dslash GB/s) in the iteration precision and in FP64
+    op = ctx.make_operator(hprobe.OP_WILSON, 0.0, KAPPA, links_dev, None)
+    ds = ctx.dslash_bench(op, DIMS, prec, args.rhs_block, 20)
+    ds64 = ctx.dslash_bench(op, DIMS, "fp64", 1, 5)
+    peak, peak_kind = hbm_peak()
+    dslash = {"precision": prec, "nrhs": args.rhs_block, "ms": ds["ms"], "GBps": ds["bytes"] / ds["ms"] / 1e6,
+              "frac_of_%s_hbm" % peak_kind: ds["bytes"] / ds["ms"] / 1e6 / peak,
+              "TFLOPs": ds["flops"] / ds["ms"] / 1e9,
+              "fp64": {"nrhs": 1, "ms": ds64["ms"], "GBps": ds64["bytes"] / ds64["ms"] / 1e6,
+                       "TFLOPs": ds64["flops"] / ds64["ms"] / 1e9}}
+
+    # roofline of the dominant kernel of the timed steps (event-timed launches, algorithmic bytes)
+    rhs_iters = iters
+    kernels = {}
+    for name, rec in prof.items():
+        b = kernel_bytes(name, prec, V, rhs_iters, rec["launches"], updates)
+        kernels[name] = {"launches": rec["launches"], "ms": rec["ms"],
+                         "GBps": (b / (rec["ms"] / 1e3) / 1e9) if b and rec["ms"] > 0 else None}
+    tot_ms = sum(r["ms"] for r in prof.values()) or 1.0
+    for k in kernels.values():
+        k["share"] = k["ms"] / tot_ms
+    top = max(kernels.items(), key=lambda kv: kv[1]["ms"])
+    top_name, top_rec = top
+    top_bytes = kernel_bytes(top_name, prec, V, rhs_iters, top_rec["launches"], updates)
+    achieved = top_bytes / (top_rec["ms"] / 1e3) / 1e9 if top_bytes else None
+    trace_ncu = NCU_TRAFFIC.get((top_name, source_hash()))
+    roofline = {"kernel": top_name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": (top_bytes / top_rec["launches"]) if top_bytes else None,
+                "mean_launch_ms": top_rec["ms"] / top_rec["launches"],
+                "traffic": trace_ncu}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline(fp64["iters_per_solve"] if fp64 else None)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math",
+                  "fp64": "f64"}[prec] + " + f64 reliable updates",
+        "data": "synthetic: SU(3) links exp(i eps H), seeded (no gauge ensemble available)",
+        "config": {"workload": "32^3x64 Wilson-Dirac, kappa 0.12, eps 0.4, %d probes x 12 dilutions per step, "
+                               "BiCGStab %s, tol 1e-10" % (P, prec),
+                   "lattice": list(DIMS), "probes_per_step": P, "rhs_per_step": 12 * P, "rhs_block": args.rhs_block,
+                   "precision": prec, "tol": TOL, "l2": "inputs larger than L2 (each field >= 100 MB)",
+                   "parallelism": "dp%d over probe blocks" % ws},
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "solver": {"rhs": rhs, "iters_per_solve": iters / max(1, rhs), "reliable_updates_per_solve": updates / max(1, rhs),
+                   "max_true_residual": max_res},
+        "fp64_solver": fp64,
+        "mixed_over_fp64": (value / ws / fp64["solves_per_s"] * ws) if fp64 else None,
+        "dslash": dslash,
+        "kernels": kernels,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_iteration_time(U, reps):
+    """Time per iteration of the oracle's BiCGStab (oracle.solvers.bicgstab, unchanged) on one
+    right-hand side, stopped after `reps` iterations by its own maxiter."""
+    from oracle import operators as O
+    from oracle import solvers as S
+
+    V = U.shape[0]
+    b = np.zeros((V, 4, 3), dtype=complex)
+    b[:, 0, 0] = 1.0             # a probing source h_0 (x) e_0; the cost per iteration does not depend on it
+    t0 = time.perf_counter()
+    try:
+        S.bicgstab(lambda v: O.wilson_apply(v, U, DIMS, KAPPA), b, tol=1e-10, maxiter=reps)
+    except RuntimeError:
+        pass
+    return (time.perf_counter() - t0) / reps
+
+
+def _links_device():
+    try:
+        import torch
+
+        return "cuda:0" if torch.cuda.is_available() else "cpu"
+    except ImportError:
+        return "cpu"
+
+
+def cpu_baseline(iters_per_solve, reps=2):
+    from paper_1302_4018_gb300 import synth
+
+    U = synth.gauge_links(DIMS, EPS, LINK_SEED, device=_links_device())
+    t_it = oracle_iteration_time(U, reps)
+    n_it = iters_per_solve or FP64_ITERS_PER_SOLVE or 100.0
+    return {"value": 1.0 / (t_it * n_it), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d oracle BiCGStab iterations (2 Wilson applications each, numpy FP64, one thread) on one "
+                      "right-hand side of the 32^3x64 workload: %.2f s per iteration, extrapolated to %.1f "
+                      "iterations per solve (the FP64 iteration count of this workload)" % (reps, t_it, n_it)}
+
+
+def run_reference(args):
+    ws, rank, local = dist_setup()
+    if rank != 0:
+        return
+    from paper_1302_4018_gb300 import synth
+
+    U = synth.gauge_links(DIMS, EPS, LINK_SEED, device=_links_device())
+    n_it = FP64_ITERS_PER_SOLVE or 100.0
+    for _ in range(args.warmup):
+        oracle_iteration_time(U, 1)
+    times = [oracle_iteration_time(U, 1) for _ in range(args.steps)]
+    t_it = sum(times) / len(times)
+    value = 1.0 / (t_it * n_it)
+    sample = ("each step: one oracle BiCGStab iteration (numpy FP64, one thread) on one right-hand side of the "
+              "32^3x64 workload; solves/s = 1 / (time per iteration x %.1f iterations per solve)" % n_it)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_it, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "32^3x64 Wilson-Dirac, kappa 0.12, eps 0.4, tol 1e-10", "lattice": list(DIMS)},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp16", choices=["fp64", "fp32", "fp16", "bf16"])
+    ap.add_argument("--probes-per-step", type=int, default=2)
+    ap.add_argument("--rhs-block", type=int, default=24)
+    ap.add_argument("--fp64-probes", type=int, default=1)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

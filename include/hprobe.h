@@ -43,7 +43,9 @@ typedef enum {
 typedef struct hp_ctx hp_ctx;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
- * to run on (NULL: the context creates its own non-blocking stream).
+ * to run on (NULL: the context creates its own blocking stream, which is
+ * ordered with the legacy default stream).  Device inputs must be ready in
+ * that stream order, and device outputs are ready in that order.
  * On success *out owns device workspace until hp_ctx_destroy. */
 hp_status hp_ctx_create(int device, void* cuda_stream, hp_ctx** out);
 void hp_ctx_destroy(hp_ctx* ctx);
@@ -226,6 +228,9 @@ hp_status hp_dslash_bench(hp_ctx* ctx, const hp_operator* op, const hp_lattice* 
  * object {"kernel": {"launches": n, "ms": t}, ...} into buf (host, size
  * bytes, NUL-terminated, truncated if short) and clears the records. */
 hp_status hp_profile_enable(hp_ctx* ctx, int32_t on);
+/* Number of kernels the context has launched since its creation (kernels
+ * replayed from captured graphs included), into *out (host). */
+hp_status hp_launch_count(hp_ctx* ctx, int64_t* out);
 hp_status hp_profile_report(hp_ctx* ctx, char* buf, int64_t size);
 
 #ifdef __cplusplus

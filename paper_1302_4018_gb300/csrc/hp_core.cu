@@ -49,7 +49,8 @@ extern "C" hp_status hp_ctx_create(int device, void* cuda_stream, hp_ctx** out) 
   if (cuda_stream) {
     c->stream = (cudaStream_t)cuda_stream;
   } else {
-    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    // a blocking stream: ordered with work on the legacy default stream of the caller
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamDefault);
     if (e != cudaSuccess) {
       delete c;
       hp_set_error("cudaStreamCreate: %s", cudaGetErrorString(e));
@@ -173,6 +174,15 @@ extern "C" hp_status hp_profile_enable(hp_ctx* ctx, int32_t on) {
     return HP_EINVAL;
   }
   ctx->profiling = on != 0;
+  return HP_OK;
+}
+
+extern "C" hp_status hp_launch_count(hp_ctx* ctx, int64_t* out) {
+  if (!ctx || !out) {
+    hp_set_error("hp_launch_count: NULL argument");
+    return HP_EINVAL;
+  }
+  *out = ctx->launches;
   return HP_OK;
 }
 

@@ -112,6 +112,7 @@ struct hp_ctx {
   std::vector<ProfRecord> prof;
   std::vector<cudaEvent_t> event_pool;
   std::map<std::string, int> autotune;       // key -> threads per block
+  long long launches = 0;                    // kernels launched (graph replays included)
 };
 
 // workspace
@@ -125,7 +126,10 @@ struct ProfScope {
   hp_ctx* ctx;
   const char* name;
   cudaEvent_t a = nullptr;
-  ProfScope(hp_ctx* c, const char* n) : ctx(c), name(n) { hp_prof_begin(ctx, name, &a); }
+  ProfScope(hp_ctx* c, const char* n) : ctx(c), name(n) {
+    ctx->launches += 1;
+    hp_prof_begin(ctx, name, &a);
+  }
   ~ProfScope() { hp_prof_end(ctx, name, a); }
 };
 

@@ -296,6 +296,7 @@ __global__ void k_lgrad(LArgs a, int lat, const int* __restrict__ slots, int nsl
 
 struct LaplaceEngine {
   static constexpr int NT = 256;
+  static constexpr int KERNELS_PER_ITERATION = 4;
   hp_ctx* ctx;
   LArgs a;
   int nslots, gy;

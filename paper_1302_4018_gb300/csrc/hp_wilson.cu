@@ -740,6 +740,7 @@ template <int SPR>
 struct WilsonEngine {
   static constexpr int EPR = SPR == PR64 ? PR64 : PR32;
   static constexpr int NT = 128;
+  static constexpr int KERNELS_PER_ITERATION = 7;
   hp_ctx* ctx;
   WArgs a;
   int nslots, gy;

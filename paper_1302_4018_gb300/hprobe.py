@@ -41,7 +41,8 @@ PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 EXPORTED = ["hp_ctx_create", "hp_ctx_destroy", "hp_last_error", "hp_ctx_synchronize", "hp_basis_info",
             "hp_phase_values",
             "hp_permutation", "hp_probe_vectors", "hp_trace_inv", "hp_trace_inv_grad", "hp_trace_inv_batch",
-            "hp_operator_apply", "hp_dslash_bench", "hp_profile_enable", "hp_profile_report"]
+            "hp_operator_apply", "hp_dslash_bench", "hp_profile_enable", "hp_profile_report",
+            "hp_launch_count"]
 
 
 class Lattice(C.Structure):
@@ -99,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hp_dslash_bench": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I32, I32, I32,
                                       C.POINTER(D), C.POINTER(D), C.POINTER(D)]),
         "hp_profile_enable": (C.c_int, [P, I32]),
+        "hp_launch_count": (C.c_int, [P, C.POINTER(I64)]),
         "hp_profile_report": (C.c_int, [P, C.c_char_p, I64]),
     }
     for name, (res, args) in sig.items():
@@ -157,9 +159,22 @@ def _ptr(x) -> Optional[int]:
 
 
 class Context:
-    """hp_ctx on one CUDA device, optionally on an existing cudaStream_t (int handle)."""
+    """hp_ctx on one CUDA device.
+
+    ``stream`` is a cudaStream_t handle (int); by default the context runs on
+    torch's current stream of that device, so its work is ordered with the
+    torch operations that produce its inputs and consume its outputs.
+    """
 
     def __init__(self, device: int = 0, stream: Optional[int] = None):
+        if stream is None:
+            try:
+                import torch
+
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream(device).cuda_stream
+            except ImportError:
+                pass
         h = C.c_void_p()
         _check(lib().hp_ctx_create(int(device), C.c_void_p(stream) if stream else None, C.byref(h)))
         self._h = h
@@ -272,6 +287,11 @@ class Context:
         return {"ms": ms.value, "bytes": by.value, "flops": fl.value}
 
     # ---------------------------------------------------------------- profiling
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        _check(lib().hp_launch_count(self._h, C.byref(n)))
+        return n.value
+
     def profile_enable(self, on: bool = True):
         _check(lib().hp_profile_enable(self._h, 1 if on else 0))
 

@@ -8,11 +8,14 @@ so the oracle can use it without touching the CUDA library.
 Gauge links (stand-in for the missing 32^3x64 ensemble of Section 5.3):
   U_mu(x) = exp(i eps H),  H = (G + G^H)/2 - tr(...)/3 I,
   G_ij = (a + i b)/sqrt(2),  a, b ~ N(0, 1) from numpy PCG64(seed), drawn in
-  the order (site, mu, i, j, re/im).  The exponential is a degree-24 Taylor
-  series (||eps H|| < 3 for every config used, so the series is converged
-  far below FP64 rounding), followed by re-unitarisation: Gram-Schmidt on
-  rows 1-2 and row 3 = conj(row1 x row2), which makes every link exactly
-  special-unitary up to rounding.  Layout complex128 [V, 4, 3, 3].
+  the order (site, mu, i, j, re/im).  The exponential is evaluated by
+  scaling and squaring: a degree-10 Taylor series of (i eps H)/8 (norm below
+  0.5 for every config used, truncation < 1e-13) squared three times,
+  followed by re-unitarisation: Gram-Schmidt on rows 1-2 and
+  row 3 = conj(row1 x row2), which makes every link special unitary to
+  rounding.  The matrix algebra runs in torch on the requested device (the
+  CPU by default); the random draws are always numpy PCG64 on the host.
+  Layout complex128 [V, 4, 3, 3].
 """
 from __future__ import annotations
 
@@ -29,44 +32,60 @@ def volume(dims: Sequence[int]) -> int:
     return v
 
 
-def _taylor_expm_i(H: np.ndarray, eps: float, degree: int = 24) -> np.ndarray:
+def _expm_i(H, eps: float, degree: int = 10, squarings: int = 3):
+    import torch
+
     n = H.shape[-1]
-    X = (1j * eps) * H
-    out = np.broadcast_to(np.eye(n, dtype=complex), H.shape).copy()
-    term = out.copy()
+    X = (1j * eps / (1 << squarings)) * H
+    eye = torch.eye(n, dtype=H.dtype, device=H.device)
+    out = eye.expand_as(H).clone()
+    term = out.clone()
     for k in range(1, degree + 1):
-        term = np.matmul(term, X) / k
+        term = torch.matmul(term, X) / k
         out += term
+    for _ in range(squarings):
+        out = torch.matmul(out, out)
     return out
 
 
-def reunitarize(U: np.ndarray) -> np.ndarray:
-    r1 = U[..., 0, :]
-    r1 = r1 / np.sqrt(np.sum(np.abs(r1) ** 2, axis=-1, keepdims=True))
-    r2 = U[..., 1, :]
-    r2 = r2 - np.sum(np.conj(r1) * r2, axis=-1, keepdims=True) * r1
-    r2 = r2 / np.sqrt(np.sum(np.abs(r2) ** 2, axis=-1, keepdims=True))
-    r3 = np.conj(np.cross(r1, r2))
-    return np.stack([r1, r2, r3], axis=-2)
+def reunitarize(U):
+    """Gram-Schmidt on rows 1-2, row 3 = conj(row1 x row2) (numpy or torch input)."""
+    import torch
+
+    T = torch.as_tensor(U)
+    r1 = T[..., 0, :]
+    r1 = r1 / torch.sqrt(torch.sum(torch.abs(r1) ** 2, dim=-1, keepdim=True))
+    r2 = T[..., 1, :]
+    r2 = r2 - torch.sum(torch.conj(r1) * r2, dim=-1, keepdim=True) * r1
+    r2 = r2 / torch.sqrt(torch.sum(torch.abs(r2) ** 2, dim=-1, keepdim=True))
+    r3 = torch.conj(torch.linalg.cross(r1, r2, dim=-1))
+    out = torch.stack([r1, r2, r3], dim=-2)
+    return out.numpy() if isinstance(U, np.ndarray) else out
 
 
-def gauge_links(dims: Sequence[int], eps: float, seed: int, chunk_sites: int = 1 << 18) -> np.ndarray:
-    """SU(3) links U = exp(i eps H) on every site and direction; complex128 [V, 4, 3, 3]."""
+def gauge_links(dims: Sequence[int], eps: float, seed: int, device: str = "cpu",
+                chunk_sites: int = 1 << 18) -> np.ndarray:
+    """SU(3) links U = exp(i eps H) on every site and direction; complex128 numpy [V, 4, 3, 3]."""
+    import torch
+
     V = volume(dims)
     rng = np.random.Generator(np.random.PCG64(seed))
     out = np.empty((V, 4, 3, 3), dtype=complex)
+    eye = None
     for s0 in range(0, V, chunk_sites):
         n = min(chunk_sites, V - s0)
-        ab = rng.standard_normal((n, 4, 3, 3, 2))
-        G = (ab[..., 0] + 1j * ab[..., 1]) / math.sqrt(2.0)
-        H = 0.5 * (G + np.conj(np.swapaxes(G, -1, -2)))
-        tr = np.trace(H, axis1=-2, axis2=-1).real
-        H = H - (tr / 3.0)[..., None, None] * np.eye(3)
+        ab = torch.from_numpy(rng.standard_normal((n, 4, 3, 3, 2))).to(device)
+        G = torch.complex(ab[..., 0], ab[..., 1]) / math.sqrt(2.0)
+        H = 0.5 * (G + torch.conj(G.transpose(-1, -2)))
+        if eye is None:
+            eye = torch.eye(3, dtype=H.dtype, device=H.device)
+        tr = torch.diagonal(H, dim1=-2, dim2=-1).sum(-1).real
+        H = H - (tr / 3.0)[..., None, None] * eye
         if eps == 0.0:
-            U = np.broadcast_to(np.eye(3, dtype=complex), (n, 4, 3, 3)).copy()
+            U = eye.expand(n, 4, 3, 3)
         else:
-            U = reunitarize(_taylor_expm_i(H, eps))
-        out[s0:s0 + n] = U
+            U = reunitarize(_expm_i(H, eps))
+        out[s0:s0 + n] = U.cpu().numpy()
     return out
 
 

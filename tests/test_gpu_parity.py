@@ -134,7 +134,7 @@ def test_wilson_apply_parity(ctx, hp, dims, prec):
 def test_wilson_apply_full_size_sampled(ctx, hp):
     dims = (32, 32, 32, 64)
     V = int(np.prod(dims))
-    U = synth.gauge_links(dims, 0.4, 1003)
+    U = synth.gauge_links(dims, 0.4, 1003, device="cuda:0")
     psi = synth.random_spinors(dims, 1, 5)[0]
     op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.12, links_dev(U), None)
     out = torch.empty(V * 24, dtype=torch.float64, device="cuda:0")
@@ -230,7 +230,7 @@ def test_wilson_full_sequence_exact_and_gauge_invariant(ctx, hp):
 def test_wilson_config2_16x16x16x16_properties(ctx, hp):
     """16^4, kappa 0.115, eps 0.3, BiCGStab 1e-10: FP64 and mixed agree, Im T = 0."""
     dims = (16, 16, 16, 16)
-    U = synth.gauge_links(dims, 0.3, 1002)
+    U = synth.gauge_links(dims, 0.3, 1002, device="cuda:0")
     op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.115, links_dev(U), None)
     T64, _, s64 = ctx.trace_inv(op, dims, 2, 1e-10, ctx.make_opts("fp64", z0_seed=2002))
     T32, _, s32 = ctx.trace_inv(op, dims, 2, 1e-10, ctx.make_opts("fp32", z0_seed=2002))
