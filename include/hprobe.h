@@ -146,8 +146,9 @@ typedef struct {
     double delta;           /* reliable-update threshold on ||r||/max||r|| (0: per precision) */
     int32_t check_every;    /* iterations between host scheduling steps (0: automatic)   */
     int32_t use_graph;      /* 1: replay the iteration chunk from a captured CUDA graph  */
-    int32_t block_threads;  /* threads per block of the stencil kernels (0: autotune)     */
-    int32_t reserved[5];
+    int32_t block_threads;  /* reserved for the stencil block size (0)                    */
+    int32_t rhs_per_thread; /* right-hand sides per thread in the stencil: 1, 2, 4 (0: autotune) */
+    int32_t reserved[4];
 } hp_solver_opts;
 
 typedef struct {
@@ -161,7 +162,7 @@ typedef struct {
     double max_true_residual;     /* max ||b - A x|| / ||b|| in FP64 at convergence    */
     double seconds;               /* wall time of the call                             */
     int32_t n_unconverged;
-    int32_t reserved;
+    int32_t group_updates;        /* FP32 group updates of x and r between FP64 ones   */
 } hp_solve_stats;
 
 /* The incremental trace estimate (Section 1: (1/s) sum_k z_k^H A^-1 z_k;

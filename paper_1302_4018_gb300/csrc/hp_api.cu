@@ -136,7 +136,7 @@ static hp_status check_solver_args(int64_t s_max, double tol, const hp_solver_op
 static int need_mask(int prec) {
   int m = 1 << PR64;
   if (prec == HP_PREC_MIXED_FP32) m |= 1 << PR32;
-  if (prec == HP_PREC_MIXED_FP16 || prec == HP_PREC_MIXED_BF16) m |= 1 << PR16;
+  if (prec == HP_PREC_MIXED_FP16 || prec == HP_PREC_MIXED_BF16) m |= (1 << PR16) | (1 << PR32);
   return m;
 }
 

@@ -76,10 +76,11 @@ enum { SLOT_EMPTY = 0, SLOT_INIT = 1, SLOT_RUN = 2, SLOT_DONE = 3, SLOT_FAIL = 4
 struct SlotState {
   double2 alpha, beta, omega, rho;   // BiCGStab scalars (CG uses .x)
   double bnorm2, rnorm2, rmax2, true_res2;
+  double rexact2, pad_d;             // ||r||^2 at the last FP64 true residual
   double2 q;                         // quadrature v^H x at harvest
-  int status, need_update, restart, iters;
+  int status, need_update, restart, iters;   // need_update: 1 group (FP32) update, 2 FP64 true residual
   int updates, lat, a, m;            // lattice index, dilution index / part, probe index
-  int sloppy_mv, fp64_mv, pad0, pad1;
+  int sloppy_mv, fp64_mv, gupdates, pad1;
 };
 
 // ------------------------------------------------------------- the context

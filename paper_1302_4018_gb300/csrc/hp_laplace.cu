@@ -297,12 +297,14 @@ __global__ void k_lgrad(LArgs a, int lat, const int* __restrict__ slots, int nsl
 struct LaplaceEngine {
   static constexpr int NT = 256;
   static constexpr int KERNELS_PER_ITERATION = 4;
+  static constexpr int GROUP_MAX = 1;
   hp_ctx* ctx;
   LArgs a;
   int nslots, gy;
   dim3 grid() const { return dim3(nslots, gy); }
+  int group() const { return 1; }
   hp_status setup(int ns, int Vmax, const LatGeom* lats_dev, SlotState* st, const hp_solver_opts& o, double tol,
-                  double) {
+                  double, const LatGeom&) {
     nslots = ns;
     memset(&a, 0, sizeof(a));
     a.lats = lats_dev;

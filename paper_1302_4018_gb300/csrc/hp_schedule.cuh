@@ -38,6 +38,10 @@ hp_status run_schedule(hp_ctx* ctx, Engine& eng, SolveProblem& pb, SolveResult& 
     nslots = (int)std::max(12LL, std::min(want, 256LL));
   }
   nslots = (int)std::min<long long>(nslots, std::max<size_t>(1, queue.size()));
+  nslots = (nslots + Engine::GROUP_MAX - 1) / Engine::GROUP_MAX * Engine::GROUP_MAX;
+  int big = 0;
+  for (int L = 1; L < nl; ++L)
+    if (pb.lats[L].V > pb.lats[big].V) big = L;
 
   void* p = nullptr;
   HP_TRY(hp_ws(ctx, "solve.lats", sizeof(LatGeom) * nl, &p));
@@ -49,7 +53,8 @@ hp_status run_schedule(hp_ctx* ctx, Engine& eng, SolveProblem& pb, SolveResult& 
   int* dev_slots = (int*)p;
   std::vector<SlotState> host(nslots);
   memset(host.data(), 0, sizeof(SlotState) * nslots);
-  HP_TRY(eng.setup(nslots, Vmax, lats_dev, st_dev, pb.opts, pb.tol, delta));
+  HP_TRY(eng.setup(nslots, Vmax, lats_dev, st_dev, pb.opts, pb.tol, delta, pb.lats[big]));
+  const int G = eng.group();   // slots refilled together (one lattice per group: the stencil shares links)
 
   const int chunk = pb.opts.check_every > 0 ? pb.opts.check_every : 8;
   const bool use_graph = pb.opts.use_graph && !ctx->profiling;
@@ -79,18 +84,24 @@ hp_status run_schedule(hp_ctx* ctx, Engine& eng, SolveProblem& pb, SolveResult& 
   hp_status status = HP_OK;
   while (true) {
     bool any_init = false, any_run = false;
-    for (int sl = 0; sl < nslots; ++sl) {
-      if (host[sl].status == SLOT_EMPTY && qpos < queue.size()) {
+    for (int g0 = 0; g0 < nslots; g0 += G) {
+      bool empty = true;
+      for (int r = 0; r < G; ++r) empty = empty && host[g0 + r].status == SLOT_EMPTY;
+      if (!empty || qpos >= queue.size()) continue;
+      const int L = queue[qpos].lat;
+      for (int r = 0; r < G && qpos < queue.size() && queue[qpos].lat == L; ++r) {
         const Item& it = queue[qpos++];
-        memset(&host[sl], 0, sizeof(SlotState));
-        host[sl].status = SLOT_INIT;
-        host[sl].lat = it.lat;
-        host[sl].m = it.m;
-        host[sl].a = it.a;
+        SlotState& S = host[g0 + r];
+        memset(&S, 0, sizeof(SlotState));
+        S.status = SLOT_INIT;
+        S.lat = it.lat;
+        S.m = it.m;
+        S.a = it.a;
         any_init = true;
       }
-      if (host[sl].status == SLOT_RUN) any_run = true;
     }
+    for (int sl = 0; sl < nslots; ++sl)
+      if (host[sl].status == SLOT_RUN) any_run = true;
     HP_CUDA(cudaMemcpyAsync(st_dev, host.data(), sizeof(SlotState) * nslots, cudaMemcpyHostToDevice, ctx->stream));
     if (any_init) HP_TRY(eng.init());
     if (!any_init && !any_run) break;
@@ -121,6 +132,7 @@ hp_status run_schedule(hp_ctx* ctx, Engine& eng, SolveProblem& pb, SolveResult& 
         res.stats.reliable_updates += S.updates;
         res.stats.sloppy_matvecs += S.sloppy_mv;
         res.stats.fp64_matvecs += S.fp64_mv;
+        res.stats.group_updates += S.gupdates;
         double rel = S.bnorm2 > 0 ? std::sqrt(S.true_res2 / S.bnorm2) : 0.0;
         res.stats.max_true_residual = std::max(res.stats.max_true_residual, rel);
         if (S.status == SLOT_FAIL) {

@@ -87,54 +87,6 @@ hp_status hp_prepare_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom* g, cons
   return HP_OK;
 }
 
-// ================================================================ plain apply
-template <int SPR>
-__global__ void k_w_from_canonical(const double2* __restrict__ in, FieldPtr f, int V, int nrhs) {
-  const long long total = (long long)nrhs * V;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    int slot = (int)(t / V), site = (int)(t - (long long)slot * V);
-    typedef typename Real_of<SPR>::T R;
-    cplx<R> s[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      double2 v = in[((size_t)slot * V + site) * 12 + k];
-      s[k] = {(R)v.x, (R)v.y};
-    }
-    SpinorIO<SPR>::store(f, V, slot, site, s);
-  }
-}
-
-template <int SPR>
-__global__ void k_w_to_canonical(FieldPtr f, int V, int nrhs, double2* __restrict__ out) {
-  const long long total = (long long)nrhs * V;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    int slot = (int)(t / V), site = (int)(t - (long long)slot * V);
-    typedef typename Real_of<SPR>::T R;
-    cplx<R> s[12];
-    SpinorIO<SPR>::load(f, V, slot, site, s);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) out[((size_t)slot * V + site) * 12 + k] = make_double2((double)s[k].x, (double)s[k].y);
-  }
-}
-
-// one launch: grid (nrhs, tiles); every thread one site of one right-hand side
-template <int SPR, int NT>
-__global__ void __launch_bounds__(NT) k_w_dslash(LatGeom g, FieldPtr in, FieldPtr out, int Vmax) {
-  typedef typename Real_of<SPR>::T R;
-  constexpr int LPR = LinkPrecOf<SPR>::v;
-  const int slot = blockIdx.x;
-  const int ntiles = (g.V + NT - 1) / NT;
-  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
-    const int site = tile * NT + threadIdx.x;
-    if (site >= g.V) continue;
-    cplx<R> o[12], c[12];
-    wilson_site<SPR, LPR, R>(g, in, Vmax, slot, site, o, c);
-    SpinorIO<SPR>::store(out, Vmax, slot, site, o);
-  }
-}
-
 template <int SPR>
 static size_t spinor_bytes_of() {
   return SPR == PR64 ? 192 : (SPR == PR32 ? 96 : 48);
@@ -165,131 +117,22 @@ static int dslash_gridy(hp_ctx* ctx, int V, int NT, int nslots) {
   return std::max(1, std::min(std::min(ntiles, want), 65535));
 }
 
-template <int SPR>
-static hp_status launch_dslash(hp_ctx* ctx, const LatGeom& g, FieldPtr in, FieldPtr out, int nrhs, int Vmax) {
-  constexpr int NT = 128;
-  dim3 grid(nrhs, dslash_gridy(ctx, g.V, NT, nrhs));
-  {
-    ProfScope ps(ctx, SPR == PR64 ? "k_w_dslash<fp64>" : SPR == PR32 ? "k_w_dslash<fp32>" : SPR == PR16 ? "k_w_dslash<fp16>" : "k_w_dslash<bf16>");
-    k_w_dslash<SPR, NT><<<grid, NT, 0, ctx->stream>>>(g, in, out, Vmax);
-  }
-  HP_LAUNCH_CHECK();
-  return HP_OK;
-}
-
-template <int SPR>
-static hp_status apply_wilson_t(hp_ctx* ctx, const LatGeom& g, int nrhs, const double* in, double* out) {
-  const int V = g.V;
-  FieldPtr fi, fo;
-  HP_TRY(alloc_field(ctx, "apply.in", SPR, nrhs, V, &fi));
-  HP_TRY(alloc_field(ctx, "apply.out", SPR, nrhs, V, &fo));
-  const size_t cbytes = sizeof(double2) * 12 * (size_t)nrhs * V;
-  const void* din = nullptr;
-  HP_TRY(hp_device_view(ctx, in, cbytes, "apply.canon_in", &din));
-  double* dout = out;
-  bool out_host = !hp_is_device_ptr(out);
-  if (out_host) {
-    void* p = nullptr;
-    HP_TRY(hp_ws(ctx, "apply.canon_out", cbytes, &p));
-    dout = (double*)p;
-  }
-  k_w_from_canonical<SPR><<<blocks_for(ctx, (long long)nrhs * V, 256), 256, 0, ctx->stream>>>((const double2*)din, fi, V, nrhs);
-  HP_LAUNCH_CHECK();
-  HP_TRY(launch_dslash<SPR>(ctx, g, fi, fo, nrhs, V));
-  k_w_to_canonical<SPR><<<blocks_for(ctx, (long long)nrhs * V, 256), 256, 0, ctx->stream>>>(fo, V, nrhs, (double2*)dout);
-  HP_LAUNCH_CHECK();
-  if (out_host) {
-    HP_CUDA(cudaMemcpyAsync(out, dout, cbytes, cudaMemcpyDeviceToHost, ctx->stream));
-    HP_CUDA(cudaStreamSynchronize(ctx->stream));
-  }
-  return HP_OK;
-}
-
-hp_status hp_apply_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrhs, int prec, const double* in,
-                          double* out) {
-  HP_TRY(hp_prepare_mass(ctx, op, &g, "apply"));
-  HP_TRY(hp_prepare_wilson(ctx, op, &g, "apply", (1 << PR64) | (1 << PR32) | (1 << PR16)));
-  switch (prec) {
-    case HP_PREC_FP64: return apply_wilson_t<PR64>(ctx, g, nrhs, in, out);
-    case HP_PREC_MIXED_FP32: return apply_wilson_t<PR32>(ctx, g, nrhs, in, out);
-    case HP_PREC_MIXED_FP16: return apply_wilson_t<PR16>(ctx, g, nrhs, in, out);
-    case HP_PREC_MIXED_BF16: return apply_wilson_t<PRB16>(ctx, g, nrhs, in, out);
-  }
-  hp_set_error("unknown precision %d", prec);
-  return HP_EINVAL;
-}
-
-// fills a field with deterministic pseudo-random values (benchmark input)
-template <int SPR>
-__global__ void k_w_fill(FieldPtr f, int V, int nrhs, unsigned long long seed) {
-  const long long total = (long long)nrhs * V;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    int slot = (int)(t / V), site = (int)(t - (long long)slot * V);
-    typedef typename Real_of<SPR>::T R;
-    cplx<R> s[12];
-    unsigned long long z = seed ^ (unsigned long long)t * 0x9E3779B97F4A7C15ull;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      z = z * 6364136223846793005ull + 1442695040888963407ull;
-      s[k] = {(R)((double)(z >> 40) / 16777216.0 - 0.5), (R)((double)((z >> 16) & 0xffffff) / 16777216.0 - 0.5)};
-    }
-    SpinorIO<SPR>::store(f, V, slot, site, s);
-  }
-}
-
-template <int SPR>
-static hp_status bench_wilson_t(hp_ctx* ctx, const LatGeom& g, int nrhs, int iters, double* ms) {
-  const int V = g.V;
-  FieldPtr fi, fo;
-  HP_TRY(alloc_field(ctx, "bench.in", SPR, nrhs, V, &fi));
-  HP_TRY(alloc_field(ctx, "bench.out", SPR, nrhs, V, &fo));
-  k_w_fill<SPR><<<blocks_for(ctx, (long long)nrhs * V, 256), 256, 0, ctx->stream>>>(fi, V, nrhs, 12345ull);
-  HP_LAUNCH_CHECK();
-  for (int w = 0; w < 3; ++w) HP_TRY(launch_dslash<SPR>(ctx, g, fi, fo, nrhs, V));
-  cudaEvent_t a, b;
-  HP_CUDA(cudaEventCreate(&a));
-  HP_CUDA(cudaEventCreate(&b));
-  HP_CUDA(cudaEventRecord(a, ctx->stream));
-  for (int i = 0; i < iters; ++i) HP_TRY(launch_dslash<SPR>(ctx, g, fi, fo, nrhs, V));
-  HP_CUDA(cudaEventRecord(b, ctx->stream));
-  HP_CUDA(cudaEventSynchronize(b));
-  float t = 0.f;
-  HP_CUDA(cudaEventElapsedTime(&t, a, b));
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
-  *ms = (double)t / iters;
-  return HP_OK;
-}
-
-hp_status hp_bench_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int prec, int nrhs, int iters, double* ms,
-                          double* bytes, double* flops) {
-  HP_TRY(hp_prepare_mass(ctx, op, &g, "bench"));
-  HP_TRY(hp_prepare_wilson(ctx, op, &g, "bench", (1 << PR64) | (1 << PR32) | (1 << PR16)));
-  double S = 0, L = 0;
-  hp_status st = HP_EINVAL;
-  switch (prec) {
-    case HP_PREC_FP64: S = 192; L = 144; st = bench_wilson_t<PR64>(ctx, g, nrhs, iters, ms); break;
-    case HP_PREC_MIXED_FP32: S = 96; L = 48; st = bench_wilson_t<PR32>(ctx, g, nrhs, iters, ms); break;
-    case HP_PREC_MIXED_FP16: S = 52; L = 24; st = bench_wilson_t<PR16>(ctx, g, nrhs, iters, ms); break;
-    case HP_PREC_MIXED_BF16: S = 52; L = 24; st = bench_wilson_t<PRB16>(ctx, g, nrhs, iters, ms); break;
-    default: hp_set_error("unknown precision %d", prec); return HP_EINVAL;
-  }
-  if (st != HP_OK) return st;
-  *bytes = (double)nrhs * g.V * (2.0 * S + 4.0 * L / nrhs);
-  *flops = 1368.0 * nrhs * g.V;
-  return HP_OK;
-}
-
 // ==================================================================== solver
 // Per slot (right-hand side) BiCGStab, x_0 = 0, shadow r^ = b:
 //   v = D p; alpha = rho / (r^, v); s = r - alpha v; t = D s;
 //   omega = (t, s) / (t, t); e += alpha p + omega s; r = s - omega t;
 //   rho' = (r^, r); beta = (rho'/rho)(alpha/omega); p = r + beta (p - omega v)
-// in the iteration precision.  Reliable update (FP64) whenever ||r|| drops
-// below delta * (largest ||r|| since the last update) or below tol ||b||:
-//   x += e; e = 0; r = b - D x (FP64 stencil, FP64 links); stop when that
-//   true residual <= tol ||b||.
+// in the iteration precision (FP16/BF16 storage with FP32 arithmetic, or
+// FP32), e accumulating the solution since the last update.  Updates:
+//   group (FP32):  whenever ||r|| < delta max||r|| since the last update:
+//                  r_g -= D e (FP32 links and arithmetic), x += e (FP64),
+//                  e = 0, r = r_g.  x and r_g stay consistent whatever the
+//                  rounding of e, and the error of D e is ~1e-7 ||r||.
+//   exact (FP64):  when ||r|| <= tol ||b|| or ||r|| < 1e-5 of the residual
+//                  at the previous exact update: x += e, e = 0,
+//                  r = r_g = b - D x with FP64 links and arithmetic; the
+//                  solve stops when this true residual is <= tol ||b||.
+// FP64 solves run the same iteration in FP64 with exact updates only.
 // All scalars live per slot in device memory; reductions are deterministic
 // (fixed shuffle trees, per-block partials summed in block order by the
 // block that finishes last).
@@ -300,9 +143,9 @@ struct WArgs {
   unsigned int* cnt;     // [nslots]
   int Vmax, gy;
   FieldPtr r, rh, p, v, s, t, e;
+  FieldPtr rg;           // group-updated residual (FP32), mixed precision only
   double2* x;            // FP64 solution [slot][12][Vmax]
-  double* grad;          // unused here
-  double tol2, delta2;
+  double tol2, delta2, epsx2;
   int maxiter;
 };
 
@@ -352,6 +195,192 @@ __device__ __forceinline__ void reduce_partials(R (&v)[NQ], double* part, int gy
   }
 }
 
+// ---- the stencil on RPT right-hand sides per thread
+// Thread = one site; it loads (and reconstructs) each of the 8 links of the
+// site once and applies it to RPT slots of the same lattice.  Epilogues:
+//   EPI_PLAIN  out = D in
+//   EPI_V      v = D p ; sigma = (r^, v) ; alpha = rho / sigma
+//   EPI_T      t = D s ; omega = (t, s) / (t, t)
+enum { EPI_PLAIN = 0, EPI_V = 1, EPI_T = 2 };
+
+template <int SPR, int RPT, int NT, int EPI>
+__global__ void __launch_bounds__(NT) k_wds(WArgs a, FieldPtr in, FieldPtr out, int nslots) {
+  typedef typename Real_of<SPR>::T R;
+  constexpr int LPR = LinkPrecOf<SPR>::v;
+  constexpr int NQ = EPI == EPI_V ? 2 : 3;
+  const int slot0 = blockIdx.x * RPT;
+  __shared__ int act_sh[RPT];
+  __shared__ int lat_sh;
+  if (threadIdx.x == 0) {
+    int lat = -1;
+    for (int r = 0; r < RPT; ++r) {
+      const int sl = slot0 + r;
+      int on = 0;
+      if (sl < nslots) {
+        if (EPI == EPI_PLAIN) {
+          on = 1;
+          lat = 0;
+        } else if (a.st[sl].status == SLOT_RUN) {
+          on = 1;
+          if (lat < 0) lat = a.st[sl].lat;
+        }
+      }
+      act_sh[r] = on;
+    }
+    lat_sh = lat;
+  }
+  __syncthreads();
+  const int lat = lat_sh;
+  if (lat < 0) return;
+  bool act[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) act[r] = act_sh[r] != 0;
+  const LatGeom& g = a.lats[lat];
+  const int ntiles = (g.V + NT - 1) / NT;
+  if ((int)blockIdx.y >= ntiles) return;
+  const int nparts = min((int)gridDim.y, ntiles);
+  R dots[RPT][NQ];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) dots[r][q] = (R)0;
+  const R kap = (R)g.kappa;
+  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+    const int site = tile * NT + threadIdx.x;
+    if (site >= g.V) continue;
+    int x[4], st[4];
+    site_coords(g, site, x, st);
+    cplx<R> acc[RPT][12];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[r][k] = {(R)0, (R)0};
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      const int L = g.L[mu];
+      const int fw = (x[mu] + 1 == L) ? site - (L - 1) * st[mu] : site + st[mu];
+      const int bw = (x[mu] == 0) ? site + (L - 1) * st[mu] : site - st[mu];
+      cplx<R> u[9];
+      LinkIO<LPR>::load(g, mu, site, u);
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        if (!act[r]) continue;
+        cplx<R> psi[12], h[6], w[6];
+        SpinorIO<SPR>::load_nc(in, a.Vmax, slot0 + r, fw, psi);
+        if (mu == 0) project<0, -1>(psi, h);
+        if (mu == 1) project<1, -1>(psi, h);
+        if (mu == 2) project<2, -1>(psi, h);
+        if (mu == 3) project<3, -1>(psi, h);
+        su3_mul<R, false>(u, h, w);
+        if (mu == 0) accumulate<0, -1>(acc[r], w);
+        if (mu == 1) accumulate<1, -1>(acc[r], w);
+        if (mu == 2) accumulate<2, -1>(acc[r], w);
+        if (mu == 3) accumulate<3, -1>(acc[r], w);
+      }
+      LinkIO<LPR>::load(g, mu, bw, u);
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        if (!act[r]) continue;
+        cplx<R> psi[12], h[6], w[6];
+        SpinorIO<SPR>::load_nc(in, a.Vmax, slot0 + r, bw, psi);
+        if (mu == 0) project<0, 1>(psi, h);
+        if (mu == 1) project<1, 1>(psi, h);
+        if (mu == 2) project<2, 1>(psi, h);
+        if (mu == 3) project<3, 1>(psi, h);
+        su3_mul<R, true>(u, h, w);
+        if (mu == 0) accumulate<0, 1>(acc[r], w);
+        if (mu == 1) accumulate<1, 1>(acc[r], w);
+        if (mu == 2) accumulate<2, 1>(acc[r], w);
+        if (mu == 3) accumulate<3, 1>(acc[r], w);
+      }
+    }
+    const R diag = (R)(1.0 + g.mass + (g.mass_field ? g.mass_field[site] : 0.0));
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      if (!act[r]) continue;
+      cplx<R> c[12];
+      SpinorIO<SPR>::load_nc(in, a.Vmax, slot0 + r, site, c);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        acc[r][k].x = diag * c[k].x - kap * acc[r][k].x;
+        acc[r][k].y = diag * c[k].y - kap * acc[r][k].y;
+      }
+      SpinorIO<SPR>::store(out, a.Vmax, slot0 + r, site, acc[r]);
+      if (EPI == EPI_V) {
+        cplx<R> rh[12];
+        SpinorIO<SPR>::load(a.rh, a.Vmax, slot0 + r, site, rh);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          cplx<R> d = cconjmul(rh[k], acc[r][k]);
+          dots[r][0] += d.x;
+          dots[r][1] += d.y;
+        }
+      } else if (EPI == EPI_T) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          cplx<R> d = cconjmul(acc[r][k], c[k]);
+          dots[r][0] += d.x;
+          dots[r][1] += d.y;
+          dots[r][2 % NQ] += acc[r][k].x * acc[r][k].x + acc[r][k].y * acc[r][k].y;
+        }
+      }
+    }
+  }
+  if (EPI == EPI_PLAIN) return;
+  // per-slot block partials: warp shuffles in the iteration precision, warps in FP64
+  __shared__ double shp[RPT][NQ][NT / 32];
+  __shared__ int last_sh[RPT];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < RPT; ++r)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      R t = dots[r][q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0) shp[r][q][warp] = (double)t;
+    }
+  __syncthreads();
+  if (threadIdx.x < RPT * NQ) {
+    const int r = threadIdx.x / NQ, q = threadIdx.x % NQ;
+    if (act_sh[r]) {
+      double t = 0.0;
+      for (int w = 0; w < NT / 32; ++w) t += shp[r][q][w];
+      a.part[((size_t)(slot0 + r) * 4 + q) * a.gy + blockIdx.y] = t;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x < RPT) {
+    int l = 0;
+    if (act_sh[threadIdx.x]) {
+      unsigned int t = atomicAdd(a.cnt + slot0 + threadIdx.x, 1u);
+      l = (t == (unsigned int)nparts - 1u);
+    }
+    last_sh[threadIdx.x] = l;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    if (!last_sh[r]) continue;
+    __threadfence();
+    double tot[NQ];
+    block_sum_partials<NQ, NT>(a.part + (size_t)(slot0 + r) * 4 * a.gy, a.gy, nparts, tot);
+    if (threadIdx.x == 0) {
+      SlotState* S = a.st + slot0 + r;
+      if (EPI == EPI_V) {
+        S->alpha = cdiv(S->rho, make_double2(tot[0], tot[1]));
+        S->restart = 0;
+        if (S->need_update == 3) S->need_update = 0;
+      } else {
+        S->omega = tot[NQ - 1] > 0.0 ? make_double2(tot[0] / tot[NQ - 1], tot[1] / tot[NQ - 1]) : make_double2(0.0, 0.0);
+      }
+      S->sloppy_mv += 1;
+      a.cnt[slot0 + r] = 0;
+    }
+  }
+}
+
 // ---- init: x = 0, e = 0, r = r^ = p = b, ||b||^2
 template <int SPR, int EPR, int NT>
 __global__ void __launch_bounds__(NT) k_bicg_init(WArgs a) {
@@ -375,15 +404,20 @@ __global__ void __launch_bounds__(NT) k_bicg_init(WArgs a) {
       if (k == comp) b[k] = {(R)bv.x, (R)bv.y};
     SpinorIO<PR64>::store(FieldPtr{a.x, nullptr}, a.Vmax, slot, site, z);
     {
-      cplx<float> zf[12];
+      cplx<typename Real_of<EPR>::T> ze[12];
 #pragma unroll
-      for (int k = 0; k < 12; ++k) zf[k] = {0.f, 0.f};
-      if (EPR == PR64) SpinorIO<PR64>::store(a.e, a.Vmax, slot, site, z);
-      else SpinorIO<PR32>::store(a.e, a.Vmax, slot, site, zf);
+      for (int k = 0; k < 12; ++k) ze[k] = {0, 0};
+      SpinorIO<EPR>::store(a.e, a.Vmax, slot, site, ze);
     }
     SpinorIO<SPR>::store(a.r, a.Vmax, slot, site, b);
     SpinorIO<SPR>::store(a.rh, a.Vmax, slot, site, b);
     SpinorIO<SPR>::store(a.p, a.Vmax, slot, site, b);
+    if (SPR != PR64) {
+      cplx<float> bf[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) bf[k] = {(float)b[k].x, (float)b[k].y};
+      SpinorIO<PR32>::store(a.rg, a.Vmax, slot, site, bf);
+    }
     acc[0] += bv.x * bv.x + bv.y * bv.y;
   }
   reduce_partials<double, 1, NT>(acc, part, a.gy);
@@ -405,42 +439,9 @@ __global__ void __launch_bounds__(NT) k_bicg_init(WArgs a) {
       S->sloppy_mv = 0;
       S->fp64_mv = 0;
       S->true_res2 = tot[0];
+      S->rexact2 = tot[0];
+      S->gupdates = 0;
       S->status = tot[0] > 0.0 ? SLOT_RUN : SLOT_DONE;
-      a.cnt[slot] = 0;
-    }
-  }
-}
-
-// ---- v = D p ; sigma = (r^, v) ; alpha = rho / sigma
-template <int SPR, int NT>
-__global__ void __launch_bounds__(NT) k_bicg_v(WArgs a) {
-  SLOT_PREAMBLE(S->status == SLOT_RUN)
-  typedef typename Real_of<SPR>::T R;
-  constexpr int LPR = LinkPrecOf<SPR>::v;
-  R acc[2] = {0, 0};
-  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
-    const int site = tile * NT + threadIdx.x;
-    if (site >= g.V) continue;
-    cplx<R> o[12], c[12], rh[12];
-    wilson_site<SPR, LPR, R>(g, a.p, a.Vmax, slot, site, o, c);
-    SpinorIO<SPR>::store(a.v, a.Vmax, slot, site, o);
-    SpinorIO<SPR>::load(a.rh, a.Vmax, slot, site, rh);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      cplx<R> d = cconjmul(rh[k], o[k]);
-      acc[0] += d.x;
-      acc[1] += d.y;
-    }
-  }
-  reduce_partials<R, 2, NT>(acc, part, a.gy);
-  if (last_block(a.cnt + slot, nparts)) {
-    double tot[2];
-    block_sum_partials<2, NT>(part, a.gy, nparts, tot);
-    if (threadIdx.x == 0) {
-      double2 sigma = make_double2(tot[0], tot[1]);
-      S->alpha = cdiv(S->rho, sigma);
-      S->restart = 0;
-      S->sloppy_mv += 1;
       a.cnt[slot] = 0;
     }
   }
@@ -465,39 +466,6 @@ __global__ void __launch_bounds__(NT) k_bicg_s(WArgs a) {
       r[k].y -= ax * v[k].y + ay * v[k].x;
     }
     SpinorIO<SPR>::store(a.s, a.Vmax, slot, site, r);
-  }
-}
-
-// ---- t = D s ; (t, s), (t, t) ; omega = (t, s) / (t, t)
-template <int SPR, int NT>
-__global__ void __launch_bounds__(NT) k_bicg_t(WArgs a) {
-  SLOT_PREAMBLE(S->status == SLOT_RUN)
-  typedef typename Real_of<SPR>::T R;
-  constexpr int LPR = LinkPrecOf<SPR>::v;
-  R acc[3] = {0, 0, 0};
-  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
-    const int site = tile * NT + threadIdx.x;
-    if (site >= g.V) continue;
-    cplx<R> o[12], c[12];
-    wilson_site<SPR, LPR, R>(g, a.s, a.Vmax, slot, site, o, c);
-    SpinorIO<SPR>::store(a.t, a.Vmax, slot, site, o);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      cplx<R> d = cconjmul(o[k], c[k]);
-      acc[0] += d.x;
-      acc[1] += d.y;
-      acc[2] += o[k].x * o[k].x + o[k].y * o[k].y;
-    }
-  }
-  reduce_partials<R, 3, NT>(acc, part, a.gy);
-  if (last_block(a.cnt + slot, nparts)) {
-    double tot[3];
-    block_sum_partials<3, NT>(part, a.gy, nparts, tot);
-    if (threadIdx.x == 0) {
-      S->omega = tot[2] > 0.0 ? make_double2(tot[0] / tot[2], tot[1] / tot[2]) : make_double2(0.0, 0.0);
-      S->sloppy_mv += 1;
-      a.cnt[slot] = 0;
-    }
   }
 }
 
@@ -563,10 +531,59 @@ __global__ void __launch_bounds__(NT) k_bicg_xr(WArgs a) {
       S->iters += 1;
       if (S->iters >= a.maxiter) {
         S->status = SLOT_FAIL;
-        S->need_update = 1;
-      } else if (rr <= a.tol2 * S->bnorm2 || rr < a.delta2 * S->rmax2 || !(rr == rr)) {
+        S->need_update = 2;
+      } else if (rr <= a.tol2 * S->bnorm2 || rr < a.epsx2 * S->rexact2 || !(rr == rr)) {
+        S->need_update = 2;
+      } else if (rr < a.delta2 * S->rmax2) {
         S->need_update = 1;
       }
+      a.cnt[slot] = 0;
+    }
+  }
+}
+
+// ---- group update (FP32): r_g -= D e ; r = r_g ; (r^, r), ||r||^2   (x += e follows)
+template <int SPR, int EPR, int NT>
+__global__ void __launch_bounds__(NT) k_grp_update(WArgs a) {
+  SLOT_PREAMBLE(S->need_update == 1)
+  typedef typename Real_of<SPR>::T R;
+  float acc[3] = {0.f, 0.f, 0.f};
+  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+    const int site = tile * NT + threadIdx.x;
+    if (site >= g.V) continue;
+    cplx<float> de[12], c[12], rg[12];
+    wilson_site<EPR, PR32, float>(g, a.e, a.Vmax, slot, site, de, c);
+    SpinorIO<PR32>::load(a.rg, a.Vmax, slot, site, rg);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      rg[k].x -= de[k].x;
+      rg[k].y -= de[k].y;
+    }
+    SpinorIO<PR32>::store(a.rg, a.Vmax, slot, site, rg);
+    cplx<R> rs[12], rh[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) rs[k] = {(R)rg[k].x, (R)rg[k].y};
+    SpinorIO<SPR>::store(a.r, a.Vmax, slot, site, rs);
+    SpinorIO<SPR>::load(a.rh, a.Vmax, slot, site, rh);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      acc[0] += rg[k].x * rg[k].x + rg[k].y * rg[k].y;
+      acc[1] += (float)rh[k].x * rg[k].x + (float)rh[k].y * rg[k].y;
+      acc[2] += (float)rh[k].x * rg[k].y - (float)rh[k].y * rg[k].x;
+    }
+  }
+  reduce_partials<float, 3, NT>(acc, part, a.gy);
+  if (last_block(a.cnt + slot, nparts)) {
+    double tot[3];
+    block_sum_partials<3, NT>(part, a.gy, nparts, tot);
+    if (threadIdx.x == 0) {
+      const double rr = tot[0];
+      S->rnorm2 = rr;
+      S->rmax2 = rr;
+      S->rho = S->restart ? make_double2(rr, 0.0) : make_double2(tot[1], tot[2]);
+      S->gupdates += 1;
+      // 3: group update done, x += e pending (k_ru_accum); cleared by the next k_bicg_v
+      S->need_update = (rr <= a.tol2 * S->bnorm2 || rr < a.epsx2 * S->rexact2) ? 2 : 3;
       a.cnt[slot] = 0;
     }
   }
@@ -599,7 +616,7 @@ __global__ void __launch_bounds__(NT) k_ru_accum(WArgs a) {
 // ---- reliable update, part 2: r = b - D x in FP64, stored in the iteration precision
 template <int SPR, int NT>
 __global__ void __launch_bounds__(NT) k_ru_residual(WArgs a) {
-  SLOT_PREAMBLE(S->need_update)
+  SLOT_PREAMBLE(S->need_update == 2)
   typedef typename Real_of<SPR>::T R;
   double acc[3] = {0.0, 0.0, 0.0};
   const int comp = S->a, m = S->m;
@@ -623,6 +640,12 @@ __global__ void __launch_bounds__(NT) k_ru_residual(WArgs a) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) rs[k] = {(R)o[k].x, (R)o[k].y};
     SpinorIO<SPR>::store(a.r, a.Vmax, slot, site, rs);
+    if (SPR != PR64) {
+      cplx<float> rf[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) rf[k] = {(float)o[k].x, (float)o[k].y};
+      SpinorIO<PR32>::store(a.rg, a.Vmax, slot, site, rf);
+    }
     SpinorIO<SPR>::load(a.rh, a.Vmax, slot, site, rh);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
@@ -647,6 +670,7 @@ __global__ void __launch_bounds__(NT) k_ru_residual(WArgs a) {
         } else {
           S->rnorm2 = rr;
           S->rmax2 = rr;
+          S->rexact2 = rr;
           S->rho = S->restart ? make_double2(rr, 0.0) : make_double2(tot[1], tot[2]);
         }
       }
@@ -737,17 +761,24 @@ __global__ void k_w_grad(WArgs a, int lat, const int* __restrict__ slots, int ns
 
 // ================================================================ the engine
 template <int SPR>
+static hp_status tune_rpt(hp_ctx* ctx, const LatGeom& g, FieldPtr fi, FieldPtr fo, int nrhs, int Vmax, int* best);
+template <int SPR>
+__global__ void k_w_fill(FieldPtr f, int V, int nrhs, unsigned long long seed);
+
+template <int SPR>
 struct WilsonEngine {
-  static constexpr int EPR = SPR == PR64 ? PR64 : PR32;
+  static constexpr int EPR = SPR;      // solution increment e kept in the iteration precision
   static constexpr int NT = 128;
-  static constexpr int KERNELS_PER_ITERATION = 7;
+  static constexpr int KERNELS_PER_ITERATION = SPR == PR64 ? 7 : 8;
+  static constexpr int GROUP_MAX = 4;
   hp_ctx* ctx;
   WArgs a;
-  int nslots, gy;
+  int nslots, gy, rpt = 1;
   dim3 grid() const { return dim3(nslots, gy); }
+  int group() const { return rpt; }
 
   hp_status setup(int ns, int Vmax, const LatGeom* lats_dev, SlotState* st, const hp_solver_opts& o, double tol,
-                  double delta) {
+                  double delta, const LatGeom& gbig) {
     nslots = ns;
     memset(&a, 0, sizeof(a));
     a.lats = lats_dev;
@@ -768,12 +799,41 @@ struct WilsonEngine {
     HP_TRY(alloc_field(ctx, "solve.s", SPR, ns, Vmax, &a.s));
     HP_TRY(alloc_field(ctx, "solve.t", SPR, ns, Vmax, &a.t));
     HP_TRY(alloc_field(ctx, "solve.e", EPR, ns, Vmax, &a.e));
+    if (SPR != PR64) HP_TRY(alloc_field(ctx, "solve.rg", PR32, ns, Vmax, &a.rg));
     HP_TRY(hp_ws(ctx, "solve.x", sizeof(double2) * 12 * (size_t)ns * Vmax, &p));
     a.x = (double2*)p;
     a.tol2 = tol * tol;
     a.delta2 = delta * delta;
+    a.epsx2 = SPR == PR64 ? 0.0 : 1e-10;   // FP64 true residual after a 1e5 reduction
     a.maxiter = o.maxiter > 0 ? o.maxiter : 10000;
+    // right-hand sides per thread of the stencil: fixed by the caller or autotuned on the largest lattice
+    const int forced = o.rhs_per_thread;
+    if (forced == 1 || forced == 2 || forced == 4) {
+      rpt = forced;
+    } else {
+      k_w_fill<SPR><<<blocks_for(ctx, (long long)ns * Vmax, 256), 256, 0, ctx->stream>>>(a.p, Vmax, ns, 777ull);
+      HP_LAUNCH_CHECK();
+      HP_TRY(tune_rpt<SPR>(ctx, gbig, a.p, a.v, ns, Vmax, &rpt));
+    }
     return HP_OK;
+  }
+  template <int RPT>
+  hp_status stencil_steps_rpt(int which) {
+    dim3 gr((nslots + RPT - 1) / RPT, gy);
+    if (which == 0) {
+      ProfScope ps(ctx, SPR == PR64 ? "k_bicg_v<fp64>" : SPR == PR32 ? "k_bicg_v<fp32>" : SPR == PR16 ? "k_bicg_v<fp16>" : "k_bicg_v<bf16>");
+      k_wds<SPR, RPT, NT, EPI_V><<<gr, NT, 0, ctx->stream>>>(a, a.p, a.v, nslots);
+    } else {
+      ProfScope ps(ctx, SPR == PR64 ? "k_bicg_t<fp64>" : SPR == PR32 ? "k_bicg_t<fp32>" : SPR == PR16 ? "k_bicg_t<fp16>" : "k_bicg_t<bf16>");
+      k_wds<SPR, RPT, NT, EPI_T><<<gr, NT, 0, ctx->stream>>>(a, a.s, a.t, nslots);
+    }
+    HP_LAUNCH_CHECK();
+    return HP_OK;
+  }
+  hp_status stencil_step(int which) {
+    if (rpt == 4) return stencil_steps_rpt<4>(which);
+    if (rpt == 2) return stencil_steps_rpt<2>(which);
+    return stencil_steps_rpt<1>(which);
   }
   hp_status init() {
     {
@@ -784,12 +844,14 @@ struct WilsonEngine {
     return HP_OK;
   }
   hp_status iteration() {
-    const char* nv = SPR == PR64 ? "k_bicg_v<fp64>" : SPR == PR32 ? "k_bicg_v<fp32>" : SPR == PR16 ? "k_bicg_v<fp16>" : "k_bicg_v<bf16>";
-    const char* nt = SPR == PR64 ? "k_bicg_t<fp64>" : SPR == PR32 ? "k_bicg_t<fp32>" : SPR == PR16 ? "k_bicg_t<fp16>" : "k_bicg_t<bf16>";
-    { ProfScope ps(ctx, nv); k_bicg_v<SPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
+    HP_TRY(stencil_step(0));
     { ProfScope ps(ctx, "k_bicg_s"); k_bicg_s<SPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
-    { ProfScope ps(ctx, nt); k_bicg_t<SPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
+    HP_TRY(stencil_step(1));
     { ProfScope ps(ctx, "k_bicg_xr"); k_bicg_xr<SPR, EPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
+    if (SPR != PR64) {
+      ProfScope ps(ctx, "k_grp_update");
+      k_grp_update<SPR, EPR, NT><<<grid(), NT, 0, ctx->stream>>>(a);
+    }
     { ProfScope ps(ctx, "k_ru_accum"); k_ru_accum<EPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
     { ProfScope ps(ctx, "k_ru_residual<fp64>"); k_ru_residual<SPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
     { ProfScope ps(ctx, "k_bicg_p"); k_bicg_p<SPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
@@ -817,6 +879,214 @@ struct WilsonEngine {
   }
 };
 
+// ================================================================ plain apply
+template <int SPR>
+__global__ void k_w_from_canonical(const double2* __restrict__ in, FieldPtr f, int V, int nrhs) {
+  const long long total = (long long)nrhs * V;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int slot = (int)(t / V), site = (int)(t - (long long)slot * V);
+    typedef typename Real_of<SPR>::T R;
+    cplx<R> s[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double2 v = in[((size_t)slot * V + site) * 12 + k];
+      s[k] = {(R)v.x, (R)v.y};
+    }
+    SpinorIO<SPR>::store(f, V, slot, site, s);
+  }
+}
+
+template <int SPR>
+__global__ void k_w_to_canonical(FieldPtr f, int V, int nrhs, double2* __restrict__ out) {
+  const long long total = (long long)nrhs * V;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int slot = (int)(t / V), site = (int)(t - (long long)slot * V);
+    typedef typename Real_of<SPR>::T R;
+    cplx<R> s[12];
+    SpinorIO<SPR>::load(f, V, slot, site, s);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[((size_t)slot * V + site) * 12 + k] = make_double2((double)s[k].x, (double)s[k].y);
+  }
+}
+
+template <int SPR, int RPT>
+static hp_status launch_dslash_rpt(hp_ctx* ctx, const WArgs& a, FieldPtr in, FieldPtr out, int nrhs, int V) {
+  constexpr int NT = 128;
+  dim3 grid((nrhs + RPT - 1) / RPT, dslash_gridy(ctx, V, NT, (nrhs + RPT - 1) / RPT));
+  {
+    ProfScope ps(ctx, SPR == PR64 ? "k_wds<fp64>" : SPR == PR32 ? "k_wds<fp32>" : SPR == PR16 ? "k_wds<fp16>" : "k_wds<bf16>");
+    k_wds<SPR, RPT, NT, EPI_PLAIN><<<grid, NT, 0, ctx->stream>>>(a, in, out, nrhs);
+  }
+  HP_LAUNCH_CHECK();
+  return HP_OK;
+}
+
+// out = D in for nrhs fields of one lattice, RPT right-hand sides per thread
+template <int SPR>
+static hp_status launch_dslash(hp_ctx* ctx, const LatGeom& g, FieldPtr in, FieldPtr out, int nrhs, int Vmax, int rpt) {
+  void* p = nullptr;
+  HP_TRY(hp_ws(ctx, "dslash.lat", sizeof(LatGeom), &p));
+  HP_CUDA(cudaMemcpyAsync(p, &g, sizeof(LatGeom), cudaMemcpyHostToDevice, ctx->stream));
+  WArgs a;
+  memset(&a, 0, sizeof(a));
+  a.lats = (const LatGeom*)p;
+  a.Vmax = Vmax;
+  switch (rpt) {
+    case 1: return launch_dslash_rpt<SPR, 1>(ctx, a, in, out, nrhs, g.V);
+    case 2: return launch_dslash_rpt<SPR, 2>(ctx, a, in, out, nrhs, g.V);
+    default: return launch_dslash_rpt<SPR, 4>(ctx, a, in, out, nrhs, g.V);
+  }
+}
+
+static int apply_rpt(int nrhs) { return nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1); }
+
+template <int SPR>
+static hp_status apply_wilson_t(hp_ctx* ctx, const LatGeom& g, int nrhs, const double* in, double* out) {
+  const int V = g.V;
+  FieldPtr fi, fo;
+  HP_TRY(alloc_field(ctx, "apply.in", SPR, nrhs, V, &fi));
+  HP_TRY(alloc_field(ctx, "apply.out", SPR, nrhs, V, &fo));
+  const size_t cbytes = sizeof(double2) * 12 * (size_t)nrhs * V;
+  const void* din = nullptr;
+  HP_TRY(hp_device_view(ctx, in, cbytes, "apply.canon_in", &din));
+  double* dout = out;
+  bool out_host = !hp_is_device_ptr(out);
+  if (out_host) {
+    void* p = nullptr;
+    HP_TRY(hp_ws(ctx, "apply.canon_out", cbytes, &p));
+    dout = (double*)p;
+  }
+  k_w_from_canonical<SPR><<<blocks_for(ctx, (long long)nrhs * V, 256), 256, 0, ctx->stream>>>((const double2*)din, fi, V, nrhs);
+  HP_LAUNCH_CHECK();
+  HP_TRY(launch_dslash<SPR>(ctx, g, fi, fo, nrhs, V, apply_rpt(nrhs)));
+  k_w_to_canonical<SPR><<<blocks_for(ctx, (long long)nrhs * V, 256), 256, 0, ctx->stream>>>(fo, V, nrhs, (double2*)dout);
+  HP_LAUNCH_CHECK();
+  if (out_host) {
+    HP_CUDA(cudaMemcpyAsync(out, dout, cbytes, cudaMemcpyDeviceToHost, ctx->stream));
+    HP_CUDA(cudaStreamSynchronize(ctx->stream));
+  }
+  return HP_OK;
+}
+
+hp_status hp_apply_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrhs, int prec, const double* in,
+                          double* out) {
+  HP_TRY(hp_prepare_mass(ctx, op, &g, "apply"));
+  HP_TRY(hp_prepare_wilson(ctx, op, &g, "apply", (1 << PR64) | (1 << PR32) | (1 << PR16)));
+  switch (prec) {
+    case HP_PREC_FP64: return apply_wilson_t<PR64>(ctx, g, nrhs, in, out);
+    case HP_PREC_MIXED_FP32: return apply_wilson_t<PR32>(ctx, g, nrhs, in, out);
+    case HP_PREC_MIXED_FP16: return apply_wilson_t<PR16>(ctx, g, nrhs, in, out);
+    case HP_PREC_MIXED_BF16: return apply_wilson_t<PRB16>(ctx, g, nrhs, in, out);
+  }
+  hp_set_error("unknown precision %d", prec);
+  return HP_EINVAL;
+}
+
+// fills a field with deterministic pseudo-random values (benchmark input)
+template <int SPR>
+__global__ void k_w_fill(FieldPtr f, int V, int nrhs, unsigned long long seed) {
+  const long long total = (long long)nrhs * V;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int slot = (int)(t / V), site = (int)(t - (long long)slot * V);
+    typedef typename Real_of<SPR>::T R;
+    cplx<R> s[12];
+    unsigned long long z = seed ^ (unsigned long long)t * 0x9E3779B97F4A7C15ull;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      z = z * 6364136223846793005ull + 1442695040888963407ull;
+      s[k] = {(R)((double)(z >> 40) / 16777216.0 - 0.5), (R)((double)((z >> 16) & 0xffffff) / 16777216.0 - 0.5)};
+    }
+    SpinorIO<SPR>::store(f, V, slot, site, s);
+  }
+}
+
+// Autotuner: times the stencil with 1, 2 and 4 right-hand sides per thread on
+// the given fields (3 launches each, CUDA events) and caches the fastest per
+// (lattice, precision, number of right-hand sides).
+template <int SPR>
+static hp_status tune_rpt(hp_ctx* ctx, const LatGeom& g, FieldPtr fi, FieldPtr fo, int nrhs, int Vmax, int* best) {
+  char key[160];
+  snprintf(key, sizeof(key), "wds:%d:%d,%d,%d,%d:%d", SPR, g.L[0], g.L[1], g.L[2], g.L[3], nrhs);
+  auto it = ctx->autotune.find(key);
+  if (it != ctx->autotune.end()) {
+    *best = it->second;
+    return HP_OK;
+  }
+  cudaEvent_t e0, e1;
+  HP_CUDA(cudaEventCreate(&e0));
+  HP_CUDA(cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  int best_r = 1;
+  const int cands[3] = {1, 2, 4};
+  for (int c : cands) {
+    if (c > 1 && c > nrhs) continue;
+    HP_TRY(launch_dslash<SPR>(ctx, g, fi, fo, nrhs, Vmax, c));
+    HP_CUDA(cudaEventRecord(e0, ctx->stream));
+    for (int i = 0; i < 3; ++i) HP_TRY(launch_dslash<SPR>(ctx, g, fi, fo, nrhs, Vmax, c));
+    HP_CUDA(cudaEventRecord(e1, ctx->stream));
+    HP_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    HP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_r = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->autotune[key] = best_r;
+  *best = best_r;
+  return HP_OK;
+}
+
+template <int SPR>
+static hp_status bench_wilson_t(hp_ctx* ctx, const LatGeom& g, int nrhs, int iters, double* ms) {
+  const int V = g.V;
+  FieldPtr fi, fo;
+  HP_TRY(alloc_field(ctx, "bench.in", SPR, nrhs, V, &fi));
+  HP_TRY(alloc_field(ctx, "bench.out", SPR, nrhs, V, &fo));
+  k_w_fill<SPR><<<blocks_for(ctx, (long long)nrhs * V, 256), 256, 0, ctx->stream>>>(fi, V, nrhs, 12345ull);
+  HP_LAUNCH_CHECK();
+  int rpt = 1;
+  HP_TRY(tune_rpt<SPR>(ctx, g, fi, fo, nrhs, V, &rpt));
+  for (int w = 0; w < 3; ++w) HP_TRY(launch_dslash<SPR>(ctx, g, fi, fo, nrhs, V, rpt));
+  cudaEvent_t a, b;
+  HP_CUDA(cudaEventCreate(&a));
+  HP_CUDA(cudaEventCreate(&b));
+  HP_CUDA(cudaEventRecord(a, ctx->stream));
+  for (int i = 0; i < iters; ++i) HP_TRY(launch_dslash<SPR>(ctx, g, fi, fo, nrhs, V, rpt));
+  HP_CUDA(cudaEventRecord(b, ctx->stream));
+  HP_CUDA(cudaEventSynchronize(b));
+  float t = 0.f;
+  HP_CUDA(cudaEventElapsedTime(&t, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  *ms = (double)t / iters;
+  return HP_OK;
+}
+
+hp_status hp_bench_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int prec, int nrhs, int iters, double* ms,
+                          double* bytes, double* flops) {
+  HP_TRY(hp_prepare_mass(ctx, op, &g, "bench"));
+  HP_TRY(hp_prepare_wilson(ctx, op, &g, "bench", (1 << PR64) | (1 << PR32) | (1 << PR16)));
+  double S = 0, L = 0;
+  hp_status st = HP_EINVAL;
+  switch (prec) {
+    case HP_PREC_FP64: S = 192; L = 144; st = bench_wilson_t<PR64>(ctx, g, nrhs, iters, ms); break;
+    case HP_PREC_MIXED_FP32: S = 96; L = 48; st = bench_wilson_t<PR32>(ctx, g, nrhs, iters, ms); break;
+    case HP_PREC_MIXED_FP16: S = 52; L = 24; st = bench_wilson_t<PR16>(ctx, g, nrhs, iters, ms); break;
+    case HP_PREC_MIXED_BF16: S = 52; L = 24; st = bench_wilson_t<PRB16>(ctx, g, nrhs, iters, ms); break;
+    default: hp_set_error("unknown precision %d", prec); return HP_EINVAL;
+  }
+  if (st != HP_OK) return st;
+  *bytes = (double)nrhs * g.V * (2.0 * S + 4.0 * L / nrhs);
+  *flops = 1368.0 * nrhs * g.V;
+  return HP_OK;
+}
+
 // generic slot scheduler shared by both operator families
 #include "hp_schedule.cuh"
 
@@ -830,7 +1100,7 @@ hp_status hp_solve_wilson(hp_ctx* ctx, SolveProblem& pb, SolveResult& res) {
     }
     case HP_PREC_MIXED_FP32: {
       WilsonEngine<PR32> e{ctx};
-      return run_schedule(ctx, e, pb, res, 12, delta > 0 ? delta : 1e-3);
+      return run_schedule(ctx, e, pb, res, 12, delta > 0 ? delta : 0.01);
     }
     case HP_PREC_MIXED_FP16: {
       WilsonEngine<PR16> e{ctx};

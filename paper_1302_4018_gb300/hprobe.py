@@ -64,14 +64,14 @@ class SolverOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("rhs_block", C.c_int32), ("maxiter", C.c_int32),
                 ("dilution", C.c_int32), ("z0_seed", C.c_uint64), ("first", C.c_int64), ("delta", C.c_double),
                 ("check_every", C.c_int32), ("use_graph", C.c_int32), ("block_threads", C.c_int32),
-                ("reserved", C.c_int32 * 5)]
+                ("rhs_per_thread", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class SolveStats(C.Structure):
     _fields_ = [("rhs_solved", C.c_int64), ("iterations_total", C.c_int64), ("iterations_max", C.c_int32),
                 ("iterations_min", C.c_int32), ("reliable_updates", C.c_int64), ("sloppy_matvecs", C.c_int64),
                 ("fp64_matvecs", C.c_int64), ("max_true_residual", C.c_double), ("seconds", C.c_double),
-                ("n_unconverged", C.c_int32), ("reserved", C.c_int32)]
+                ("n_unconverged", C.c_int32), ("group_updates", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -214,17 +214,20 @@ class Context:
     # ---------------------------------------------------------------- operators
     @staticmethod
     def make_operator(kind: int, mass: float = 0.0, kappa: float = 0.0, links=None, mass_field=None) -> Operator:
+        """The operator struct; it keeps the link and mass-field arrays alive (the C struct only
+        holds their addresses)."""
         op = Operator()
         op.kind = kind
         op.mass = float(mass)
         op.kappa = float(kappa)
         op.links = _ptr(links)
         op.mass_field = _ptr(mass_field)
+        op._keep = (links, mass_field)
         return op
 
     @staticmethod
     def make_opts(precision="fp64", rhs_block=0, maxiter=0, z0_seed=0, first=0, delta=0.0, check_every=0,
-                  use_graph=0, block_threads=0, dilution=0) -> SolverOpts:
+                  use_graph=0, block_threads=0, dilution=0, rhs_per_thread=0) -> SolverOpts:
         o = SolverOpts()
         o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
         o.rhs_block = rhs_block
@@ -236,6 +239,7 @@ class Context:
         o.check_every = check_every
         o.use_graph = use_graph
         o.block_threads = block_threads
+        o.rhs_per_thread = rhs_per_thread
         return o
 
     def operator_apply(self, op: Operator, dims, nrhs: int, precision, inp, out):

@@ -116,10 +116,10 @@ WILSON_TOL = {"fp64": 1e-13, "fp32": 3e-6, "fp16": 4e-3, "bf16": 3e-2}
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (3, 5, 4, 6), (2, 2, 2, 2), (8, 4, 6, 2), (1, 4, 1, 3)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
-def test_wilson_apply_parity(ctx, hp, dims, prec):
+@pytest.mark.parametrize("nrhs", [1, 3, 5])      # 1, 2 and 4 right-hand sides per thread (with idle tails)
+def test_wilson_apply_parity(ctx, hp, dims, prec, nrhs):
     U = synth.gauge_links(dims, 0.4, 7)
     mf = synth.mass_field(dims, 0.01, 8)
-    nrhs = 3
     psi = synth.random_spinors(dims, nrhs, 9)
     op = ctx.make_operator(hp.OP_WILSON, 0.03, 0.12, links_dev(U), dev(mf))
     out = torch.empty(psi.size * 2, dtype=torch.float64, device="cuda:0")
@@ -200,13 +200,15 @@ def test_laplacian_complex_probes(ctx, hp):
     assert abs(T[-1].real - laplacian_trace_inverse(dims, 0.2)) <= 1e-9 * laplacian_trace_inverse(dims, 0.2)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
-def test_wilson_trace_parity(ctx, hp, prec):
+@pytest.mark.parametrize("prec,rpt", [("fp64", 0), ("fp64", 1), ("fp32", 1), ("fp32", 2), ("fp32", 4),
+                                      ("fp16", 1), ("fp16", 2), ("fp16", 4), ("bf16", 0), ("bf16", 2)])
+def test_wilson_trace_parity(ctx, hp, prec, rpt):
     dims = (4, 4, 4, 4)
     U = synth.gauge_links(dims, 0.3, 1002)
     op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.115, links_dev(U), None)
     s = 6
-    T, _, st = ctx.trace_inv(op, dims, s, 1e-10, ctx.make_opts(prec, z0_seed=2002, rhs_block=24))
+    T, _, st = ctx.trace_inv(op, dims, s, 1e-10, ctx.make_opts(prec, z0_seed=2002, rhs_block=24,
+                                                                rhs_per_thread=rpt))
     T_ref = E.trace_prefix(E.wilson_quadratures(dims, U, 0.115, 0, s, 2002, method="dense"))
     assert np.all(rel(T, T_ref) <= TRACE_RTOL), (T, T_ref)
     assert st["max_true_residual"] <= 1e-10
