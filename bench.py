@@ -179,11 +179,20 @@ def run_ours(args):
     links_dev = torch.from_numpy(U.view(np.float64).reshape(-1)).to(device)
     links_host = torch.from_numpy(U.view(np.float64).reshape(-1)).pin_memory()
     del U
+    from paper_1302_4018_gb300.sharding import probe_block
+
     prec = args.precision
     P = args.probes_per_step
-    total_steps = args.warmup + args.steps
-    base = rank * (total_steps + 4) * P       # disjoint probe range per rank
-    q = np.zeros(base + (total_steps + 4) * P + 16, dtype=np.complex128)
+    rounds = args.warmup + args.steps + 4
+    q = np.zeros((rounds * ws + 1) * P + args.fp64_probes + 16, dtype=np.complex128)
+    round_no = [0]
+
+    def next_first():
+        # rank r solves block r of every round (disjoint probes; its prefix below is left at q = 0 here,
+        # the ranks' quadrature blocks concatenate into the nested sequence)
+        first, _ = probe_block(rank, ws, P, round_no[0])
+        round_no[0] += 1
+        return first
 
     def step(first, links, precision=prec, probes=P, rhs_block=args.rhs_block):
         op = ctx.make_operator(hprobe.OP_WILSON, 0.0, KAPPA, links, None)
@@ -194,12 +203,8 @@ def run_ours(args):
         q[:s_max] = qq
         return st
 
-    first = base
-    # rank r owns probes [base, ...): its prefix below `base` is left at q = 0 here (the ranks'
-    # quadrature blocks are disjoint and concatenate into the nested sequence)
     for _ in range(args.warmup):
-        step(first, links_dev)
-        first += P
+        step(next_first(), links_dev)
     ctx.profile_enable(True)
     ctx.profile_report()
     clocks = Clocks(local)
@@ -211,8 +216,7 @@ def run_ours(args):
     ev0.record(stream)
     stats = []
     for _ in range(args.steps):
-        stats.append(step(first, links_dev))
-        first += P
+        stats.append(step(next_first(), links_dev))
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -220,6 +224,7 @@ def run_ours(args):
     ms_dev = ev0.elapsed_time(ev1)
     launches = ctx.launch_count() - n0
     prof = ctx.profile_report()
+    autotune = prof.pop("_autotune", {})
     ctx.profile_enable(False)
     ms_max = max_over_ranks(ws, ms_dev, device)
     rhs = sum(s["rhs_solved"] for s in stats)
@@ -236,10 +241,10 @@ def run_ours(args):
     e2e_rhs = 0
     h2d = d2h = 0
     for _ in range(e2e_steps):
+        first = next_first()
         e2e_rhs += step(first, links_host)["rhs_solved"]
         h2d += V * 72 * 8 + 16 * first          # links, earlier quadratures
         d2h += 2 * 16 * (first + P)             # quadratures and prefix estimates
-        first += P
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(ws, time.perf_counter() - t0, device)
     e2e = {"value": ws * e2e_rhs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d / e2e_steps),
@@ -248,6 +253,7 @@ def run_ours(args):
     # plain FP64 solver on the same GPU (one probe = 12 solves), for the mixed-vs-FP64 ratio
     fp64 = None
     if not args.no_fp64:
+        first = next_first()
         step(first, links_dev, precision="fp64", probes=1, rhs_block=12)   # warm-up (allocation)
         first += 1
         torch.cuda.synchronize()
@@ -256,7 +262,6 @@ def run_ours(args):
         st64 = step(first, links_dev, precision="fp64", probes=args.fp64_probes, rhs_block=12)
         e1.record(stream)
         torch.cuda.synchronize()
-        first += args.fp64_probes
         ms64 = max_over_ranks(ws, e0.elapsed_time(e1), device)
         fp64 = {"solves_per_s": ws * st64["rhs_solved"] / (ms64 / 1e3), "rhs": st64["rhs_solved"],
                 "iters_per_solve": st64["iterations_total"] / max(1, st64["rhs_solved"]),
@@ -320,6 +325,7 @@ def run_ours(args):
         "mixed_over_fp64": (value / ws / fp64["solves_per_s"] * ws) if fp64 else None,
         "dslash": dslash,
         "kernels": kernels,
+        "autotune": autotune,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -226,8 +226,9 @@ hp_status hp_dslash_bench(hp_ctx* ctx, const hp_operator* op, const hp_lattice* 
 
 /* Per-kernel timing of everything the context launches while enabled
  * (CUDA events around each launch).  hp_profile_report writes a JSON
- * object {"kernel": {"launches": n, "ms": t}, ...} into buf (host, size
- * bytes, NUL-terminated, truncated if short) and clears the records. */
+ * object {"kernel": {"launches": n, "ms": t}, ..., "_autotune": {key: choice}}
+ * into buf (host, size bytes, NUL-terminated, truncated if short) and clears
+ * the timing records. */
 hp_status hp_profile_enable(hp_ctx* ctx, int32_t on);
 /* Number of kernels the context has launched since its creation (kernels
  * replayed from captured graphs included), into *out (host). */

@@ -212,7 +212,16 @@ extern "C" hp_status hp_profile_report(hp_ctx* ctx, char* buf, int64_t size) {
     s += line;
     firstk = false;
   }
-  s += "}";
+  // autotuner decisions (stencil right-hand sides per thread, per lattice/precision/slot count)
+  s += firstk ? "\"_autotune\": {" : ", \"_autotune\": {";
+  bool firsta = true;
+  for (auto& kv : ctx->autotune) {
+    char line[256];
+    snprintf(line, sizeof(line), "%s\"%s\": %d", firsta ? "" : ", ", kv.first.c_str(), kv.second);
+    s += line;
+    firsta = false;
+  }
+  s += "}}";
   size_t n = s.size() < (size_t)(size - 1) ? s.size() : (size_t)(size - 1);
   memcpy(buf, s.data(), n);
   buf[n] = 0;

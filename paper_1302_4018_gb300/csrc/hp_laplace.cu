@@ -81,7 +81,7 @@ struct LArgs {
   const int slot = blockIdx.x;                                     \
   SlotState* S = a.st + slot;                                      \
   if (!(COND)) return;                                             \
-  const LatGeom& g = a.lats[S->lat];                               \
+  const LatGeom g = a.lats[S->lat];                                \
   const int ntiles = (g.V + NT - 1) / NT;                          \
   if ((int)blockIdx.y >= ntiles) return;                           \
   const int nparts = min((int)gridDim.y, ntiles);                  \
@@ -311,7 +311,7 @@ struct LaplaceEngine {
     a.st = st;
     a.Vmax = Vmax;
     int ntiles = (Vmax + NT - 1) / NT;
-    gy = std::max(1, std::min(std::min(ntiles, (ctx->num_sms * 8 + ns - 1) / ns), 65535));
+    gy = std::max(1, std::min(std::min(ntiles, ctx->num_sms * 4), 65535));
     a.gy = gy;
     void* p = nullptr;
     HP_TRY(hp_ws(ctx, "solve.part", sizeof(double) * 4 * (size_t)ns * gy, &p));

@@ -111,9 +111,12 @@ static hp_status alloc_field(hp_ctx* ctx, const std::string& name, int spr, int 
   return HP_OK;
 }
 
+// Blocks per slot: enough for one active slot to fill the GPU on its own
+// (masked launches often carry a single slot), grid-stride over the tiles.
 static int dslash_gridy(hp_ctx* ctx, int V, int NT, int nslots) {
+  (void)nslots;
   int ntiles = (V + NT - 1) / NT;
-  int want = (ctx->num_sms * 16 + nslots - 1) / nslots;
+  int want = ctx->num_sms * 8;
   return std::max(1, std::min(std::min(ntiles, want), 65535));
 }
 
@@ -153,7 +156,7 @@ struct WArgs {
   const int slot = blockIdx.x;                                     \
   SlotState* S = a.st + slot;                                      \
   if (!(COND)) return;                                             \
-  const LatGeom& g = a.lats[S->lat];                               \
+  const LatGeom g = a.lats[S->lat];                                \
   const int ntiles = (g.V + NT - 1) / NT;                          \
   if ((int)blockIdx.y >= ntiles) return;                           \
   const int nparts = min((int)gridDim.y, ntiles);                  \
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(NT) k_wds(WArgs a, FieldPtr in, FieldPtr out, 
   bool act[RPT];
 #pragma unroll
   for (int r = 0; r < RPT; ++r) act[r] = act_sh[r] != 0;
-  const LatGeom& g = a.lats[lat];
+  const LatGeom g = a.lats[lat];   // by value: the fields used in the loop stay in registers
   const int ntiles = (g.V + NT - 1) / NT;
   if ((int)blockIdx.y >= ntiles) return;
   const int nparts = min((int)gridDim.y, ntiles);

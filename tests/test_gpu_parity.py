@@ -354,3 +354,79 @@ def test_batch_matches_single_lattice_oracle(ctx, hp):
         for T, T_ref in zip(outs, refs):
             assert np.all(rel(T, T_ref) <= TRACE_RTOL)
         assert st["rhs_solved"] == 12 * sum(smax)
+
+
+# ------------------------------------------------------------------ uneven batch at full lattice sizes
+def test_batch_uneven_lattices_full_size(ctx, hp):
+    """8^4, 12^4, 16^3x32, 24^3x48 with kappa, eps from PCG64(3000) in one schedule (truncated s):
+    each lattice's prefix equals its own single-lattice solve.  12^4 runs past 256 vectors
+    into the three-colour / Fourier level."""
+    cfg = synth.batch_config()
+    s_list = [4, 260, 2, 2]          # 12^4: probes 0..259 include 256..259 of the F_3 level
+    ops, dims_list, keep = [], [], []
+    for c in cfg:
+        U = synth.gauge_links(c["dims"], c["eps"], c["link_seed"], device="cuda:0")
+        L = links_dev(U)
+        keep.append(L)
+        ops.append(ctx.make_operator(hp.OP_WILSON, 0.0, c["kappa"], L, None))
+        dims_list.append(c["dims"])
+    outs, st = ctx.trace_inv_batch(ops, dims_list, s_list, 1e-10, ctx.make_opts("fp16", z0_seed=3000,
+                                                                                rhs_block=48, use_graph=1))
+    assert st["rhs_solved"] == 12 * sum(s_list) and st["max_true_residual"] <= 1e-10
+    for op, dims, s, T in zip(ops, dims_list, s_list, outs):
+        T1, _, _ = ctx.trace_inv(op, dims, s, 1e-10, ctx.make_opts("fp64", z0_seed=3000))
+        assert np.all(rel(T, T1) <= TRACE_RTOL), (dims, T[:3], T1[:3])
+        assert np.max(np.abs(T.imag)) <= 1e-8 * np.max(np.abs(T.real))
+
+
+# ------------------------------------------------------------------ differentiation config
+def test_gradient_config_8x8x8x8_copy_vs_oracle_and_fd(ctx, hp):
+    """kappa 0.118, eps 0.3, mu(x) ~ N(0, 0.01) from PCG64(5000) on the 8^4 copy: the adjoint
+    (gamma_5) gradient equals the oracle's explicit-adjoint gradient and central differences."""
+    dims = (8, 8, 8, 8)
+    V = 4096
+    U = synth.gauge_links(dims, 0.3, 1005)
+    mf = synth.mass_field(dims, 0.01, 5000)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.118, links_dev(U), dev(mf))
+    s = 2
+    g = np.zeros(V)
+    T, dTdm, st = ctx.trace_inv_grad(op, dims, s, 1e-12, ctx.make_opts("fp64", z0_seed=5001), g)
+    g_ref = E.wilson_grad_mass_field(dims, U, 0.118, s, 5001, tol=1e-13, mass_field=mf).real
+    assert np.allclose(g, g_ref, rtol=1e-7, atol=1e-9 * np.abs(g_ref).max())
+    h = 1e-5
+    for site in (0, 1234, 4095):
+        e = mf.copy()
+        e[site] += h
+        tp, _, _ = ctx.trace_inv(ctx.make_operator(hp.OP_WILSON, 0.0, 0.118, links_dev(U), dev(e)), dims, s, 1e-13,
+                                 ctx.make_opts("fp64", z0_seed=5001))
+        e[site] -= 2 * h
+        tm, _, _ = ctx.trace_inv(ctx.make_operator(hp.OP_WILSON, 0.0, 0.118, links_dev(U), dev(e)), dims, s, 1e-13,
+                                 ctx.make_opts("fp64", z0_seed=5001))
+        fd = (tp[-1] - tm[-1]).real / (2 * h)
+        assert abs(fd - g[site]) <= 1e-4 * max(1.0, abs(g[site])), (site, fd, g[site])
+
+
+def test_gradient_config_24x24x24x48_properties(ctx, hp):
+    """24^3x48, kappa 0.118, eps 0.3 (truncated to s = 2): mixed and FP64 gradients agree, the
+    uniform-mass derivative equals the sum of the per-site one, and it matches central
+    differences of the uniform mass."""
+    dims = (24, 24, 24, 48)
+    V = 663552
+    U = synth.gauge_links(dims, 0.3, 1005, device="cuda:0")
+    mf = dev(synth.mass_field(dims, 0.01, 5000))
+    L = links_dev(U)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.118, L, mf)
+    g64 = torch.zeros(V, dtype=torch.float64, device="cuda:0")
+    g16 = torch.zeros(V, dtype=torch.float64, device="cuda:0")
+    T64, dm64, _ = ctx.trace_inv_grad(op, dims, 2, 1e-10, ctx.make_opts("fp64", z0_seed=5001), g64)
+    T16, dm16, _ = ctx.trace_inv_grad(op, dims, 2, 1e-10, ctx.make_opts("fp16", z0_seed=5001), g16)
+    assert abs(dm64 - g64.sum().item()) <= 1e-10 * abs(dm64)
+    assert abs(dm16 - dm64) <= 1e-7 * abs(dm64)
+    assert torch.allclose(g16, g64, rtol=1e-6, atol=1e-8 * g64.abs().max().item())
+    h = 1e-5
+    tp, _, _ = ctx.trace_inv(ctx.make_operator(hp.OP_WILSON, h, 0.118, L, mf), dims, 2, 1e-12,
+                             ctx.make_opts("fp64", z0_seed=5001))
+    tm, _, _ = ctx.trace_inv(ctx.make_operator(hp.OP_WILSON, -h, 0.118, L, mf), dims, 2, 1e-12,
+                             ctx.make_opts("fp64", z0_seed=5001))
+    fd = (tp[-1] - tm[-1]).real / (2 * h)
+    assert abs(fd - dm64) <= 1e-5 * abs(dm64), (fd, dm64)
