@@ -399,6 +399,96 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------------------------ other workloads
+def run_batch(args):
+    """Uneven batch: 8^4, 12^4, 16^3x32, 24^3x48 with kappa, eps, s from PCG64(3000), one schedule.
+    A step solves the next 1/8 of every lattice's probe sequence (all lattices in the same launches)."""
+    import torch
+
+    from paper_1302_4018_gb300 import hprobe, synth
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = hprobe.Context(0, stream=stream.cuda_stream)
+    cfg = synth.batch_config()
+    ops, dims_list, keep = [], [], []
+    for c in cfg:
+        U = synth.gauge_links(c["dims"], c["eps"], c["link_seed"], device="cuda:0")
+        L = torch.from_numpy(U.view(np.float64).reshape(-1)).cuda()
+        keep.append(L)
+        ops.append(ctx.make_operator(hprobe.OP_WILSON, 0.0, c["kappa"], L, None))
+        dims_list.append(c["dims"])
+    frac = 8
+    blocks = [c["s"] // frac for c in cfg]
+    opts = ctx.make_opts(args.precision, z0_seed=3000, use_graph=1, rhs_block=args.rhs_block * 2)
+
+    def one_step():
+        outs, st = ctx.trace_inv_batch(ops, dims_list, blocks, TOL, opts)
+        return st
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = ctx.launch_count()
+    e0.record(stream)
+    stats = [one_step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rhs = sum(s["rhs_solved"] for s in stats)
+    out = {"metric": "batched probing solves/s (uneven Wilson lattices, mixed precision, 1e-10)",
+           "value": rhs / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": args.precision + " iteration + f64 true residual", "data": "synthetic",
+           "config": {"workload": "batch [8^4, 12^4, 16^3x32, 24^3x48], kappa/eps/s from PCG64(3000), "
+                                  "probes per step s/8 each, one schedule, CUDA-graph iteration",
+                      "lattices": [list(d) for d in dims_list], "kappa": [c["kappa"] for c in cfg],
+                      "eps": [c["eps"] for c in cfg], "s": [c["s"] for c in cfg], "probes_per_step": blocks},
+           "gpu_launches": ctx.launch_count() - n0,
+           "solver": {"rhs": rhs, "iters_per_solve": sum(s["iterations_total"] for s in stats) / max(1, rhs),
+                      "max_true_residual": max(s["max_true_residual"] for s in stats)}}
+    print(json.dumps(out), flush=True)
+
+
+def run_grad(args):
+    """24^3x48, kappa 0.118, eps 0.3, mu(x) ~ N(0, 0.01): estimate and per-site mass gradient, s = 128."""
+    import torch
+
+    from paper_1302_4018_gb300 import hprobe, synth
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = hprobe.Context(0, stream=stream.cuda_stream)
+    dims = (24, 24, 24, 48)
+    U = synth.gauge_links(dims, 0.3, 1005, device="cuda:0")
+    links = torch.from_numpy(U.view(np.float64).reshape(-1)).cuda()
+    mf = torch.from_numpy(synth.mass_field(dims, 0.01, 5000)).cuda()
+    op = ctx.make_operator(hprobe.OP_WILSON, 0.0, 0.118, links, mf)
+    s_max = args.grad_probes
+    g = torch.zeros(mf.numel(), dtype=torch.float64, device="cuda:0")
+    opts = ctx.make_opts(args.precision, z0_seed=5001, rhs_block=args.rhs_block)
+    for _ in range(args.warmup):
+        ctx.trace_inv_grad(op, dims, s_max, TOL, opts, g)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = [ctx.trace_inv_grad(op, dims, s_max, TOL, opts, g) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rhs = sum(r[2]["rhs_solved"] for r in res)
+    T, dTdm, st = res[-1]
+    out = {"metric": "probing solves/s with the mass-field gradient (24^3x48 Wilson, 1e-10)",
+           "value": rhs / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": args.precision + " iteration + f64 true residual and gradient accumulation", "data": "synthetic",
+           "config": {"workload": "24^3x48 Wilson kappa 0.118 eps 0.3, mu ~ N(0, 0.01), s = %d, gradient" % s_max},
+           "estimate": {"T_s": T[-1].real, "dT_dm": dTdm, "grad_norm": float(torch.linalg.norm(g))},
+           "solver": st}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -411,9 +501,15 @@ def main():
     ap.add_argument("--fp64-probes", type=int, default=1)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="headline", choices=["headline", "batch", "grad"])
+    ap.add_argument("--grad-probes", type=int, default=128)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "grad":
+        run_grad(args)
     else:
         run_ours(args)
 

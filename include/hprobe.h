@@ -147,7 +147,8 @@ typedef struct {
     int32_t check_every;    /* iterations between host scheduling steps (0: automatic)   */
     int32_t use_graph;      /* 1: replay the iteration chunk from a captured CUDA graph  */
     int32_t block_threads;  /* reserved for the stencil block size (0)                    */
-    int32_t rhs_per_thread; /* right-hand sides per thread in the stencil: 1, 2, 4 (0: autotune) */
+    int32_t rhs_per_thread; /* stencil variant: 1, 2, 4 right-hand sides per thread with 12-real
+                               links, + 100 for 18-real links (0: autotune)                 */
     int32_t reserved[4];
 } hp_solver_opts;
 

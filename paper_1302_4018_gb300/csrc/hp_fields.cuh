@@ -10,8 +10,12 @@
 //         FP32 norm = max |component| so the stored values lie in [-1, 1])
 // Links of one lattice ([4][chunks][V], same coalescing):
 //   FP64: 9 double2 per link (full 3x3)
-//   FP32: 3 float4 per link (rows 1-2, 12 reals); row 3 = conj(row1 x row2)
-//   FP16: 3 uint2 per link (rows 1-2 in binary16), row 3 reconstructed
+//   FP32, 12 reals: 3 float4 per link (rows 1-2); row 3 = conj(row1 x row2)
+//   FP32, 18 reals: 4 float4 + 1 float2 per link (all entries, no reconstruction)
+//   FP16, 12 reals: 3 uint2 per link (rows 1-2 in binary16), row 3 reconstructed
+//   FP16, 18 reals: 2 uint4 + 1 half2 per link
+// (the 18-real forms trade bytes, shared by all right-hand sides of a launch,
+// for the reconstruction arithmetic of the ALU-bound sloppy stencil)
 #pragma once
 #include "hp_internal.h"
 
@@ -57,6 +61,12 @@ struct SpinorIO<PR64> {
     }
   }
   template <typename R>
+  __device__ static __forceinline__ void load_nc_raw(FieldPtr f, int Vmax, int slot, int site, cplx<R> (&s)[12],
+                                                     R& n) {
+    load_nc(f, Vmax, slot, site, s);
+    n = (R)1;
+  }
+  template <typename R>
   __device__ static __forceinline__ void store(FieldPtr f, int Vmax, int slot, int site, const cplx<R> (&s)[12]) {
     double2* b = (double2*)f.p + (size_t)slot * 12 * Vmax + site;
 #pragma unroll
@@ -93,6 +103,12 @@ struct SpinorIO<PR32> {
 #pragma unroll
     for (int k = 0; k < 6; ++k) c[k] = __ldg(b + (size_t)k * Vmax);
     unpack(c, s);
+  }
+  template <typename R>
+  __device__ static __forceinline__ void load_nc_raw(FieldPtr f, int Vmax, int slot, int site, cplx<R> (&s)[12],
+                                                     R& n) {
+    load_nc(f, Vmax, slot, site, s);
+    n = (R)1;
   }
   template <typename R>
   __device__ static __forceinline__ void store(FieldPtr f, int Vmax, int slot, int site, const cplx<R> (&s)[12]) {
@@ -160,6 +176,17 @@ struct SpinorIOHalf {
     for (int k = 0; k < 3; ++k) c[k] = __ldg(b + (size_t)k * Vmax);
     unpack(c, __ldg(f.nrm + (size_t)slot * Vmax + site), s);
   }
+  // values without the per-site norm, which is returned in n
+  template <typename R>
+  __device__ static __forceinline__ void load_nc_raw(FieldPtr f, int Vmax, int slot, int site, cplx<R> (&s)[12],
+                                                     R& n) {
+    const uint4* b = (const uint4*)f.p + (size_t)slot * 3 * Vmax + site;
+    uint4 c[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[k] = __ldg(b + (size_t)k * Vmax);
+    n = __ldg(f.nrm + (size_t)slot * Vmax + site);
+    unpack(c, 1.0f, s);
+  }
   template <typename R>
   __device__ static __forceinline__ void store(FieldPtr f, int Vmax, int slot, int site, const cplx<R> (&s)[12]) {
     float m = 0.f;
@@ -198,11 +225,12 @@ __device__ __forceinline__ void reconstruct_row3(cplx<R> (&u)[9]) {
   u[8] = {a.x - b.x, -(a.y - b.y)};
 }
 
-template <int LPR>
+// REC = 12: rows 1-2 stored, row 3 reconstructed; REC = 18: all nine entries stored
+template <int LPR, int REC = 12>
 struct LinkIO;
 
-template <>
-struct LinkIO<PR64> {
+template <int REC>
+struct LinkIO<PR64, REC> {
   static constexpr int BYTES = 144;
   template <typename R>
   __device__ static __forceinline__ void load(const LatGeom& g, int mu, int site, cplx<R> (&u)[9]) {
@@ -217,7 +245,7 @@ struct LinkIO<PR64> {
 };
 
 template <>
-struct LinkIO<PR32> {
+struct LinkIO<PR32, 12> {
   static constexpr int BYTES = 48;
   template <typename R>
   __device__ static __forceinline__ void load(const LatGeom& g, int mu, int site, cplx<R> (&u)[9]) {
@@ -233,7 +261,7 @@ struct LinkIO<PR32> {
 };
 
 template <>
-struct LinkIO<PR16> {
+struct LinkIO<PR16, 12> {
   static constexpr int BYTES = 24;
   template <typename R>
   __device__ static __forceinline__ void load(const LatGeom& g, int mu, int site, cplx<R> (&u)[9]) {
@@ -246,6 +274,44 @@ struct LinkIO<PR16> {
       u[2 * k + 1] = {c.x, c.y};
     }
     reconstruct_row3(u);
+  }
+};
+
+template <>
+struct LinkIO<PR32, 18> {
+  static constexpr int BYTES = 72;
+  template <typename R>
+  __device__ static __forceinline__ void load(const LatGeom& g, int mu, int site, cplx<R> (&u)[9]) {
+    const float4* b = g.U32f + (size_t)mu * 4 * g.V + site;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float4 v = __ldg(b + (size_t)k * g.V);
+      u[2 * k] = {v.x, v.y};
+      u[2 * k + 1] = {v.z, v.w};
+    }
+    float2 e = __ldg(g.U32g + (size_t)mu * g.V + site);
+    u[8] = {e.x, e.y};
+  }
+};
+
+template <>
+struct LinkIO<PR16, 18> {
+  static constexpr int BYTES = 36;
+  template <typename R>
+  __device__ static __forceinline__ void load(const LatGeom& g, int mu, int site, cplx<R> (&u)[9]) {
+    const uint4* b = g.U16f + (size_t)mu * 2 * g.V + site;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      uint4 v = __ldg(b + (size_t)k * g.V);
+      float2 a = Half2Ops<PR16>::to_f2(v.x), c = Half2Ops<PR16>::to_f2(v.y);
+      float2 d = Half2Ops<PR16>::to_f2(v.z), e = Half2Ops<PR16>::to_f2(v.w);
+      u[4 * k + 0] = {a.x, a.y};
+      u[4 * k + 1] = {c.x, c.y};
+      u[4 * k + 2] = {d.x, d.y};
+      u[4 * k + 3] = {e.x, e.y};
+    }
+    float2 f8 = Half2Ops<PR16>::to_f2(__ldg(g.U16g + (size_t)mu * g.V + site));
+    u[8] = {f8.x, f8.y};
   }
 };
 
@@ -309,6 +375,41 @@ __device__ __forceinline__ void accumulate(cplx<R> (&acc)[12], const cplx<R> (&w
     } else {   // -A^H v = -v;  A^H w = w
       acc[6 + c] = SIGN < 0 ? c_sub(acc[6 + c], w0) : c_add(acc[6 + c], w0);
       acc[9 + c] = SIGN < 0 ? c_sub(acc[9 + c], w1) : c_add(acc[9 + c], w1);
+    }
+  }
+}
+
+// acc += sc * (the spin reconstruction of w), as FMAs: the per-site norm of a
+// half-precision spinor and the factor -kappa ride along for free
+template <typename R>
+__device__ __forceinline__ void fadd_s(cplx<R>& a, cplx<R> w, R sc) {   // a += sc w
+  a.x = fma(sc, w.x, a.x);
+  a.y = fma(sc, w.y, a.y);
+}
+template <typename R>
+__device__ __forceinline__ void faddi_s(cplx<R>& a, cplx<R> w, R sc) {  // a += i sc w
+  a.x = fma(-sc, w.y, a.x);
+  a.y = fma(sc, w.x, a.y);
+}
+template <int MU, int SIGN, typename R>
+__device__ __forceinline__ void accumulate_s(cplx<R> (&acc)[12], const cplx<R> (&w)[6], R sc) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    cplx<R> w0 = w[c], w1 = w[3 + c];
+    fadd_s(acc[c], w0, sc);
+    fadd_s(acc[3 + c], w1, sc);
+    if (MU == 0) {   // -A^H v = (-i v1, -i v0);  A^H w = (i w1, i w0)
+      faddi_s(acc[6 + c], w1, SIGN < 0 ? -sc : sc);
+      faddi_s(acc[9 + c], w0, SIGN < 0 ? -sc : sc);
+    } else if (MU == 1) {   // -A^H v = (-v1, v0);  A^H w = (w1, -w0)
+      fadd_s(acc[6 + c], w1, SIGN < 0 ? -sc : sc);
+      fadd_s(acc[9 + c], w0, SIGN < 0 ? sc : -sc);
+    } else if (MU == 2) {   // -A^H v = (-i v0, i v1);  A^H w = (i w0, -i w1)
+      faddi_s(acc[6 + c], w0, SIGN < 0 ? -sc : sc);
+      faddi_s(acc[9 + c], w1, SIGN < 0 ? sc : -sc);
+    } else {   // -A^H v = -v;  A^H w = w
+      fadd_s(acc[6 + c], w0, SIGN < 0 ? -sc : sc);
+      fadd_s(acc[9 + c], w1, SIGN < 0 ? -sc : sc);
     }
   }
 }

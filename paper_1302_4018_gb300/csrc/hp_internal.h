@@ -66,6 +66,10 @@ struct LatGeom {
   const double2* U64;         // [4][9][V]
   const float4* U32;          // [4][3][V]  first two rows
   const uint2* U16;           // [4][3][V]  first two rows, binary16
+  const float4* U32f;         // [4][4][V]  entries 0-7 of the full link, FP32
+  const float2* U32g;         // [4][V]     entry 8
+  const uint4* U16f;          // [4][2][V]  entries 0-7 of the full link, binary16
+  const unsigned int* U16g;   // [4][V]     entry 8
   int dof;                    // unknowns per site that carry a source (12 Wilson, 1 Laplacian)
   int parts;                  // Laplacian: 2 when probes are complex (re, im solved apart)
 };

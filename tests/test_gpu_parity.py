@@ -114,9 +114,12 @@ def test_probe_errors(ctx, hp):
 WILSON_TOL = {"fp64": 1e-13, "fp32": 3e-6, "fp16": 4e-3, "bf16": 3e-2}
 
 
-@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (3, 5, 4, 6), (2, 2, 2, 2), (8, 4, 6, 2), (1, 4, 1, 3)])
+APPLY_CASES = [(d, n) for d in [(4, 4, 4, 4), (3, 5, 4, 6), (1, 4, 1, 3)] for n in (1, 2, 3, 4, 5, 6)] + \
+              [(d, 3) for d in [(2, 2, 2, 2), (8, 4, 6, 2)]]
+
+
+@pytest.mark.parametrize("dims,nrhs", APPLY_CASES)   # nrhs 1..6 select every stencil variant
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
-@pytest.mark.parametrize("nrhs", [1, 3, 5])      # 1, 2 and 4 right-hand sides per thread (with idle tails)
 def test_wilson_apply_parity(ctx, hp, dims, prec, nrhs):
     U = synth.gauge_links(dims, 0.4, 7)
     mf = synth.mass_field(dims, 0.01, 8)
@@ -200,8 +203,9 @@ def test_laplacian_complex_probes(ctx, hp):
     assert abs(T[-1].real - laplacian_trace_inverse(dims, 0.2)) <= 1e-9 * laplacian_trace_inverse(dims, 0.2)
 
 
-@pytest.mark.parametrize("prec,rpt", [("fp64", 0), ("fp64", 1), ("fp32", 1), ("fp32", 2), ("fp32", 4),
-                                      ("fp16", 1), ("fp16", 2), ("fp16", 4), ("bf16", 0), ("bf16", 2)])
+@pytest.mark.parametrize("prec,rpt", [("fp64", 0), ("fp64", 1), ("fp32", 1), ("fp32", 2), ("fp32", 4), ("fp32", 101),
+                                      ("fp32", 104), ("fp16", 1), ("fp16", 2), ("fp16", 4), ("fp16", 101),
+                                      ("fp16", 102), ("bf16", 0), ("bf16", 2), ("bf16", 104)])
 def test_wilson_trace_parity(ctx, hp, prec, rpt):
     dims = (4, 4, 4, 4)
     U = synth.gauge_links(dims, 0.3, 1002)
