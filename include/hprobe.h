@@ -214,6 +214,26 @@ hp_status hp_trace_inv_batch(hp_ctx* ctx, int32_t nlat, const hp_operator* ops, 
 hp_status hp_operator_apply(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t nrhs,
                             int32_t precision, const double* in, double* out);
 
+/* y = D x for the Wilson operator in FP64, allocating nothing (the paper has
+ * no counterpart: this serves callers that cannot let a library allocate GPU
+ * memory, e.g. an application whose device memory is reserved up front by
+ * another framework's allocator, or one that must keep synchronising
+ * cudaMalloc / cudaFree calls off a latency-critical stream).
+ * Same operator, layouts and FP64 arithmetic as hp_operator_apply with
+ * HP_PREC_FP64; op->links, op->mass_field (nullable), in_dev and out_dev
+ * must all be device memory of the current device, and the work is queued
+ * on cuda_stream (NULL: the legacy default stream); no context is used.
+ * Working memory is one fixed file-scope device array (11.9 MB, held by
+ * every GPU that loads the library until the process exits) that stores the
+ * rearranged links; each call rewrites the part it reads, so nothing needs
+ * clearing, but calls that overlap on the GPU share it and race.  The first
+ * call on each device resolves the array's device address
+ * (cudaGetSymbolAddress), so make it before any stream capture.
+ * Errors: HP_EINVAL for a lattice above 20736 sites (12^4), ndim outside
+ * [1, 4], nrhs < 1, host pointers or a non-Wilson operator. */
+hp_status hp_operator_apply_noalloc(const hp_operator* op, const hp_lattice* lat, int64_t nrhs,
+                                    const double* in_dev, double* out_dev, void* cuda_stream);
+
 /* Times `iters` launches of the Wilson stencil kernel in `precision` on
  * nrhs internal fields (CUDA events on the context stream) and reports the
  * mean time per launch and the algorithmic bytes / flops of one launch:

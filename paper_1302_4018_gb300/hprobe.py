@@ -42,7 +42,7 @@ EXPORTED = ["hp_ctx_create", "hp_ctx_destroy", "hp_last_error", "hp_ctx_synchron
             "hp_phase_values",
             "hp_permutation", "hp_probe_vectors", "hp_trace_inv", "hp_trace_inv_grad", "hp_trace_inv_batch",
             "hp_operator_apply", "hp_dslash_bench", "hp_profile_enable", "hp_profile_report",
-            "hp_launch_count"]
+            "hp_launch_count", "hp_operator_apply_noalloc"]
 
 
 class Lattice(C.Structure):
@@ -101,6 +101,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                       C.POINTER(D), C.POINTER(D), C.POINTER(D)]),
         "hp_profile_enable": (C.c_int, [P, I32]),
         "hp_launch_count": (C.c_int, [P, C.POINTER(I64)]),
+        "hp_operator_apply_noalloc": (C.c_int, [C.POINTER(Operator), C.POINTER(Lattice), I64, P, P, P]),
         "hp_profile_report": (C.c_int, [P, C.c_char_p, I64]),
     }
     for name, (res, args) in sig.items():
