@@ -36,8 +36,9 @@ METRIC = "probing solves/s (32^3x64 Wilson, mixed precision, true residual 1e-10
 UNIT = "solves/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK = 6800.0
-# mean BiCGStab iterations per solve of this workload in FP64 (measured on the GPU)
-FP64_ITERS_PER_SOLVE = None
+# mean iterations per solve of this workload with the oracle's algorithm (unpreconditioned BiCGStab
+# in FP64), measured with the library's FP64 solver on a GB300 (12 right-hand sides, 44.75)
+FP64_ITERS_PER_SOLVE = 44.75
 
 
 def hbm_peak():
@@ -197,7 +198,8 @@ def run_ours(args):
     def step(first, links, precision=prec, probes=P, rhs_block=args.rhs_block):
         op = ctx.make_operator(hprobe.OP_WILSON, 0.0, KAPPA, links, None)
         s_max = first + probes
-        opts = ctx.make_opts(precision, z0_seed=Z0_SEED, first=first, rhs_block=rhs_block)
+        opts = ctx.make_opts(precision, z0_seed=Z0_SEED, first=first, rhs_block=rhs_block,
+                             even_odd=1 if args.even_odd else 0)
         qq = q[:s_max].copy()
         T, qq, st = ctx.trace_inv(op, DIMS, s_max, TOL, opts, q_inout=qq)
         q[:s_max] = qq
@@ -301,7 +303,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        cpu = cpu_baseline(fp64["iters_per_solve"] if fp64 else None)
+        cpu = cpu_baseline(FP64_ITERS_PER_SOLVE)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -310,7 +312,9 @@ def run_ours(args):
                   "fp64": "f64"}[prec] + " + f64 reliable updates",
         "data": "synthetic: SU(3) links exp(i eps H), seeded (no gauge ensemble available)",
         "config": {"workload": "32^3x64 Wilson-Dirac, kappa 0.12, eps 0.4, %d probes x 12 dilutions per step, "
-                               "BiCGStab %s, tol 1e-10" % (P, prec),
+                               "BiCGStab %s%s, tol 1e-10" % (P, prec, " on the even-odd Schur complement"
+                                                              if args.even_odd else ""),
+                   "even_odd": bool(args.even_odd),
                    "lattice": list(DIMS), "probes_per_step": P, "rhs_per_step": 12 * P, "rhs_block": args.rhs_block,
                    "precision": prec, "tol": TOL, "l2": "inputs larger than L2 (each field >= 100 MB)",
                    "parallelism": "dp%d over probe blocks" % ws},
@@ -420,7 +424,8 @@ def run_batch(args):
         dims_list.append(c["dims"])
     frac = 8
     blocks = [c["s"] // frac for c in cfg]
-    opts = ctx.make_opts(args.precision, z0_seed=3000, use_graph=1, rhs_block=args.rhs_block * 2)
+    opts = ctx.make_opts(args.precision, z0_seed=3000, use_graph=1, rhs_block=args.rhs_block * 2,
+                         even_odd=args.even_odd)
 
     def one_step():
         outs, st = ctx.trace_inv_batch(ops, dims_list, blocks, TOL, opts)
@@ -467,7 +472,7 @@ def run_grad(args):
     op = ctx.make_operator(hprobe.OP_WILSON, 0.0, 0.118, links, mf)
     s_max = args.grad_probes
     g = torch.zeros(mf.numel(), dtype=torch.float64, device="cuda:0")
-    opts = ctx.make_opts(args.precision, z0_seed=5001, rhs_block=args.rhs_block)
+    opts = ctx.make_opts(args.precision, z0_seed=5001, rhs_block=args.rhs_block, even_odd=args.even_odd)
     for _ in range(args.warmup):
         ctx.trace_inv_grad(op, dims, s_max, TOL, opts, g)
     torch.cuda.synchronize()
@@ -502,6 +507,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="headline", choices=["headline", "batch", "grad"])
+    ap.add_argument("--even-odd", type=int, default=1, help="1: iterate on the odd-site Schur complement")
     ap.add_argument("--grad-probes", type=int, default=128)
     args = ap.parse_args()
     if args.impl == "reference":

@@ -148,8 +148,12 @@ typedef struct {
     int32_t use_graph;      /* 1: replay the iteration chunk from a captured CUDA graph  */
     int32_t block_threads;  /* reserved for the stencil block size (0)                    */
     int32_t rhs_per_thread; /* stencil variant: 1, 2, 4 right-hand sides per thread with 12-real
-                               links, + 100 for 18-real links (0: autotune)                 */
-    int32_t reserved[4];
+                               links, + 100 for 18-real links, + 1000 G to sweep the lattice
+                               in groups of G slots (0: autotune)                           */
+    int32_t even_odd;       /* Wilson: 1 = iterate on the odd-site Schur complement
+                               d_o - kappa^2 H_oe d_e^-1 H_eo (needs L_1 even; the certified
+                               residual is still that of the full system)                   */
+    int32_t reserved[3];
 } hp_solver_opts;
 
 typedef struct {

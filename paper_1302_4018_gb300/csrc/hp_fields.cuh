@@ -19,6 +19,53 @@
 #pragma once
 #include "hp_internal.h"
 
+// ----------------------------------------------------------------- float-float
+// An unevaluated sum hi + lo of two FP32 numbers (|lo| <= ulp(hi)/2): a 48-bit
+// significand on the FP32 pipes.  GB300 executes FP64 at 1/58 of the FP32 rate,
+// so the true-residual stencil of the mixed-precision solver runs in this
+// arithmetic.  Addition is Knuth's TwoSum followed by renormalisation; the
+// product uses an FMA to obtain the exact rounding error of hi*hi (TwoProduct)
+// plus the cross terms.  The intrinsics keep the compiler from contracting or
+// reassociating the error-free transformations.
+struct ffl {
+  float hi, lo;
+  __host__ __device__ ffl() {}
+  __host__ __device__ ffl(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ ffl(float h) : hi(h), lo(0.f) {}
+  __host__ __device__ ffl(int i) : hi((float)i), lo(0.f) {}
+  __host__ __device__ ffl(double d) : hi((float)d), lo((float)(d - (double)(float)d)) {}
+};
+__device__ __forceinline__ ffl ffl_renorm(float s, float e) {   // |s| >= |e|
+  float h = __fadd_rn(s, e);
+  return ffl(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ ffl operator+(ffl a, ffl b) {
+  float s = __fadd_rn(a.hi, b.hi);
+  float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return ffl_renorm(s, e);
+}
+__device__ __forceinline__ ffl operator-(ffl a) { return ffl(-a.hi, -a.lo); }
+__device__ __forceinline__ ffl operator-(ffl a, ffl b) { return a + (-b); }
+__device__ __forceinline__ ffl operator*(ffl a, ffl b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ffl_renorm(p, e);
+}
+__device__ __forceinline__ ffl fma(ffl a, ffl b, ffl c) { return a * b + c; }
+__device__ __forceinline__ ffl& operator+=(ffl& a, ffl b) {
+  a = a + b;
+  return a;
+}
+__device__ __forceinline__ ffl& operator-=(ffl& a, ffl b) {
+  a = a - b;
+  return a;
+}
+__device__ __forceinline__ double ffl_to_double(ffl a) { return (double)a.hi + (double)a.lo; }
+
 template <int PR>
 struct Real_of {
   typedef float T;
@@ -27,10 +74,15 @@ template <>
 struct Real_of<PR64> {
   typedef double T;
 };
+template <>
+struct Real_of<PRFF> {
+  typedef ffl T;
+};
 
 struct FieldPtr {
   void* p;
   float* nrm;   // half precisions only
+  void* lo;     // float-float fields: the FP32 field of low parts (p holds the high parts)
 };
 
 template <int PR>
@@ -116,6 +168,44 @@ struct SpinorIO<PR32> {
 #pragma unroll
     for (int k = 0; k < 6; ++k)
       b[(size_t)k * Vmax] = make_float4((float)s[2 * k].x, (float)s[2 * k].y, (float)s[2 * k + 1].x, (float)s[2 * k + 1].y);
+  }
+};
+
+template <>
+struct SpinorIO<PRFF> {
+  static constexpr int NCH = 6;
+  static constexpr int BYTES = 192;
+  template <typename R>
+  __device__ static __forceinline__ void load(FieldPtr f, int Vmax, int slot, int site, cplx<R> (&s)[12]) {
+    cplx<float> h[12], l[12];
+    SpinorIO<PR32>::load(FieldPtr{f.p, nullptr, nullptr}, Vmax, slot, site, h);
+    SpinorIO<PR32>::load(FieldPtr{f.lo, nullptr, nullptr}, Vmax, slot, site, l);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s[k] = {R(ffl(h[k].x, l[k].x)), R(ffl(h[k].y, l[k].y))};
+  }
+  template <typename R>
+  __device__ static __forceinline__ void load_nc(FieldPtr f, int Vmax, int slot, int site, cplx<R> (&s)[12]) {
+    cplx<float> h[12], l[12];
+    SpinorIO<PR32>::load_nc(FieldPtr{f.p, nullptr, nullptr}, Vmax, slot, site, h);
+    SpinorIO<PR32>::load_nc(FieldPtr{f.lo, nullptr, nullptr}, Vmax, slot, site, l);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s[k] = {R(ffl(h[k].x, l[k].x)), R(ffl(h[k].y, l[k].y))};
+  }
+  template <typename R>
+  __device__ static __forceinline__ void load_nc_raw(FieldPtr f, int Vmax, int slot, int site, cplx<R> (&s)[12],
+                                                     R& n) {
+    load_nc(f, Vmax, slot, site, s);
+    n = R(1);
+  }
+  __device__ static __forceinline__ void store(FieldPtr f, int Vmax, int slot, int site, const cplx<ffl> (&s)[12]) {
+    cplx<float> h[12], l[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      h[k] = {s[k].x.hi, s[k].y.hi};
+      l[k] = {s[k].x.lo, s[k].y.lo};
+    }
+    SpinorIO<PR32>::store(FieldPtr{f.p, nullptr, nullptr}, Vmax, slot, site, h);
+    SpinorIO<PR32>::store(FieldPtr{f.lo, nullptr, nullptr}, Vmax, slot, site, l);
   }
 };
 
@@ -291,6 +381,24 @@ struct LinkIO<PR32, 18> {
     }
     float2 e = __ldg(g.U32g + (size_t)mu * g.V + site);
     u[8] = {e.x, e.y};
+  }
+};
+
+template <int REC>
+struct LinkIO<PRFF, REC> {
+  static constexpr int BYTES = 144;
+  template <typename R>
+  __device__ static __forceinline__ void load(const LatGeom& g, int mu, int site, cplx<R> (&u)[9]) {
+    const float4* b = g.U32f + (size_t)mu * 4 * g.V + site;
+    const float4* c = g.U32fl + (size_t)mu * 4 * g.V + site;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float4 v = __ldg(b + (size_t)k * g.V), w = __ldg(c + (size_t)k * g.V);
+      u[2 * k] = {ffl(v.x, w.x), ffl(v.y, w.y)};
+      u[2 * k + 1] = {ffl(v.z, w.z), ffl(v.w, w.w)};
+    }
+    float2 e = __ldg(g.U32g + (size_t)mu * g.V + site), f = __ldg(g.U32gl + (size_t)mu * g.V + site);
+    u[8] = {ffl(e.x, f.x), ffl(e.y, f.y)};
   }
 };
 

@@ -41,7 +41,8 @@ void hp_set_error(const char* fmt, ...);
   } while (0)
 
 // -------------------------------------------------------------- precisions
-enum { PR64 = 0, PR32 = 1, PR16 = 2, PRB16 = 3 };
+// PRFF: float-float (an unevaluated sum hi + lo of two FP32 numbers, 48-bit significand)
+enum { PR64 = 0, PR32 = 1, PR16 = 2, PRB16 = 3, PRFF = 4 };
 
 // ---------------------------------------------------------- lattice (device)
 // Everything a kernel needs about one lattice: geometry, probing basis and
@@ -63,6 +64,8 @@ struct LatGeom {
   int op_kind;
   double kappa, mass;
   const double* mass_field;   // [V] or nullptr
+  const float* mass_field32;  // FP32 copy of mass_field for the FP32-arithmetic kernels
+  float diag0;                // 1 + mass in FP32
   const double2* U64;         // [4][9][V]
   const float4* U32;          // [4][3][V]  first two rows
   const uint2* U16;           // [4][3][V]  first two rows, binary16
@@ -70,6 +73,8 @@ struct LatGeom {
   const float2* U32g;         // [4][V]     entry 8
   const uint4* U16f;          // [4][2][V]  entries 0-7 of the full link, binary16
   const unsigned int* U16g;   // [4][V]     entry 8
+  const float4* U32fl;        // [4][4][V]  low parts (u - (float)u) of entries 0-7, float-float links
+  const float2* U32gl;        // [4][V]     low part of entry 8
   int dof;                    // unknowns per site that carry a source (12 Wilson, 1 Laplacian)
   int parts;                  // Laplacian: 2 when probes are complex (re, im solved apart)
 };

@@ -296,7 +296,7 @@ __global__ void k_lgrad(LArgs a, int lat, const int* __restrict__ slots, int nsl
 
 struct LaplaceEngine {
   static constexpr int NT = 256;
-  static constexpr int KERNELS_PER_ITERATION = 4;
+  int kernels_per_iteration() const { return 4; }
   static constexpr int GROUP_MAX = 1;
   hp_ctx* ctx;
   LArgs a;

@@ -107,7 +107,7 @@ hp_status run_schedule(hp_ctx* ctx, Engine& eng, SolveProblem& pb, SolveResult& 
     if (!any_init && !any_run) break;
     if (use_graph) {
       HP_CUDA(cudaGraphLaunch(gexec, ctx->stream));
-      ctx->launches += (long long)chunk * Engine::KERNELS_PER_ITERATION;
+      ctx->launches += (long long)chunk * eng.kernels_per_iteration();
     } else {
       for (int c = 0; c < chunk; ++c) HP_TRY(eng.iteration());
     }

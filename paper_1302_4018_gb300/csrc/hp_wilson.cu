@@ -13,7 +13,8 @@
 // canonical complex128 [V][4][3][3]  ->  internal layouts
 __global__ void k_links_convert(const double2* __restrict__ in, int V, double2* __restrict__ U64,
                                 float4* __restrict__ U32, uint2* __restrict__ U16, float4* __restrict__ U32f,
-                                float2* __restrict__ U32g, uint4* __restrict__ U16f, unsigned int* __restrict__ U16g) {
+                                float2* __restrict__ U32g, uint4* __restrict__ U16f, unsigned int* __restrict__ U16g,
+                                float4* __restrict__ U32fl, float2* __restrict__ U32gl) {
   const long long total = 4LL * V;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
@@ -47,6 +48,14 @@ __global__ void k_links_convert(const double2* __restrict__ in, int V, double2* 
             make_float4((float)u[2 * k].x, (float)u[2 * k].y, (float)u[2 * k + 1].x, (float)u[2 * k + 1].y);
       U32g[(size_t)mu * V + site] = make_float2((float)u[8].x, (float)u[8].y);
     }
+    if (U32fl) {   // low parts of the float-float links: u - (float)u, exact in FP32
+      auto lo = [](double v) { return (float)(v - (double)(float)v); };
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        U32fl[((size_t)mu * 4 + k) * V + site] =
+            make_float4(lo(u[2 * k].x), lo(u[2 * k].y), lo(u[2 * k + 1].x), lo(u[2 * k + 1].y));
+      U32gl[(size_t)mu * V + site] = make_float2(lo(u[8].x), lo(u[8].y));
+    }
     if (U16f) {
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
@@ -68,15 +77,29 @@ static int blocks_for(hp_ctx* ctx, long long n, int threads) {
   return (int)std::max(1LL, std::min(b, cap));
 }
 
+__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = (float)in[i];
+}
+
 hp_status hp_prepare_mass(hp_ctx* ctx, const hp_operator* op, LatGeom* g, const char* tag) {
   g->mass = op->mass;
   g->kappa = op->kappa;
+  g->diag0 = (float)(1.0 + op->mass);
   g->mass_field = nullptr;
+  g->mass_field32 = nullptr;
   if (op->mass_field) {
     std::string n = std::string(tag) + ".mass";
     const void* d = nullptr;
     HP_TRY(hp_device_view(ctx, op->mass_field, sizeof(double) * (size_t)g->V, n.c_str(), &d));
     g->mass_field = (const double*)d;
+    void* f = nullptr;
+    HP_TRY(hp_ws(ctx, (n + "32").c_str(), sizeof(float) * (size_t)g->V, &f));
+    {
+      ProfScope ps(ctx, "k_to_float");
+      k_to_float<<<blocks_for(ctx, g->V, 256), 256, 0, ctx->stream>>>(g->mass_field, (float*)f, g->V);
+    }
+    HP_LAUNCH_CHECK();
+    g->mass_field32 = (const float*)f;
   }
   return HP_OK;
 }
@@ -92,12 +115,14 @@ hp_status hp_prepare_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom* g, cons
   const void* src = nullptr;
   HP_TRY(hp_device_view(ctx, op->links, sizeof(double) * 72 * V, (base + ".links_in").c_str(), &src));
   void *u64 = nullptr, *u32 = nullptr, *u16 = nullptr, *u32f = nullptr, *u32g = nullptr, *u16f = nullptr,
-       *u16g = nullptr;
+       *u16g = nullptr, *u32fl = nullptr, *u32gl = nullptr;
   HP_TRY(hp_ws(ctx, (base + ".U64").c_str(), sizeof(double2) * 36 * V, &u64));   // always: true residual
   if (need_prec & (1 << PR32)) {
     HP_TRY(hp_ws(ctx, (base + ".U32").c_str(), sizeof(float4) * 12 * V, &u32));
     HP_TRY(hp_ws(ctx, (base + ".U32f").c_str(), sizeof(float4) * 16 * V, &u32f));
     HP_TRY(hp_ws(ctx, (base + ".U32g").c_str(), sizeof(float2) * 4 * V, &u32g));
+    HP_TRY(hp_ws(ctx, (base + ".U32fl").c_str(), sizeof(float4) * 16 * V, &u32fl));
+    HP_TRY(hp_ws(ctx, (base + ".U32gl").c_str(), sizeof(float2) * 4 * V, &u32gl));
   }
   if (need_prec & (1 << PR16)) {
     HP_TRY(hp_ws(ctx, (base + ".U16").c_str(), sizeof(uint2) * 12 * V, &u16));
@@ -108,7 +133,7 @@ hp_status hp_prepare_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom* g, cons
     ProfScope ps(ctx, "k_links_convert");
     k_links_convert<<<blocks_for(ctx, 4LL * V, 256), 256, 0, ctx->stream>>>(
         (const double2*)src, (int)V, (double2*)u64, (float4*)u32, (uint2*)u16, (float4*)u32f, (float2*)u32g,
-        (uint4*)u16f, (unsigned int*)u16g);
+        (uint4*)u16f, (unsigned int*)u16g, (float4*)u32fl, (float2*)u32gl);
   }
   HP_LAUNCH_CHECK();
   g->U64 = (const double2*)u64;
@@ -118,6 +143,8 @@ hp_status hp_prepare_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom* g, cons
   g->U32g = (const float2*)u32g;
   g->U16f = (const uint4*)u16f;
   g->U16g = (const unsigned int*)u16g;
+  g->U32fl = (const float4*)u32fl;
+  g->U32gl = (const float2*)u32gl;
   return HP_OK;
 }
 
@@ -145,10 +172,21 @@ static hp_status alloc_field(hp_ctx* ctx, const std::string& name, int spr, int 
   return HP_OK;
 }
 
-// Stencil variants: right-hand sides per thread (1, 2, 4) x link storage (12 or 18 reals),
-// encoded as variant = 10 * RPT + (REC == 18).  FP64 always uses full links.
-static int variant_rpt(int v) { return v / 10; }
+// Stencil variants: slots per sweep group G (0 = all slots in one sweep), right-hand sides per
+// thread (1, 2, 4) and link storage (12 or 18 reals), encoded as
+// variant = 100 * G + 10 * RPT + (REC == 18).  FP64 always uses full links.
+static int variant_rpt(int v) { return (v % 100) / 10; }
 static int variant_rec(int v) { return (v % 10) ? 18 : 12; }
+static int variant_group(int v) { return v / 100; }
+// launch grid of the stencil for nslots slots: (group members, tiles, groups)
+static dim3 stencil_grid(int variant, int nslots, int ntiles_y) {
+  const int rpt = variant_rpt(variant);
+  const int units = (nslots + rpt - 1) / rpt;                 // blocks needed along the slots
+  int g = variant_group(variant);
+  int gx = g > 0 ? std::max(1, std::min(units, g / rpt)) : units;
+  int gz = (units + gx - 1) / gx;
+  return dim3(gx, ntiles_y, gz);
+}
 
 // Blocks per slot: every tile of the lattice, so one active slot fills the GPU on its own
 // (masked launches often carry a single slot).
@@ -188,9 +226,16 @@ struct WArgs {
   int Vmax, gy;
   FieldPtr r, rh, p, v, s, t, e;
   FieldPtr rg;           // group-updated residual (FP32), mixed precision only
-  double2* x;            // FP64 solution [slot][12][Vmax]
+  double2* x;            // FP64 solution [slot][12][Vmax] (FP64 solves)
+  FieldPtr xff;          // float-float solution (hi, lo FP32 fields), mixed precision
   double tol2, delta2, epsx2;
   int maxiter;
+  // even-odd: Krylov fields live on the odd sites (half-site index = site >> 1)
+  int eo;
+  FieldPtr mid;          // even-site intermediate of the Schur operator (iteration precision)
+  FieldPtr mid32;        // even-site intermediate of group updates (FP32)
+  double2* xe;           // even-site solution, FP64 solves
+  FieldPtr xeff;         // even-site solution, float-float (mixed)
 };
 
 #define SLOT_PREAMBLE(COND)                                        \
@@ -198,11 +243,13 @@ struct WArgs {
   SlotState* S = a.st + slot;                                      \
   if (!(COND)) return;                                             \
   const LatGeom g = a.lats[S->lat];                                \
-  const int ntiles = (g.V + NT - 1) / NT;                          \
+  const int nsite = a.eo ? (g.V >> 1) : g.V;                       \
+  const int ntiles = (nsite + NT - 1) / NT;                        \
   if ((int)blockIdx.y >= ntiles) return;                           \
   const int nparts = min((int)gridDim.y, ntiles);                  \
   double* part = a.part + (size_t)slot * 4 * a.gy;                 \
   (void)nparts;                                                    \
+  (void)nsite;                                                     \
   (void)part;
 
 __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
@@ -239,6 +286,16 @@ __device__ __forceinline__ void reduce_partials(R (&v)[NQ], double* part, int gy
   }
 }
 
+// diagonal 1 + m + mu(x) in the kernel's arithmetic (FP32 kernels read an FP32 copy of mu)
+template <typename R>
+__device__ __forceinline__ R site_diag(const LatGeom& g, int site) {
+  return (R)g.diag0 + (g.mass_field32 ? (R)g.mass_field32[site] : (R)0);
+}
+template <>
+__device__ __forceinline__ double site_diag<double>(const LatGeom& g, int site) {
+  return 1.0 + g.mass + (g.mass_field ? g.mass_field[site] : 0.0);
+}
+
 // ---- the stencil on RPT right-hand sides per thread
 // Thread = one site; it loads (and reconstructs) each of the 8 links of the
 // site once and applies it to RPT slots of the same lattice.  Epilogues:
@@ -247,12 +304,16 @@ __device__ __forceinline__ void reduce_partials(R (&v)[NQ], double* part, int gy
 //   EPI_T      t = D s ; omega = (t, s) / (t, t)
 enum { EPI_PLAIN = 0, EPI_V = 1, EPI_T = 2 };
 
+// Grid: x = member of a slot group (RPT slots each), y = tile, z = slot group.  Blocks run in
+// index order, so a group sweeps the lattice with its slots interleaved per tile (the links of
+// a tile are read once per group) and groups follow one another (the +-t neighbours of a tile
+// are still in L2 when the sweep of a group reaches them).
 template <int SPR, int RPT, int NT, int EPI, int REC>
 __global__ void __launch_bounds__(NT) k_wds(WArgs a, FieldPtr in, FieldPtr out, int nslots) {
   typedef typename Real_of<SPR>::T R;
   constexpr int LPR = LinkPrecOf<SPR>::v;
   constexpr int NQ = EPI == EPI_V ? 2 : 3;
-  const int slot0 = blockIdx.x * RPT;
+  const int slot0 = (blockIdx.z * gridDim.x + blockIdx.x) * RPT;
   __shared__ int act_sh[RPT];
   __shared__ int lat_sh;
   if (threadIdx.x == 0) {
@@ -343,7 +404,7 @@ __global__ void __launch_bounds__(NT) k_wds(WArgs a, FieldPtr in, FieldPtr out, 
         if (mu == 3) accumulate_s<3, 1>(acc[r], w, sc);
       }
     }
-    const R diag = (R)(1.0 + g.mass + (g.mass_field ? g.mass_field[site] : 0.0));
+    const R diag = site_diag<R>(g, site);
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       if (!act[r]) continue;
@@ -456,7 +517,15 @@ __global__ void __launch_bounds__(NT) k_bicg_init(WArgs a) {
 #pragma unroll
     for (int k = 0; k < 12; ++k)
       if (k == comp) b[k] = {(R)bv.x, (R)bv.y};
-    SpinorIO<PR64>::store(FieldPtr{a.x, nullptr}, a.Vmax, slot, site, z);
+    if (SPR == PR64) {
+      SpinorIO<PR64>::store(FieldPtr{a.x, nullptr, nullptr}, a.Vmax, slot, site, z);
+    } else {
+      cplx<float> zf[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) zf[k] = {0.f, 0.f};
+      SpinorIO<PR32>::store(FieldPtr{a.xff.p, nullptr, nullptr}, a.Vmax, slot, site, zf);
+      SpinorIO<PR32>::store(FieldPtr{a.xff.lo, nullptr, nullptr}, a.Vmax, slot, site, zf);
+    }
     {
       cplx<typename Real_of<EPR>::T> ze[12];
 #pragma unroll
@@ -510,7 +579,7 @@ __global__ void __launch_bounds__(NT) k_bicg_s(WArgs a) {
   const R ax = (R)al.x, ay = (R)al.y;
   for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
     const int site = tile * NT + threadIdx.x;
-    if (site >= g.V) continue;
+    if (site >= nsite) continue;
     cplx<R> r[12], v[12];
     SpinorIO<SPR>::load(a.r, a.Vmax, slot, site, r);
     SpinorIO<SPR>::load(a.v, a.Vmax, slot, site, v);
@@ -533,7 +602,7 @@ __global__ void __launch_bounds__(NT) k_bicg_xr(WArgs a) {
   R acc[3] = {0, 0, 0};
   for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
     const int site = tile * NT + threadIdx.x;
-    if (site >= g.V) continue;
+    if (site >= nsite) continue;
     cplx<R> p[12], s[12], t[12], rh[12];
     cplx<RE> e[12];
     SpinorIO<SPR>::load(a.p, a.Vmax, slot, site, p);
@@ -643,93 +712,140 @@ __global__ void __launch_bounds__(NT) k_grp_update(WArgs a) {
   }
 }
 
-// ---- reliable update, part 1: x += e ; e = 0  (FP64)
-template <int EPR, int NT>
+// ---- reliable update, part 1: x += e ; e = 0
+// FP64 solves keep x in FP64; mixed solves keep x in float-float (hi, lo FP32 fields)
+template <int SPR, int EPR, int NT>
 __global__ void __launch_bounds__(NT) k_ru_accum(WArgs a) {
   SLOT_PREAMBLE(S->need_update)
   typedef typename Real_of<EPR>::T RE;
-  FieldPtr xf{a.x, nullptr};
   for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
     const int site = tile * NT + threadIdx.x;
-    if (site >= g.V) continue;
-    cplx<double> x[12];
+    if (site >= nsite) continue;
     cplx<RE> e[12];
-    SpinorIO<PR64>::load(xf, a.Vmax, slot, site, x);
     SpinorIO<EPR>::load(a.e, a.Vmax, slot, site, e);
+    if (SPR == PR64) {
+      FieldPtr xf{a.x, nullptr, nullptr};
+      cplx<double> x[12];
+      SpinorIO<PR64>::load(xf, a.Vmax, slot, site, x);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      x[k].x += (double)e[k].x;
-      x[k].y += (double)e[k].y;
-      e[k] = {(RE)0, (RE)0};
+      for (int k = 0; k < 12; ++k) {
+        x[k].x += (double)e[k].x;
+        x[k].y += (double)e[k].y;
+      }
+      SpinorIO<PR64>::store(xf, a.Vmax, slot, site, x);
+    } else {
+      cplx<ffl> x[12];
+      SpinorIO<PRFF>::load(a.xff, a.Vmax, slot, site, x);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        x[k].x += ffl((float)e[k].x);
+        x[k].y += ffl((float)e[k].y);
+      }
+      SpinorIO<PRFF>::store(a.xff, a.Vmax, slot, site, x);
     }
-    SpinorIO<PR64>::store(xf, a.Vmax, slot, site, x);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) e[k] = {(RE)0, (RE)0};
     SpinorIO<EPR>::store(a.e, a.Vmax, slot, site, e);
   }
 }
 
-// ---- reliable update, part 2: r = b - D x in FP64, stored in the iteration precision
+// finalize of a true residual (both arithmetics)
+__device__ __forceinline__ void ru_finalize(WArgs& a, SlotState* S, const double (&tot)[3], int slot) {
+  double rr = tot[0];
+  S->true_res2 = rr;
+  S->updates += 1;
+  S->fp64_mv += 1;
+  S->need_update = 0;
+  if (S->status == SLOT_RUN) {
+    if (rr <= a.tol2 * S->bnorm2) {
+      S->status = SLOT_DONE;
+    } else {
+      S->rnorm2 = rr;
+      S->rmax2 = rr;
+      S->rexact2 = rr;
+      S->rho = S->restart ? make_double2(rr, 0.0) : make_double2(tot[1], tot[2]);
+    }
+  }
+  a.cnt[slot] = 0;
+}
+
+// ---- reliable update, part 2: the true residual r = b - D x, stored in the iteration precision
+// (and in the FP32 group residual).  FP64 solves: FP64 links and arithmetic.  Mixed solves:
+// float-float links, solution and arithmetic on the FP32 pipes (48-bit significand: the
+// rounding error of b - D x is ~1e-14 ||b||, far below any tolerance the solver certifies).
 template <int SPR, int NT>
 __global__ void __launch_bounds__(NT) k_ru_residual(WArgs a) {
   SLOT_PREAMBLE(S->need_update == 2)
   typedef typename Real_of<SPR>::T R;
-  double acc[3] = {0.0, 0.0, 0.0};
   const int comp = S->a, m = S->m;
-  FieldPtr xf{a.x, nullptr};
-  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
-    const int site = tile * NT + threadIdx.x;
-    if (site >= g.V) continue;
-    cplx<double> o[12], c[12];
-    wilson_site<PR64, PR64, double>(g, xf, a.Vmax, slot, site, o, c);
-    double2 bv = source_value(g, site, m);
+  if (SPR == PR64) {
+    double acc[3] = {0.0, 0.0, 0.0};
+    FieldPtr xf{a.x, nullptr, nullptr};
+    for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+      const int site = tile * NT + threadIdx.x;
+      if (site >= g.V) continue;
+      cplx<double> o[12], c[12];
+      wilson_site<PR64, PR64, double>(g, xf, a.Vmax, slot, site, o, c);
+      double2 bv = source_value(g, site, m);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      o[k].x = -o[k].x;
-      o[k].y = -o[k].y;
-      if (k == comp) {
-        o[k].x += bv.x;
-        o[k].y += bv.y;
+      for (int k = 0; k < 12; ++k) {
+        o[k].x = -o[k].x;
+        o[k].y = -o[k].y;
+        if (k == comp) {
+          o[k].x += bv.x;
+          o[k].y += bv.y;
+        }
+      }
+      cplx<R> rs[12], rh[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) rs[k] = {(R)o[k].x, (R)o[k].y};
+      SpinorIO<SPR>::store(a.r, a.Vmax, slot, site, rs);
+      SpinorIO<SPR>::load(a.rh, a.Vmax, slot, site, rh);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        acc[0] += o[k].x * o[k].x + o[k].y * o[k].y;
+        acc[1] += (double)rh[k].x * o[k].x + (double)rh[k].y * o[k].y;
+        acc[2] += (double)rh[k].x * o[k].y - (double)rh[k].y * o[k].x;
       }
     }
-    cplx<R> rs[12], rh[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) rs[k] = {(R)o[k].x, (R)o[k].y};
-    SpinorIO<SPR>::store(a.r, a.Vmax, slot, site, rs);
-    if (SPR != PR64) {
+    reduce_partials<double, 3, NT>(acc, part, a.gy);
+  } else {
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+      const int site = tile * NT + threadIdx.x;
+      if (site >= g.V) continue;
+      cplx<ffl> o[12], c[12];
+      wilson_site<PRFF, PRFF, ffl>(g, a.xff, a.Vmax, slot, site, o, c);
+      double2 bv = source_value(g, site, m);
       cplx<float> rf[12];
 #pragma unroll
-      for (int k = 0; k < 12; ++k) rf[k] = {(float)o[k].x, (float)o[k].y};
-      SpinorIO<PR32>::store(a.rg, a.Vmax, slot, site, rf);
-    }
-    SpinorIO<SPR>::load(a.rh, a.Vmax, slot, site, rh);
+      for (int k = 0; k < 12; ++k) {
+        ffl rx = -o[k].x, ry = -o[k].y;
+        if (k == comp) {
+          rx += ffl(bv.x);
+          ry += ffl(bv.y);
+        }
+        rf[k] = {rx.hi, ry.hi};
+      }
+      cplx<R> rs[12], rh[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      acc[0] += o[k].x * o[k].x + o[k].y * o[k].y;
-      acc[1] += (double)rh[k].x * o[k].x + (double)rh[k].y * o[k].y;
-      acc[2] += (double)rh[k].x * o[k].y - (double)rh[k].y * o[k].x;
+      for (int k = 0; k < 12; ++k) rs[k] = {(R)rf[k].x, (R)rf[k].y};
+      SpinorIO<SPR>::store(a.r, a.Vmax, slot, site, rs);
+      SpinorIO<PR32>::store(a.rg, a.Vmax, slot, site, rf);
+      SpinorIO<SPR>::load(a.rh, a.Vmax, slot, site, rh);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        acc[0] += rf[k].x * rf[k].x + rf[k].y * rf[k].y;
+        acc[1] += (float)rh[k].x * rf[k].x + (float)rh[k].y * rf[k].y;
+        acc[2] += (float)rh[k].x * rf[k].y - (float)rh[k].y * rf[k].x;
+      }
     }
+    reduce_partials<float, 3, NT>(acc, part, a.gy);
   }
-  reduce_partials<double, 3, NT>(acc, part, a.gy);
   if (last_block(a.cnt + slot, nparts)) {
     double tot[3];
     block_sum_partials<3, NT>(part, a.gy, nparts, tot);
-    if (threadIdx.x == 0) {
-      double rr = tot[0];
-      S->true_res2 = rr;
-      S->updates += 1;
-      S->fp64_mv += 1;
-      S->need_update = 0;
-      if (S->status == SLOT_RUN) {
-        if (rr <= a.tol2 * S->bnorm2) {
-          S->status = SLOT_DONE;
-        } else {
-          S->rnorm2 = rr;
-          S->rmax2 = rr;
-          S->rexact2 = rr;
-          S->rho = S->restart ? make_double2(rr, 0.0) : make_double2(tot[1], tot[2]);
-        }
-      }
-      a.cnt[slot] = 0;
-    }
+    if (threadIdx.x == 0) ru_finalize(a, S, tot, slot);
   }
 }
 
@@ -743,7 +859,7 @@ __global__ void __launch_bounds__(NT) k_bicg_p(WArgs a) {
   const R bx = (R)be.x, by = (R)be.y, ox = (R)om.x, oy = (R)om.y;
   for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
     const int site = tile * NT + threadIdx.x;
-    if (site >= g.V) continue;
+    if (site >= nsite) continue;
     cplx<R> r[12], p[12], v[12];
     SpinorIO<SPR>::load(a.r, a.Vmax, slot, site, r);
     if (restart) {
@@ -765,17 +881,25 @@ __global__ void __launch_bounds__(NT) k_bicg_p(WArgs a) {
 }
 
 // ---- harvest: q = v^H x = sum_site conj(v(site)) x(site, a)   (FP64)
+// one component of the converged solution in FP64 (from FP64 or float-float storage)
+__device__ __forceinline__ double2 solution_component(const WArgs& a, int slot, int site, int comp) {
+  if (a.x) return a.x[((size_t)slot * 12 + comp) * a.Vmax + site];
+  const size_t off = ((size_t)slot * 6 + comp / 2) * a.Vmax + site;
+  const float4 h = ((const float4*)a.xff.p)[off], l = ((const float4*)a.xff.lo)[off];
+  return (comp & 1) ? make_double2((double)h.z + (double)l.z, (double)h.w + (double)l.w)
+                    : make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+}
+
 template <int NT>
 __global__ void __launch_bounds__(NT) k_quad(WArgs a) {
   SLOT_PREAMBLE(S->status == SLOT_DONE || S->status == SLOT_FAIL)
   double acc[2] = {0.0, 0.0};
   const int comp = S->a, m = S->m;
-  const double2* x = a.x + ((size_t)slot * 12 + comp) * a.Vmax;
   for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
     const int site = tile * NT + threadIdx.x;
     if (site >= g.V) continue;
     double2 bv = source_value(g, site, m);
-    double2 xv = x[site];
+    const double2 xv = solution_component(a, slot, site, comp);
     acc[0] += bv.x * xv.x + bv.y * xv.y;
     acc[1] += bv.x * xv.y - bv.y * xv.x;
   }
@@ -800,11 +924,472 @@ __global__ void k_w_grad(WArgs a, int lat, const int* __restrict__ slots, int ns
       const SlotState* S = a.st + slot;
       if (S->lat != lat) continue;
       const double sa = S->a < 6 ? 1.0 : -1.0;
-      const double2* x = a.x + (size_t)slot * 12 * a.Vmax + site;
       double t = 0.0;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        double2 v = x[(size_t)k * a.Vmax];
+        const double2 v = solution_component(a, slot, site, k);
+        t += (k < 6 ? 1.0 : -1.0) * (v.x * v.x + v.y * v.y);
+      }
+      acc += sa * t;
+    }
+    grad[site] += acc;
+  }
+}
+
+// ============================================================= even-odd (Schur)
+// With d(x) = 1 + m + mu(x) and H the hopping term, D = [[d_e, -k H_eo], [-k H_oe, d_o]].
+// The odd-site Schur complement  S = d_o - k^2 H_oe d_e^-1 H_eo  is solved for x_o; the even
+// half follows as x_e = d_e^-1 (b_e + k H_eo x_o), and then the odd part of the full residual
+// is  r_o = b_o - d_o x_o + k H_oe x_e  while the even part vanishes by construction: the
+// certified residual is the residual of the full system.  Sites of one parity are numbered
+// by site >> 1 (needs L_1 even).
+enum { MASK_RUN = 0, MASK_GROUP = 1, MASK_EXACT = 2 };
+
+__device__ __forceinline__ bool eo_mask(const SlotState* S, int mask) {
+  if (mask == MASK_RUN) return S->status == SLOT_RUN;
+  if (mask == MASK_GROUP) return S->need_update == 1;
+  return S->need_update == 2;
+}
+
+// full index and coordinates of half-site h of parity `par`
+__device__ __forceinline__ int eo_site(const LatGeom& g, int h, int par, int (&x)[4], int (&st)[4]) {
+  const int l1h = g.L[0] >> 1;
+  const int x1h = h % l1h;
+  int rest = h / l1h;
+  x[1] = rest % g.L[1];
+  rest /= g.L[1];
+  x[2] = rest % g.L[2];
+  x[3] = rest / g.L[2];
+  x[0] = 2 * x1h + ((par + x[1] + x[2] + x[3]) & 1);
+  st[0] = 1;
+  st[1] = g.L[0];
+  st[2] = g.L[0] * g.L[1];
+  st[3] = st[2] * g.L[2];
+  return x[0] + st[1] * x[1] + st[2] * x[2] + st[3] * x[3];
+}
+
+// acc += sc * hop(in) at full site `site`, `in` a half-lattice field of the other parity
+template <int SPR, int LPR, int REC, typename R>
+__device__ __forceinline__ void eo_hop(const LatGeom& g, FieldPtr in, int Vs, int slot, int site, const int (&x)[4],
+                                       const int (&st)[4], R sc, cplx<R> (&acc)[12]) {
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    const int L = g.L[mu];
+    const int fw = (x[mu] + 1 == L) ? site - (L - 1) * st[mu] : site + st[mu];
+    const int bw = (x[mu] == 0) ? site + (L - 1) * st[mu] : site - st[mu];
+    cplx<R> u[9], psi[12], h[6], w[6];
+    R n;
+    LinkIO<LPR, REC>::load(g, mu, site, u);
+    SpinorIO<SPR>::load_nc_raw(in, Vs, slot, fw >> 1, psi, n);
+    if (mu == 0) project<0, -1>(psi, h);
+    if (mu == 1) project<1, -1>(psi, h);
+    if (mu == 2) project<2, -1>(psi, h);
+    if (mu == 3) project<3, -1>(psi, h);
+    su3_mul<R, false>(u, h, w);
+    if (mu == 0) accumulate_s<0, -1>(acc, w, sc * n);
+    if (mu == 1) accumulate_s<1, -1>(acc, w, sc * n);
+    if (mu == 2) accumulate_s<2, -1>(acc, w, sc * n);
+    if (mu == 3) accumulate_s<3, -1>(acc, w, sc * n);
+    LinkIO<LPR, REC>::load(g, mu, bw, u);
+    SpinorIO<SPR>::load_nc_raw(in, Vs, slot, bw >> 1, psi, n);
+    if (mu == 0) project<0, 1>(psi, h);
+    if (mu == 1) project<1, 1>(psi, h);
+    if (mu == 2) project<2, 1>(psi, h);
+    if (mu == 3) project<3, 1>(psi, h);
+    su3_mul<R, true>(u, h, w);
+    if (mu == 0) accumulate_s<0, 1>(acc, w, sc * n);
+    if (mu == 1) accumulate_s<1, 1>(acc, w, sc * n);
+    if (mu == 2) accumulate_s<2, 1>(acc, w, sc * n);
+    if (mu == 3) accumulate_s<3, 1>(acc, w, sc * n);
+  }
+}
+
+__device__ __forceinline__ double leading_part(double v) { return v; }
+__device__ __forceinline__ double leading_part(ffl v) { return (double)v.hi; }
+
+// slot of a stencil block (same grid as k_wds, one slot per block)
+#define EO_PREAMBLE(MASK)                                                 \
+  const int slot = blockIdx.z * gridDim.x + blockIdx.x;                   \
+  if (slot >= nslots) return;                                             \
+  SlotState* S = a.st + slot;                                             \
+  if (!eo_mask(S, MASK)) return;                                          \
+  const LatGeom g = a.lats[S->lat];                                       \
+  const int nsite = g.V >> 1;                                             \
+  const int ntiles = (nsite + NT - 1) / NT;                               \
+  if ((int)blockIdx.y >= ntiles) return;                                  \
+  const int nparts = min((int)gridDim.y, ntiles);                         \
+  double* part = a.part + (size_t)slot * 4 * a.gy;                        \
+  (void)nparts;                                                           \
+  (void)part;
+
+// ---- even sites: mid = d_e^-1 hop(in_o)
+template <int SIN, int LPR, int REC, int SOUT, int NT, int MASK>
+__global__ void __launch_bounds__(NT) k_eo_even(WArgs a, FieldPtr in, FieldPtr mid, int nslots) {
+  EO_PREAMBLE(MASK)
+  typedef float R;
+  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+    const int h = tile * NT + threadIdx.x;
+    if (h >= nsite) continue;
+    int x[4], st[4];
+    const int site = eo_site(g, h, 0, x, st);
+    const R inv = (R)1 / site_diag<R>(g, site);
+    cplx<R> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = {(R)0, (R)0};
+    eo_hop<SIN, LPR, REC, R>(g, in, a.Vmax, slot, site, x, st, inv, acc);
+    SpinorIO<SOUT>::store(mid, a.Vmax, slot, h, acc);
+  }
+}
+
+// ---- odd sites: out = d_o in - k^2 hop(mid), with the solver epilogues
+//   EPI_V: v = S p, (r^, v), alpha       EPI_T: t = S s, (t, s), (t, t), omega
+//   EPI_G: group update r_g -= S e, r = r_g, (r^, r_g), ||r_g||^2   (in = e, mid FP32)
+enum { EPI_G = 3 };
+
+template <int SIN, int SMID, int LPR, int REC, int NT, int EPI>
+__global__ void __launch_bounds__(NT) k_eo_odd(WArgs a, FieldPtr in, FieldPtr mid, FieldPtr out, int nslots) {
+  EO_PREAMBLE(EPI == EPI_G ? MASK_GROUP : MASK_RUN)
+  typedef float R;
+  constexpr int NQ = EPI == EPI_V ? 2 : 3;
+  R dots[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) dots[q] = (R)0;
+  const R mk2 = -(R)(g.kappa * g.kappa);
+  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+    const int h = tile * NT + threadIdx.x;
+    if (h >= nsite) continue;
+    int x[4], st[4];
+    const int site = eo_site(g, h, 1, x, st);
+    cplx<R> acc[12], c[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = {(R)0, (R)0};
+    eo_hop<SMID, LPR, REC, R>(g, mid, a.Vmax, slot, site, x, st, mk2, acc);
+    R nc;
+    SpinorIO<SIN>::load_nc_raw(in, a.Vmax, slot, h, c, nc);
+    const R dn = site_diag<R>(g, site) * nc;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      acc[k].x = fma(dn, c[k].x, acc[k].x);
+      acc[k].y = fma(dn, c[k].y, acc[k].y);
+    }
+    if (EPI == EPI_G) {
+      cplx<R> rg[12], rh[12];
+      SpinorIO<PR32>::load(a.rg, a.Vmax, slot, h, rg);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        rg[k].x -= acc[k].x;
+        rg[k].y -= acc[k].y;
+      }
+      SpinorIO<PR32>::store(a.rg, a.Vmax, slot, h, rg);
+      SpinorIO<SIN>::store(a.r, a.Vmax, slot, h, rg);
+      SpinorIO<SIN>::load(a.rh, a.Vmax, slot, h, rh);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        dots[0] += rg[k].x * rg[k].x + rg[k].y * rg[k].y;
+        dots[1] += rh[k].x * rg[k].x + rh[k].y * rg[k].y;
+        dots[2 % NQ] += rh[k].x * rg[k].y - rh[k].y * rg[k].x;
+      }
+      continue;
+    }
+    SpinorIO<SIN>::store(out, a.Vmax, slot, h, acc);
+    if (EPI == EPI_V) {
+      cplx<R> rh[12];
+      SpinorIO<SIN>::load(a.rh, a.Vmax, slot, h, rh);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        cplx<R> d = cconjmul(rh[k], acc[k]);
+        dots[0] += d.x;
+        dots[1] += d.y;
+      }
+    } else {
+      R d0 = 0, d1 = 0;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        cplx<R> d = cconjmul(acc[k], c[k]);
+        d0 += d.x;
+        d1 += d.y;
+        dots[2 % NQ] += acc[k].x * acc[k].x + acc[k].y * acc[k].y;
+      }
+      dots[0] += nc * d0;
+      dots[1] += nc * d1;
+    }
+  }
+  reduce_partials<R, NQ, NT>(dots, part, a.gy);
+  if (last_block(a.cnt + slot, nparts)) {
+    double tot[NQ];
+    block_sum_partials<NQ, NT>(part, a.gy, nparts, tot);
+    if (threadIdx.x == 0) {
+      if (EPI == EPI_V) {
+        S->alpha = cdiv(S->rho, make_double2(tot[0], tot[1]));
+        S->restart = 0;
+        if (S->need_update == 3) S->need_update = 0;
+        S->sloppy_mv += 1;
+      } else if (EPI == EPI_T) {
+        S->omega = tot[NQ - 1] > 0.0 ? make_double2(tot[0] / tot[NQ - 1], tot[1] / tot[NQ - 1]) : make_double2(0.0, 0.0);
+        S->sloppy_mv += 1;
+      } else {
+        const double rr = tot[0];
+        S->rnorm2 = rr;
+        S->rmax2 = rr;
+        S->rho = S->restart ? make_double2(rr, 0.0) : make_double2(tot[1], tot[2]);
+        S->gupdates += 1;
+        S->need_update = (rr <= a.tol2 * S->bnorm2 || rr < a.epsx2 * S->rexact2) ? 2 : 3;
+      }
+      a.cnt[slot] = 0;
+    }
+  }
+}
+
+// ---- exact step 1: x_e = d_e^-1 (b_e + k hop(x_o))   (FP64 or float-float)
+template <int PX, int NT>
+__global__ void __launch_bounds__(NT) k_eo_x1(WArgs a, int nslots) {
+  EO_PREAMBLE(MASK_EXACT)
+  typedef typename Real_of<PX>::T R;
+  const int comp = S->a, m = S->m;
+  FieldPtr xo = PX == PR64 ? FieldPtr{a.x, nullptr, nullptr} : a.xff;
+  FieldPtr xe = PX == PR64 ? FieldPtr{a.xe, nullptr, nullptr} : a.xeff;
+  const R kap = R(g.kappa);
+  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+    const int h = tile * NT + threadIdx.x;
+    if (h >= nsite) continue;
+    int x[4], st[4];
+    const int site = eo_site(g, h, 0, x, st);
+    cplx<R> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
+    eo_hop<PX, PX, 12, R>(g, xo, a.Vmax, slot, site, x, st, kap, acc);
+    const double2 bv = source_value(g, site, m);
+    const R inv = R(1.0 / (1.0 + g.mass + (g.mass_field ? g.mass_field[site] : 0.0)));
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      if (k == comp) {
+        acc[k].x = acc[k].x + R(bv.x);
+        acc[k].y = acc[k].y + R(bv.y);
+      }
+      acc[k].x = inv * acc[k].x;
+      acc[k].y = inv * acc[k].y;
+    }
+    SpinorIO<PX>::store(xe, a.Vmax, slot, h, acc);
+  }
+}
+
+// ---- exact step 2: r_o = b_o - d_o x_o + k hop(x_e); a fresh slot also sets r^ = p = r
+template <int SPR, int PX, int NT>
+__global__ void __launch_bounds__(NT) k_eo_x2(WArgs a, int nslots) {
+  EO_PREAMBLE(MASK_EXACT)
+  typedef typename Real_of<PX>::T R;
+  typedef typename Real_of<SPR>::T RS;
+  const int comp = S->a, m = S->m;
+  const bool fresh = S->restart == 2;
+  FieldPtr xo = PX == PR64 ? FieldPtr{a.x, nullptr, nullptr} : a.xff;
+  FieldPtr xe = PX == PR64 ? FieldPtr{a.xe, nullptr, nullptr} : a.xeff;
+  const R kap = R(g.kappa);
+  float acc3[3] = {0.f, 0.f, 0.f};
+  double accd[3] = {0.0, 0.0, 0.0};
+  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+    const int h = tile * NT + threadIdx.x;
+    if (h >= nsite) continue;
+    int x[4], st[4];
+    const int site = eo_site(g, h, 1, x, st);
+    cplx<R> acc[12], c[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
+    eo_hop<PX, PX, 12, R>(g, xe, a.Vmax, slot, site, x, st, kap, acc);
+    SpinorIO<PX>::load_nc(xo, a.Vmax, slot, h, c);
+    const R d = R(1.0 + g.mass + (g.mass_field ? g.mass_field[site] : 0.0));
+    const double2 bv = source_value(g, site, m);
+    cplx<RS> rs[12];
+    cplx<float> rf[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      R rx = acc[k].x - d * c[k].x, ry = acc[k].y - d * c[k].y;
+      if (k == comp) {
+        rx = rx + R(bv.x);
+        ry = ry + R(bv.y);
+      }
+      const double dx = leading_part(rx), dy = leading_part(ry);
+      rs[k] = {(RS)dx, (RS)dy};
+      rf[k] = {(float)dx, (float)dy};
+    }
+    SpinorIO<SPR>::store(a.r, a.Vmax, slot, h, rs);
+    if (PX != PR64) SpinorIO<PR32>::store(a.rg, a.Vmax, slot, h, rf);
+    if (fresh) {
+      SpinorIO<SPR>::store(a.rh, a.Vmax, slot, h, rs);
+      SpinorIO<SPR>::store(a.p, a.Vmax, slot, h, rs);
+    }
+    cplx<RS> rh[12];
+    SpinorIO<SPR>::load(a.rh, a.Vmax, slot, h, rh);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      if (PX == PR64) {
+        accd[0] += (double)rs[k].x * rs[k].x + (double)rs[k].y * rs[k].y;
+        accd[1] += (double)rh[k].x * rs[k].x + (double)rh[k].y * rs[k].y;
+        accd[2] += (double)rh[k].x * rs[k].y - (double)rh[k].y * rs[k].x;
+      } else {
+        acc3[0] += rf[k].x * rf[k].x + rf[k].y * rf[k].y;
+        acc3[1] += (float)rh[k].x * rf[k].x + (float)rh[k].y * rf[k].y;
+        acc3[2] += (float)rh[k].x * rf[k].y - (float)rh[k].y * rf[k].x;
+      }
+    }
+  }
+  if (PX == PR64) reduce_partials<double, 3, NT>(accd, part, a.gy);
+  else reduce_partials<float, 3, NT>(acc3, part, a.gy);
+  if (last_block(a.cnt + slot, nparts)) {
+    double tot[3];
+    block_sum_partials<3, NT>(part, a.gy, nparts, tot);
+    if (threadIdx.x == 0) {
+      if (fresh) {   // initial residual of the Schur system: start the iteration from it
+        S->restart = 0;
+        S->need_update = 0;
+        S->rnorm2 = S->rmax2 = S->rexact2 = tot[0];
+        S->rho = make_double2(tot[0], 0.0);
+        S->true_res2 = tot[0];
+        if (!(tot[0] > a.tol2 * S->bnorm2)) S->status = SLOT_DONE;
+        a.cnt[slot] = 0;
+      } else {
+        ru_finalize(a, S, tot, slot);
+      }
+    }
+  }
+}
+
+// ---- init: x_o = 0, e = 0, ||b||^2 over the whole lattice; the exact steps then set
+// x_e = d_e^-1 b_e and r = r^ = p = b_o + k H_oe x_e
+template <int SPR, int EPR, int NT>
+__global__ void __launch_bounds__(NT) k_eo_init(WArgs a, int nslots) {
+  const int slot = blockIdx.x;
+  if (slot >= nslots) return;
+  SlotState* S = a.st + slot;
+  if (S->status != SLOT_INIT) return;
+  const LatGeom g = a.lats[S->lat];
+  const int ntiles = (g.V + NT - 1) / NT;
+  if ((int)blockIdx.y >= ntiles) return;
+  const int nparts = min((int)gridDim.y, ntiles);
+  double* part = a.part + (size_t)slot * 4 * a.gy;
+  const int m = S->m;
+  double acc[1] = {0.0};
+  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+    const int site = tile * NT + threadIdx.x;
+    if (site >= g.V) continue;
+    const double2 bv = source_value(g, site, m);
+    acc[0] += bv.x * bv.x + bv.y * bv.y;
+    const int h = site >> 1;
+    int r = site, par = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      par += r % g.L[j];
+      r /= g.L[j];
+    }
+    if ((par & 1) == 0) continue;   // odd sites carry the Krylov vectors
+    cplx<typename Real_of<EPR>::T> ze[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) ze[k] = {0, 0};
+    SpinorIO<EPR>::store(a.e, a.Vmax, slot, h, ze);
+    if (SPR == PR64) {
+      cplx<double> z[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) z[k] = {0.0, 0.0};
+      SpinorIO<PR64>::store(FieldPtr{a.x, nullptr, nullptr}, a.Vmax, slot, h, z);
+    } else {
+      cplx<float> z[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) z[k] = {0.f, 0.f};
+      SpinorIO<PR32>::store(FieldPtr{a.xff.p, nullptr, nullptr}, a.Vmax, slot, h, z);
+      SpinorIO<PR32>::store(FieldPtr{a.xff.lo, nullptr, nullptr}, a.Vmax, slot, h, z);
+    }
+  }
+  reduce_partials<double, 1, NT>(acc, part, a.gy);
+  if (last_block(a.cnt + slot, nparts)) {
+    double tot[1];
+    block_sum_partials<1, NT>(part, a.gy, nparts, tot);
+    if (threadIdx.x == 0) {
+      S->bnorm2 = tot[0];
+      S->alpha = make_double2(1.0, 0.0);
+      S->omega = make_double2(1.0, 0.0);
+      S->beta = make_double2(0.0, 0.0);
+      S->iters = 0;
+      S->updates = 0;
+      S->sloppy_mv = 0;
+      S->fp64_mv = 0;
+      S->gupdates = 0;
+      S->restart = 2;          // fresh: the exact steps below produce the initial residual
+      S->need_update = 2;
+      S->status = tot[0] > 0.0 ? SLOT_RUN : SLOT_DONE;
+      a.cnt[slot] = 0;
+    }
+  }
+}
+
+// one component of the converged solution at a full site, from the parity fields
+__device__ __forceinline__ double2 eo_solution_component(const WArgs& a, int slot, int site, int par, int comp) {
+  const int h = site >> 1;
+  if (a.x) {
+    const double2* f = par ? a.x : a.xe;
+    return f[((size_t)slot * 12 + comp) * a.Vmax + h];
+  }
+  const FieldPtr f = par ? a.xff : a.xeff;
+  const size_t off = ((size_t)slot * 6 + comp / 2) * a.Vmax + h;
+  const float4 hi = ((const float4*)f.p)[off], lo = ((const float4*)f.lo)[off];
+  return (comp & 1) ? make_double2((double)hi.z + (double)lo.z, (double)hi.w + (double)lo.w)
+                    : make_double2((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y);
+}
+
+__device__ __forceinline__ int site_parity(const LatGeom& g, int site) {
+  int r = site, par = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    par += r % g.L[j];
+    r /= g.L[j];
+  }
+  return par & 1;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_eo_quad(WArgs a, int nslots) {
+  const int slot = blockIdx.x;
+  if (slot >= nslots) return;
+  SlotState* S = a.st + slot;
+  if (!(S->status == SLOT_DONE || S->status == SLOT_FAIL)) return;
+  const LatGeom g = a.lats[S->lat];
+  const int ntiles = (g.V + NT - 1) / NT;
+  if ((int)blockIdx.y >= ntiles) return;
+  const int nparts = min((int)gridDim.y, ntiles);
+  double* part = a.part + (size_t)slot * 4 * a.gy;
+  double acc[2] = {0.0, 0.0};
+  const int comp = S->a, m = S->m;
+  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+    const int site = tile * NT + threadIdx.x;
+    if (site >= g.V) continue;
+    const double2 bv = source_value(g, site, m);
+    const double2 xv = eo_solution_component(a, slot, site, site_parity(g, site), comp);
+    acc[0] += bv.x * xv.x + bv.y * xv.y;
+    acc[1] += bv.x * xv.y - bv.y * xv.x;
+  }
+  reduce_partials<double, 2, NT>(acc, part, a.gy);
+  if (last_block(a.cnt + slot, nparts)) {
+    double tot[2];
+    block_sum_partials<2, NT>(part, a.gy, nparts, tot);
+    if (threadIdx.x == 0) {
+      S->q = make_double2(tot[0], tot[1]);
+      a.cnt[slot] = 0;
+    }
+  }
+}
+
+__global__ void k_eo_grad(WArgs a, int lat, const int* __restrict__ slots, int nsl, double* __restrict__ grad,
+                          LatGeom g) {
+  for (int site = blockIdx.x * blockDim.x + threadIdx.x; site < g.V; site += gridDim.x * blockDim.x) {
+    const int par = site_parity(g, site);
+    double acc = 0.0;
+    for (int i = 0; i < nsl; ++i) {
+      const int slot = slots[i];
+      const SlotState* S = a.st + slot;
+      if (S->lat != lat) continue;
+      const double sa = S->a < 6 ? 1.0 : -1.0;
+      double t = 0.0;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const double2 v = eo_solution_component(a, slot, site, par, k);
         t += (k < 6 ? 1.0 : -1.0) * (v.x * v.x + v.y * v.y);
       }
       acc += sa * t;
@@ -823,12 +1408,17 @@ template <int SPR>
 struct WilsonEngine {
   static constexpr int EPR = SPR;      // solution increment e kept in the iteration precision
   static constexpr int NT = 128;
-  static constexpr int KERNELS_PER_ITERATION = SPR == PR64 ? 7 : 8;
   static constexpr int GROUP_MAX = 4;
+  static constexpr int PX = SPR == PR64 ? PR64 : PRFF;   // arithmetic of the true residual
   hp_ctx* ctx;
+  bool eo = false;     // even-odd (Schur complement) iteration; set before setup
   WArgs a;
-  int nslots, gy, rpt = 1, variant = 10;
-  dim3 grid() const { return dim3(nslots, gy); }
+  int nslots, gy, gyb, rpt = 1, variant = 10;
+  int kernels_per_iteration() const { return eo ? (SPR == PR64 ? 10 : 12) : (SPR == PR64 ? 7 : 8); }
+  // streaming kernels: grid-stride with 8 blocks per SM per slot (few partial sums and atomic tickets);
+  // stencil kernels: one block per tile (gy) so that the lattice is swept once in site order
+  dim3 grid() const { return dim3(nslots, gyb); }
+  dim3 grid_stencil() const { return dim3(nslots, gy); }
   int group() const { return rpt; }
 
   hp_status setup(int ns, int Vmax, const LatGeom* lats_dev, SlotState* st, const hp_solver_opts& o, double tol,
@@ -837,9 +1427,12 @@ struct WilsonEngine {
     memset(&a, 0, sizeof(a));
     a.lats = lats_dev;
     a.st = st;
+    a.eo = eo ? 1 : 0;
+    if (eo) Vmax = (Vmax + 1) / 2;   // every field lives on one parity
     a.Vmax = Vmax;
     gy = dslash_gridy(ctx, Vmax, NT, ns);
-    a.gy = gy;
+    gyb = std::max(1, std::min(gy, ctx->num_sms * 8));
+    a.gy = gy;   // stride of the partial sums: the largest grid height of any kernel
     void* p = nullptr;
     HP_TRY(hp_ws(ctx, "solve.part", sizeof(double) * 4 * (size_t)ns * gy, &p));
     a.part = (double*)p;
@@ -854,8 +1447,28 @@ struct WilsonEngine {
     HP_TRY(alloc_field(ctx, "solve.t", SPR, ns, Vmax, &a.t));
     HP_TRY(alloc_field(ctx, "solve.e", EPR, ns, Vmax, &a.e));
     if (SPR != PR64) HP_TRY(alloc_field(ctx, "solve.rg", PR32, ns, Vmax, &a.rg));
-    HP_TRY(hp_ws(ctx, "solve.x", sizeof(double2) * 12 * (size_t)ns * Vmax, &p));
-    a.x = (double2*)p;
+    if (SPR == PR64) {
+      HP_TRY(hp_ws(ctx, "solve.x", sizeof(double2) * 12 * (size_t)ns * Vmax, &p));
+      a.x = (double2*)p;
+      if (eo) {
+        HP_TRY(hp_ws(ctx, "solve.xe", sizeof(double2) * 12 * (size_t)ns * Vmax, &p));
+        a.xe = (double2*)p;
+      }
+    } else {   // float-float solution
+      HP_TRY(alloc_field(ctx, "solve.xhi", PR32, ns, Vmax, &a.xff));
+      FieldPtr lo;
+      HP_TRY(alloc_field(ctx, "solve.xlo", PR32, ns, Vmax, &lo));
+      a.xff.lo = lo.p;
+      if (eo) {
+        HP_TRY(alloc_field(ctx, "solve.xehi", PR32, ns, Vmax, &a.xeff));
+        HP_TRY(alloc_field(ctx, "solve.xelo", PR32, ns, Vmax, &lo));
+        a.xeff.lo = lo.p;
+      }
+    }
+    if (eo) {
+      HP_TRY(alloc_field(ctx, "solve.mid", SPR, ns, Vmax, &a.mid));
+      if (SPR != PR64) HP_TRY(alloc_field(ctx, "solve.mid32", PR32, ns, Vmax, &a.mid32));
+    }
     a.tol2 = tol * tol;
     a.delta2 = delta * delta;
     a.epsx2 = SPR == PR64 ? 0.0 : 1e-10;   // FP64 true residual after a 1e5 reduction
@@ -863,20 +1476,73 @@ struct WilsonEngine {
     // right-hand sides per thread of the stencil: fixed by the caller or autotuned on the largest lattice
     // stencil variant: fixed by the caller (right-hand sides per thread, 12-real links) or autotuned
     // on the largest lattice of the problem
-    const int forced = o.rhs_per_thread % 100, full = o.rhs_per_thread >= 100;
+    const int forced = o.rhs_per_thread % 100, full = (o.rhs_per_thread / 100) % 10 == 1,
+              group = o.rhs_per_thread / 1000;
     if (forced == 1 || forced == 2 || forced == 4) {
-      variant = 10 * forced + (full ? 1 : 0);
+      variant = 100 * group + 10 * forced + (full ? 1 : 0);
+    } else if (eo) {
+      // the full-lattice tuner cannot run on half-lattice fields: slot groups of 4 and 18-real links
+      variant = 411;
     } else {
       k_w_fill<SPR><<<blocks_for(ctx, (long long)ns * Vmax, 256), 256, 0, ctx->stream>>>(a.p, Vmax, ns, 777ull);
       HP_LAUNCH_CHECK();
       HP_TRY(tune_rpt<SPR>(ctx, gbig, a.p, a.v, ns, Vmax, &variant));
     }
     rpt = variant_rpt(variant);
+    if (eo) {   // the even-odd kernels take one right-hand side per thread; keep the group and link form
+      variant = 100 * variant_group(variant) + 10 + (variant % 10);
+      rpt = 1;
+    }
+    return HP_OK;
+  }
+  // ---- even-odd steps
+  template <int REC>
+  hp_status eo_schur(int which) {   // which: 0 v = S p, 1 t = S s, 2 group update with e
+    dim3 gr = stencil_grid(variant, nslots, gy);
+    constexpr int LPR = LinkPrecOf<SPR>::v;
+    if (which == 0) {
+      ProfScope ps(ctx, "k_eo_even");
+      k_eo_even<SPR, LPR, REC, SPR, NT, MASK_RUN><<<gr, NT, 0, ctx->stream>>>(a, a.p, a.mid, nslots);
+      HP_LAUNCH_CHECK();
+      ProfScope ps2(ctx, SPR == PR64 ? "k_eo_odd_v<fp64>" : SPR == PR32 ? "k_eo_odd_v<fp32>" : SPR == PR16 ? "k_eo_odd_v<fp16>" : "k_eo_odd_v<bf16>");
+      k_eo_odd<SPR, SPR, LPR, REC, NT, EPI_V><<<gr, NT, 0, ctx->stream>>>(a, a.p, a.mid, a.v, nslots);
+    } else if (which == 1) {
+      ProfScope ps(ctx, "k_eo_even");
+      k_eo_even<SPR, LPR, REC, SPR, NT, MASK_RUN><<<gr, NT, 0, ctx->stream>>>(a, a.s, a.mid, nslots);
+      HP_LAUNCH_CHECK();
+      ProfScope ps2(ctx, SPR == PR64 ? "k_eo_odd_t<fp64>" : SPR == PR32 ? "k_eo_odd_t<fp32>" : SPR == PR16 ? "k_eo_odd_t<fp16>" : "k_eo_odd_t<bf16>");
+      k_eo_odd<SPR, SPR, LPR, REC, NT, EPI_T><<<gr, NT, 0, ctx->stream>>>(a, a.s, a.mid, a.t, nslots);
+    } else if (SPR != PR64) {
+      ProfScope ps(ctx, "k_eo_even<grp>");
+      k_eo_even<EPR, PR32, 12, PR32, NT, MASK_GROUP><<<gr, NT, 0, ctx->stream>>>(a, a.e, a.mid32, nslots);
+      HP_LAUNCH_CHECK();
+      ProfScope ps2(ctx, "k_eo_odd<grp>");
+      k_eo_odd<EPR, PR32, PR32, 12, NT, EPI_G><<<gr, NT, 0, ctx->stream>>>(a, a.e, a.mid32, a.rg, nslots);
+    }
+    HP_LAUNCH_CHECK();
+    return HP_OK;
+  }
+  hp_status eo_step(int which) {
+    const bool full = variant_rec(variant) == 18 && SPR != PR64;
+    return full ? eo_schur<18>(which) : eo_schur<12>(which);
+  }
+  hp_status eo_exact() {
+    dim3 gr = stencil_grid(variant, nslots, gy);
+    {
+      ProfScope ps(ctx, PX == PR64 ? "k_eo_x1<fp64>" : "k_eo_x1<ff>");
+      k_eo_x1<PX, NT><<<gr, NT, 0, ctx->stream>>>(a, nslots);
+    }
+    HP_LAUNCH_CHECK();
+    {
+      ProfScope ps(ctx, PX == PR64 ? "k_eo_x2<fp64>" : "k_eo_x2<ff>");
+      k_eo_x2<SPR, PX, NT><<<gr, NT, 0, ctx->stream>>>(a, nslots);
+    }
+    HP_LAUNCH_CHECK();
     return HP_OK;
   }
   template <int RPT, int REC>
   hp_status stencil_steps_rpt(int which) {
-    dim3 gr((nslots + RPT - 1) / RPT, gy);
+    dim3 gr = stencil_grid(variant, nslots, gy);
     if (which == 0) {
       ProfScope ps(ctx, SPR == PR64 ? "k_bicg_v<fp64>" : SPR == PR32 ? "k_bicg_v<fp32>" : SPR == PR16 ? "k_bicg_v<fp16>" : "k_bicg_v<bf16>");
       k_wds<SPR, RPT, NT, EPI_V, REC><<<gr, NT, 0, ctx->stream>>>(a, a.p, a.v, nslots);
@@ -894,6 +1560,14 @@ struct WilsonEngine {
     return full ? stencil_steps_rpt<1, 18>(which) : stencil_steps_rpt<1, 12>(which);
   }
   hp_status init() {
+    if (eo) {
+      {
+        ProfScope ps(ctx, "k_eo_init");
+        k_eo_init<SPR, EPR, NT><<<grid(), NT, 0, ctx->stream>>>(a, nslots);
+      }
+      HP_LAUNCH_CHECK();
+      return eo_exact();   // x_e = d_e^-1 b_e and the initial residual of the Schur system
+    }
     {
       ProfScope ps(ctx, "k_bicg_init");
       k_bicg_init<SPR, EPR, NT><<<grid(), NT, 0, ctx->stream>>>(a);
@@ -902,21 +1576,55 @@ struct WilsonEngine {
     return HP_OK;
   }
   hp_status iteration() {
+    if (eo) {
+      HP_TRY(eo_step(0));
+      { ProfScope ps(ctx, "k_bicg_s"); k_bicg_s<SPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
+      HP_TRY(eo_step(1));
+      { ProfScope ps(ctx, "k_bicg_xr"); k_bicg_xr<SPR, EPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
+      if (SPR != PR64) HP_TRY(eo_step(2));
+      { ProfScope ps(ctx, "k_ru_accum"); k_ru_accum<SPR, EPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
+      HP_TRY(eo_exact());
+      { ProfScope ps(ctx, "k_bicg_p"); k_bicg_p<SPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
+      HP_LAUNCH_CHECK();
+      return HP_OK;
+    }
     HP_TRY(stencil_step(0));
     { ProfScope ps(ctx, "k_bicg_s"); k_bicg_s<SPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
     HP_TRY(stencil_step(1));
     { ProfScope ps(ctx, "k_bicg_xr"); k_bicg_xr<SPR, EPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
     if (SPR != PR64) {
       ProfScope ps(ctx, "k_grp_update");
-      k_grp_update<SPR, EPR, NT><<<grid(), NT, 0, ctx->stream>>>(a);
+      k_grp_update<SPR, EPR, NT><<<grid_stencil(), NT, 0, ctx->stream>>>(a);
     }
-    { ProfScope ps(ctx, "k_ru_accum"); k_ru_accum<EPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
-    { ProfScope ps(ctx, "k_ru_residual<fp64>"); k_ru_residual<SPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
+    { ProfScope ps(ctx, "k_ru_accum"); k_ru_accum<SPR, EPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
+    {
+      ProfScope ps(ctx, SPR == PR64 ? "k_ru_residual<fp64>" : "k_ru_residual<ff>");
+      k_ru_residual<SPR, NT><<<grid_stencil(), NT, 0, ctx->stream>>>(a);
+    }
     { ProfScope ps(ctx, "k_bicg_p"); k_bicg_p<SPR, NT><<<grid(), NT, 0, ctx->stream>>>(a); }
     HP_LAUNCH_CHECK();
     return HP_OK;
   }
   hp_status harvest(const std::vector<int>& done_slots, const SolveProblem& pb, int* dev_slots) {
+    if (eo) {
+      {
+        ProfScope ps(ctx, "k_quad");
+        k_eo_quad<NT><<<grid(), NT, 0, ctx->stream>>>(a, nslots);
+      }
+      HP_LAUNCH_CHECK();
+      if (pb.want_grad && !done_slots.empty()) {
+        HP_CUDA(cudaMemcpyAsync(dev_slots, done_slots.data(), sizeof(int) * done_slots.size(),
+                                cudaMemcpyHostToDevice, ctx->stream));
+        for (size_t L = 0; L < pb.lats.size(); ++L) {
+          ProfScope ps(ctx, "k_w_grad");
+          k_eo_grad<<<blocks_for(ctx, pb.lats[L].V, 256), 256, 0, ctx->stream>>>(a, (int)L, dev_slots,
+                                                                                  (int)done_slots.size(),
+                                                                                  pb.grad_dev[L], pb.lats[L]);
+        }
+        HP_LAUNCH_CHECK();
+      }
+      return HP_OK;
+    }
     {
       ProfScope ps(ctx, "k_quad");
       k_quad<NT><<<grid(), NT, 0, ctx->stream>>>(a);
@@ -970,9 +1678,10 @@ __global__ void k_w_to_canonical(FieldPtr f, int V, int nrhs, double2* __restric
 }
 
 template <int SPR, int RPT, int REC>
-static hp_status launch_dslash_rpt(hp_ctx* ctx, const WArgs& a, FieldPtr in, FieldPtr out, int nrhs, int V) {
+static hp_status launch_dslash_rpt(hp_ctx* ctx, const WArgs& a, FieldPtr in, FieldPtr out, int nrhs, int V,
+                                   int variant) {
   constexpr int NT = 128;
-  dim3 grid((nrhs + RPT - 1) / RPT, dslash_gridy(ctx, V, NT, (nrhs + RPT - 1) / RPT));
+  dim3 grid = stencil_grid(variant, nrhs, dslash_gridy(ctx, V, NT, nrhs));
   {
     ProfScope ps(ctx, SPR == PR64 ? "k_wds<fp64>" : SPR == PR32 ? "k_wds<fp32>" : SPR == PR16 ? "k_wds<fp16>" : "k_wds<bf16>");
     k_wds<SPR, RPT, NT, EPI_PLAIN, REC><<<grid, NT, 0, ctx->stream>>>(a, in, out, nrhs);
@@ -995,9 +1704,9 @@ static hp_status launch_dslash(hp_ctx* ctx, const LatGeom& g, FieldPtr in, Field
   a.Vmax = Vmax;
   const bool full = variant_rec(variant) == 18 && SPR != PR64;
   switch (variant_rpt(variant)) {
-    case 1: return full ? launch_dslash_rpt<SPR, 1, 18>(ctx, a, in, out, nrhs, g.V) : launch_dslash_rpt<SPR, 1, 12>(ctx, a, in, out, nrhs, g.V);
-    case 2: return full ? launch_dslash_rpt<SPR, 2, 18>(ctx, a, in, out, nrhs, g.V) : launch_dslash_rpt<SPR, 2, 12>(ctx, a, in, out, nrhs, g.V);
-    default: return full ? launch_dslash_rpt<SPR, 4, 18>(ctx, a, in, out, nrhs, g.V) : launch_dslash_rpt<SPR, 4, 12>(ctx, a, in, out, nrhs, g.V);
+    case 1: return full ? launch_dslash_rpt<SPR, 1, 18>(ctx, a, in, out, nrhs, g.V, variant) : launch_dslash_rpt<SPR, 1, 12>(ctx, a, in, out, nrhs, g.V, variant);
+    case 2: return full ? launch_dslash_rpt<SPR, 2, 18>(ctx, a, in, out, nrhs, g.V, variant) : launch_dslash_rpt<SPR, 2, 12>(ctx, a, in, out, nrhs, g.V, variant);
+    default: return full ? launch_dslash_rpt<SPR, 4, 18>(ctx, a, in, out, nrhs, g.V, variant) : launch_dslash_rpt<SPR, 4, 12>(ctx, a, in, out, nrhs, g.V, variant);
   }
 }
 
@@ -1083,10 +1792,11 @@ static hp_status tune_rpt(hp_ctx* ctx, const LatGeom& g, FieldPtr fi, FieldPtr f
   HP_CUDA(cudaEventCreate(&e1));
   float best_ms = 1e30f;
   int best_r = 10;
-  const int cands[6] = {10, 11, 20, 21, 40, 41};
+  const int cands[14] = {10, 11, 20, 21, 40, 41, 410, 411, 421, 810, 811, 821, 1611, 1621};
   for (int c : cands) {
     if (variant_rpt(c) > 1 && variant_rpt(c) > nrhs) continue;
-    if (SPR == PR64 && variant_rec(c) == 18) continue;
+    if (SPR == PR64 && (variant_rec(c) == 18 || variant_rpt(c) > 1)) continue;
+    if (variant_group(c) > 0 && variant_group(c) >= nrhs) continue;
     HP_TRY(launch_dslash<SPR>(ctx, g, fi, fo, nrhs, Vmax, c));
     HP_CUDA(cudaEventRecord(e0, ctx->stream));
     for (int i = 0; i < 3; ++i) HP_TRY(launch_dslash<SPR>(ctx, g, fi, fo, nrhs, Vmax, c));
@@ -1157,21 +1867,28 @@ hp_status hp_bench_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int pre
 hp_status hp_solve_wilson(hp_ctx* ctx, SolveProblem& pb, SolveResult& res) {
   const int prec = pb.opts.precision;
   double delta = pb.opts.delta;
+  bool eo = pb.opts.even_odd != 0;
+  for (auto& g : pb.lats)
+    if (g.L[0] % 2) eo = false;   // parity numbering by site >> 1 needs L_1 even
   switch (prec) {
     case HP_PREC_FP64: {
       WilsonEngine<PR64> e{ctx};
+      e.eo = eo;
       return run_schedule(ctx, e, pb, res, 12, delta > 0 ? delta : 0.0);
     }
     case HP_PREC_MIXED_FP32: {
       WilsonEngine<PR32> e{ctx};
+      e.eo = eo;
       return run_schedule(ctx, e, pb, res, 12, delta > 0 ? delta : 0.01);
     }
     case HP_PREC_MIXED_FP16: {
       WilsonEngine<PR16> e{ctx};
+      e.eo = eo;
       return run_schedule(ctx, e, pb, res, 12, delta > 0 ? delta : 0.1);
     }
     case HP_PREC_MIXED_BF16: {
       WilsonEngine<PRB16> e{ctx};
+      e.eo = eo;
       return run_schedule(ctx, e, pb, res, 12, delta > 0 ? delta : 0.1);
     }
   }

@@ -64,7 +64,7 @@ class SolverOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("rhs_block", C.c_int32), ("maxiter", C.c_int32),
                 ("dilution", C.c_int32), ("z0_seed", C.c_uint64), ("first", C.c_int64), ("delta", C.c_double),
                 ("check_every", C.c_int32), ("use_graph", C.c_int32), ("block_threads", C.c_int32),
-                ("rhs_per_thread", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("rhs_per_thread", C.c_int32), ("even_odd", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 class SolveStats(C.Structure):
@@ -228,7 +228,7 @@ class Context:
 
     @staticmethod
     def make_opts(precision="fp64", rhs_block=0, maxiter=0, z0_seed=0, first=0, delta=0.0, check_every=0,
-                  use_graph=0, block_threads=0, dilution=0, rhs_per_thread=0) -> SolverOpts:
+                  use_graph=0, block_threads=0, dilution=0, rhs_per_thread=0, even_odd=0) -> SolverOpts:
         o = SolverOpts()
         o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
         o.rhs_block = rhs_block
@@ -241,6 +241,7 @@ class Context:
         o.use_graph = use_graph
         o.block_threads = block_threads
         o.rhs_per_thread = rhs_per_thread
+        o.even_odd = even_odd
         return o
 
     def operator_apply(self, op: Operator, dims, nrhs: int, precision, inp, out):

@@ -205,7 +205,8 @@ def test_laplacian_complex_probes(ctx, hp):
 
 @pytest.mark.parametrize("prec,rpt", [("fp64", 0), ("fp64", 1), ("fp32", 1), ("fp32", 2), ("fp32", 4), ("fp32", 101),
                                       ("fp32", 104), ("fp16", 1), ("fp16", 2), ("fp16", 4), ("fp16", 101),
-                                      ("fp16", 102), ("bf16", 0), ("bf16", 2), ("bf16", 104)])
+                                      ("fp16", 102), ("bf16", 0), ("bf16", 2), ("bf16", 104),
+                                      ("fp16", 4101), ("fp32", 2002), ("fp16", 8121)])
 def test_wilson_trace_parity(ctx, hp, prec, rpt):
     dims = (4, 4, 4, 4)
     U = synth.gauge_links(dims, 0.3, 1002)
@@ -434,3 +435,85 @@ def test_gradient_config_24x24x24x48_properties(ctx, hp):
                              ctx.make_opts("fp64", z0_seed=5001))
     fd = (tp[-1] - tm[-1]).real / (2 * h)
     assert abs(fd - dm64) <= 1e-5 * abs(dm64), (fd, dm64)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "fp32", "bf16"])
+def test_mixed_precision_true_residual_reaches_1e12(ctx, hp, prec):
+    """The mixed solvers certify their solutions with a float-float true residual b - D x: driving
+    them to 1e-12 (100x below the configs' tolerance) must still reproduce the dense-LU trace."""
+    dims = (4, 4, 2, 4)
+    U = synth.gauge_links(dims, 0.4, 44)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.12, links_dev(U), None)
+    T, _, st = ctx.trace_inv(op, dims, 3, 1e-12, ctx.make_opts(prec, z0_seed=4))
+    T_ref = E.trace_prefix(E.wilson_quadratures(dims, U, 0.12, 0, 3, 4, method="dense"))
+    assert st["max_true_residual"] <= 1e-12
+    assert np.all(rel(T, T_ref) <= 1e-11), (T, T_ref)
+
+
+# ------------------------------------------------------------------ even-odd (Schur complement) iteration
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+def test_even_odd_trace_parity(ctx, hp, prec):
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_links(dims, 0.3, 1002)
+    mf = synth.mass_field(dims, 0.01, 77)
+    op = ctx.make_operator(hp.OP_WILSON, 0.01, 0.115, links_dev(U), dev(mf))
+    s = 6
+    T, _, st = ctx.trace_inv(op, dims, s, 1e-10, ctx.make_opts(prec, z0_seed=2002, rhs_block=24, even_odd=1))
+    T_ref = E.trace_prefix(E.wilson_quadratures(dims, U, 0.115, 0, s, 2002, mass=0.01, mass_field=mf,
+                                                method="dense"))
+    assert np.all(rel(T, T_ref) <= TRACE_RTOL), (T, T_ref)
+    assert st["max_true_residual"] <= 1e-10 and st["rhs_solved"] == 12 * s
+
+
+def test_even_odd_full_sequence_and_fallback(ctx, hp):
+    from pins import free_wilson_trace_inverse
+
+    dims = (4, 4, 2, 4)
+    V = 128
+    Ufree = np.broadcast_to(np.eye(3, dtype=complex), (V, 4, 3, 3)).copy()
+    Ug, _ = synth.gauge_transform(Ufree, dims, 78)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.12, links_dev(Ug), None)
+    T, _, _ = ctx.trace_inv(op, dims, V, 1e-11, ctx.make_opts("fp16", z0_seed=5, even_odd=1))
+    exact = free_wilson_trace_inverse(dims, 0.12)
+    assert abs(T[-1].real - exact) <= 1e-9 * exact
+    # odd L_1: the even-odd request falls back to the full iteration and stays exact
+    dims = (3, 4, 2, 4)
+    U = synth.gauge_links(dims, 0.3, 79)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.12, links_dev(U), None)
+    T, _, _ = ctx.trace_inv(op, dims, 4, 1e-10, ctx.make_opts("fp16", z0_seed=5, even_odd=1))
+    T_ref = E.trace_prefix(E.wilson_quadratures(dims, U, 0.12, 0, 4, 5, method="dense"))
+    assert np.all(rel(T, T_ref) <= TRACE_RTOL)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp16"])
+def test_even_odd_gradient_and_tight_residual(ctx, hp, prec):
+    dims = (4, 4, 2, 4)
+    U = synth.gauge_links(dims, 0.3, 21)
+    mf = synth.mass_field(dims, 0.01, 5000)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.118, links_dev(U), dev(mf))
+    g = np.zeros(128)
+    T, dTdm, st = ctx.trace_inv_grad(op, dims, 3, 1e-12, ctx.make_opts(prec, z0_seed=7, even_odd=1), g)
+    g_ref = E.wilson_grad_mass_field(dims, U, 0.118, 3, 7, mass_field=mf, method="dense").real
+    assert st["max_true_residual"] <= 1e-12
+    assert np.allclose(g, g_ref, rtol=1e-7, atol=1e-9)
+    T_ref = E.trace_prefix(E.wilson_quadratures(dims, U, 0.118, 0, 3, 7, mass_field=mf, method="dense"))
+    assert np.all(rel(T, T_ref) <= 1e-11)
+
+
+def test_even_odd_batch_and_config_sizes(ctx, hp):
+    """Uneven batch at full lattice sizes with the Schur iteration equals the full iteration."""
+    cfg = synth.batch_config()
+    s_list = [3, 2, 2, 2]
+    ops, dims_list, keep = [], [], []
+    for c in cfg:
+        U = synth.gauge_links(c["dims"], c["eps"], c["link_seed"], device="cuda:0")
+        L = links_dev(U)
+        keep.append(L)
+        ops.append(ctx.make_operator(hp.OP_WILSON, 0.0, c["kappa"], L, None))
+        dims_list.append(c["dims"])
+    eo, st = ctx.trace_inv_batch(ops, dims_list, s_list, 1e-10, ctx.make_opts("fp16", z0_seed=3000, even_odd=1,
+                                                                              use_graph=1))
+    full, _ = ctx.trace_inv_batch(ops, dims_list, s_list, 1e-10, ctx.make_opts("fp64", z0_seed=3000))
+    for a_, b_ in zip(eo, full):
+        assert np.all(rel(a_, b_) <= TRACE_RTOL)
+    assert st["max_true_residual"] <= 1e-10
