@@ -140,27 +140,49 @@ def max_over_ranks(ws, value, device):
 
 # ------------------------------------------------------------------ algorithmic bytes
 def spinor_link_bytes(prec):
-    return {"fp64": (192, 144, 192), "fp32": (96, 48, 96), "fp16": (52, 24, 96), "bf16": (52, 24, 96)}[prec]
+    """(spinor bytes per site, link bytes per link as the stencil reads it, correction-field bytes
+    per site): fp16/bf16 spinors carry a 4-byte norm per site; the mixed modes read 18-real links."""
+    return {"fp64": (192, 144, 192), "fp32": (96, 72, 96), "fp16": (52, 36, 96), "bf16": (52, 36, 96)}[prec]
 
 
-def kernel_bytes(name, prec, V, rhs_iters, launches, updates):
-    """Algorithmic DRAM bytes of one solver kernel over the run (each vector read/written once,
-    links once per launch): rhs_iters = right-hand-side iterations, updates = FP64 reliable updates."""
+def kernel_bytes(name, prec, V, c):
+    """Algorithmic DRAM bytes of one solver kernel over the run: every vector it touches read or
+    written once, the links once per launch.  c: counts of the run -- rhs_iters (right-hand-side
+    iterations), launches (of this kernel), exact (true-residual evaluations, including the
+    initial one), groups (FP32 group updates), eo (iterating on the odd half)."""
     S, L, E = spinor_link_bytes(prec)
+    X = 192                                   # FP64 or float-float solution, per site
+    n, it, la = c["eo"], c["rhs_iters"], c["launches"]
+    Vf = V // 2 if n else V                   # sites of the iterated vectors
+    links = 4 * V * L * la
     if name.startswith("k_bicg_v"):
-        return V * (3 * S * rhs_iters + 4 * L * launches)
+        return Vf * 3 * S * it + links
     if name.startswith("k_bicg_t"):
-        return V * (2 * S * rhs_iters + 4 * L * launches)
+        return Vf * 2 * S * it + links
     if name == "k_bicg_s":
-        return V * 3 * S * rhs_iters
+        return Vf * 3 * S * it
     if name == "k_bicg_xr":
-        return V * (5 * S + 2 * E) * rhs_iters
+        return Vf * (5 * S + 2 * E) * it
     if name == "k_bicg_p":
-        return V * 4 * S * rhs_iters
-    if name == "k_ru_accum":
-        return V * (2 * 192 + 2 * E) * updates
+        return Vf * 4 * S * it
+    if name == "k_ru_accum":                  # x += e after group and exact updates (upper bound)
+        return Vf * (2 * X + 2 * E) * (c["groups"] + c["updates"])
     if name.startswith("k_ru_residual"):
-        return V * ((192 + 2 * S) * updates + 4 * 144 * launches)
+        return V * (X + 2 * S) * c["exact"] + 4 * V * 144 * la
+    if name == "k_eo_even":                   # V and T steps: mid = d_e^-1 H_eo in
+        return Vf * 2 * S * 2 * it + links
+    if name.startswith("k_eo_odd_v"):         # v = d_o p - k^2 H_oe mid, (r^, v)
+        return Vf * 4 * S * it + links
+    if name.startswith("k_eo_odd_t"):         # t = d_o s - k^2 H_oe mid, (t, s), (t, t)
+        return Vf * 3 * S * it + links
+    if name == "k_eo_even<grp>":              # mid32 = d_e^-1 H_eo e (FP32)
+        return Vf * (E + 96) * c["groups"] + 4 * V * 48 * la
+    if name == "k_eo_odd<grp>":               # r_g -= d_o e - k^2 H_oe mid32; r = r_g; dots
+        return Vf * (96 + E + 2 * 96 + 2 * S) * c["groups"] + 4 * V * 48 * la
+    if name.startswith("k_eo_x1"):            # x_e = d_e^-1 (b_e + k H_eo x_o)
+        return Vf * 2 * X * c["exact"] + 4 * V * 144 * la
+    if name.startswith("k_eo_x2"):            # r_o = b_o - d_o x_o + k H_oe x_e
+        return Vf * (2 * X + 2 * S + 96) * c["exact"] + 4 * V * 144 * la
     return None
 
 
@@ -236,7 +258,7 @@ def run_ours(args):
     max_res = max(s["max_true_residual"] for s in stats)
 
     # end to end through the C ABI with host buffers: links from pinned host memory, T back to host
-    e2e_steps = max(1, min(2, args.steps))
+    e2e_steps = 0 if args.no_e2e else max(1, min(2, args.steps))
     barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -249,8 +271,10 @@ def run_ours(args):
         d2h += 2 * 16 * (first + P)             # quadratures and prefix estimates
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(ws, time.perf_counter() - t0, device)
-    e2e = {"value": ws * e2e_rhs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d / e2e_steps),
-           "d2h_bytes_per_step": int(d2h / e2e_steps), "steps": e2e_steps}
+    e2e = None
+    if e2e_steps:
+        e2e = {"value": ws * e2e_rhs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d / e2e_steps),
+               "d2h_bytes_per_step": int(d2h / e2e_steps), "steps": e2e_steps}
 
     # plain FP64 solver on the same GPU (one probe = 12 solves), for the mixed-vs-FP64 ratio
     fp64 = None
@@ -270,21 +294,24 @@ def run_ours(args):
                 "max_true_residual": st64["max_true_residual"]}
 
     # stencil alone (Dslash GB/s) in the iteration precision and in FP64
-    op = ctx.make_operator(hprobe.OP_WILSON, 0.0, KAPPA, links_dev, None)
-    ds = ctx.dslash_bench(op, DIMS, prec, args.rhs_block, 20)
-    ds64 = ctx.dslash_bench(op, DIMS, "fp64", 1, 5)
     peak, peak_kind = hbm_peak()
-    dslash = {"precision": prec, "nrhs": args.rhs_block, "ms": ds["ms"], "GBps": ds["bytes"] / ds["ms"] / 1e6,
-              "frac_of_%s_hbm" % peak_kind: ds["bytes"] / ds["ms"] / 1e6 / peak,
-              "TFLOPs": ds["flops"] / ds["ms"] / 1e9,
-              "fp64": {"nrhs": 1, "ms": ds64["ms"], "GBps": ds64["bytes"] / ds64["ms"] / 1e6,
-                       "TFLOPs": ds64["flops"] / ds64["ms"] / 1e9}}
+    dslash = None
+    if not args.no_dslash:
+        op = ctx.make_operator(hprobe.OP_WILSON, 0.0, KAPPA, links_dev, None)
+        ds = ctx.dslash_bench(op, DIMS, prec, args.rhs_block, 20)
+        ds64 = ctx.dslash_bench(op, DIMS, "fp64", 1, 5)
+        dslash = {"precision": prec, "nrhs": args.rhs_block, "ms": ds["ms"], "GBps": ds["bytes"] / ds["ms"] / 1e6,
+                  "frac_of_%s_hbm" % peak_kind: ds["bytes"] / ds["ms"] / 1e6 / peak,
+                  "TFLOPs": ds["flops"] / ds["ms"] / 1e9,
+                  "fp64": {"nrhs": 1, "ms": ds64["ms"], "GBps": ds64["bytes"] / ds64["ms"] / 1e6,
+                           "TFLOPs": ds64["flops"] / ds64["ms"] / 1e9}}
 
     # roofline of the dominant kernel of the timed steps (event-timed launches, algorithmic bytes)
-    rhs_iters = iters
+    counts = {"rhs_iters": iters, "updates": updates, "exact": updates + (rhs if args.even_odd and prec == "fp64" else 0),
+              "groups": sum(s["group_updates"] for s in stats), "eo": bool(args.even_odd)}
     kernels = {}
     for name, rec in prof.items():
-        b = kernel_bytes(name, prec, V, rhs_iters, rec["launches"], updates)
+        b = kernel_bytes(name, prec, V, dict(counts, launches=rec["launches"]))
         kernels[name] = {"launches": rec["launches"], "ms": rec["ms"],
                          "GBps": (b / (rec["ms"] / 1e3) / 1e9) if b and rec["ms"] > 0 else None}
     tot_ms = sum(r["ms"] for r in prof.values()) or 1.0
@@ -292,7 +319,7 @@ def run_ours(args):
         k["share"] = k["ms"] / tot_ms
     top = max(kernels.items(), key=lambda kv: kv[1]["ms"])
     top_name, top_rec = top
-    top_bytes = kernel_bytes(top_name, prec, V, rhs_iters, top_rec["launches"], updates)
+    top_bytes = kernel_bytes(top_name, prec, V, dict(counts, launches=top_rec["launches"]))
     achieved = top_bytes / (top_rec["ms"] / 1e3) / 1e9 if top_bytes else None
     trace_ncu = NCU_TRAFFIC.get((top_name, source_hash()))
     roofline = {"kernel": top_name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -311,8 +338,9 @@ def run_ours(args):
         "dtype": {"fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math",
                   "fp64": "f64"}[prec] + " + f64 reliable updates",
         "data": "synthetic: SU(3) links exp(i eps H), seeded (no gauge ensemble available)",
-        "config": {"workload": "32^3x64 Wilson-Dirac, kappa 0.12, eps 0.4, %d probes x 12 dilutions per step, "
-                               "BiCGStab %s%s, tol 1e-10" % (P, prec, " on the even-odd Schur complement"
+        "config": {"workload": "%s Wilson-Dirac, kappa 0.12, eps 0.4, %d probes x 12 dilutions per step, "
+                               "BiCGStab %s%s, tol 1e-10" % ("x".join(map(str, DIMS)), P, prec,
+                                                              " on the even-odd Schur complement"
                                                               if args.even_odd else ""),
                    "even_odd": bool(args.even_odd),
                    "lattice": list(DIMS), "probes_per_step": P, "rhs_per_step": 12 * P, "rhs_block": args.rhs_block,
@@ -509,7 +537,16 @@ def main():
     ap.add_argument("--workload", default="headline", choices=["headline", "batch", "grad"])
     ap.add_argument("--even-odd", type=int, default=1, help="1: iterate on the odd-site Schur complement")
     ap.add_argument("--grad-probes", type=int, default=128)
+    ap.add_argument("--lattice", default=None,
+                    help="L1,L2,L3,L4: another lattice for the headline path (profiling small cases; "
+                         "not the benchmark workload)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-dslash", action="store_true")
     args = ap.parse_args()
+    if args.lattice:
+        global DIMS
+        DIMS = tuple(int(v) for v in args.lattice.split(","))
+        assert len(DIMS) == 4
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":

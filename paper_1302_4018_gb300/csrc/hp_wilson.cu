@@ -943,11 +943,12 @@ __global__ void k_w_grad(WArgs a, int lat, const int* __restrict__ slots, int ns
 // is  r_o = b_o - d_o x_o + k H_oe x_e  while the even part vanishes by construction: the
 // certified residual is the residual of the full system.  Sites of one parity are numbered
 // by site >> 1 (needs L_1 even).
-enum { MASK_RUN = 0, MASK_GROUP = 1, MASK_EXACT = 2 };
+enum { MASK_RUN = 0, MASK_GROUP = 1, MASK_EXACT = 2, MASK_FRESH = 3 };
 
 __device__ __forceinline__ bool eo_mask(const SlotState* S, int mask) {
   if (mask == MASK_RUN) return S->status == SLOT_RUN;
   if (mask == MASK_GROUP) return S->need_update == 1;
+  if (mask == MASK_FRESH) return S->status == SLOT_RUN && S->restart == 2 && S->need_update == 0;
   return S->need_update == 2;
 }
 
@@ -1280,7 +1281,16 @@ __global__ void __launch_bounds__(NT) k_eo_init(WArgs a, int nslots) {
       par += r % g.L[j];
       r /= g.L[j];
     }
-    if ((par & 1) == 0) continue;   // odd sites carry the Krylov vectors
+    if ((par & 1) == 0) {           // odd sites carry the Krylov vectors
+      if (SPR != PR64) {            // x_e = 0 until the first exact step (the mixed start skips it)
+        cplx<float> z[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) z[k] = {0.f, 0.f};
+        SpinorIO<PR32>::store(FieldPtr{a.xeff.p, nullptr, nullptr}, a.Vmax, slot, h, z);
+        SpinorIO<PR32>::store(FieldPtr{a.xeff.lo, nullptr, nullptr}, a.Vmax, slot, h, z);
+      }
+      continue;
+    }
     cplx<typename Real_of<EPR>::T> ze[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) ze[k] = {0, 0};
@@ -1312,9 +1322,83 @@ __global__ void __launch_bounds__(NT) k_eo_init(WArgs a, int nslots) {
       S->sloppy_mv = 0;
       S->fp64_mv = 0;
       S->gupdates = 0;
-      S->restart = 2;          // fresh: the exact steps below produce the initial residual
-      S->need_update = 2;
+      S->restart = 2;          // fresh: the start kernels produce the initial residual
+      S->need_update = SPR == PR64 ? 2 : 0;   // FP64: the exact steps; mixed: the FP32 start
       S->status = tot[0] > 0.0 ? SLOT_RUN : SLOT_DONE;
+      a.cnt[slot] = 0;
+    }
+  }
+}
+
+// ---- mixed-precision start (FP32), in place of the exact steps of the FP64 mode:
+//   mid32 = d_e^-1 b_e on the even sites, then r = r^ = p = r_g = b_o + k H_oe mid32.
+// The initial residual only seeds the iteration (every exact step recomputes the residual from
+// x, and x_e from x_o), so FP32 accuracy suffices here.  A start residual at or below the
+// tolerance is handed to the exact steps, which certify or continue it.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_eo_src(WArgs a, int nslots) {
+  EO_PREAMBLE(MASK_FRESH)
+  const int comp = S->a, m = S->m;
+  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+    const int h = tile * NT + threadIdx.x;
+    if (h >= nsite) continue;
+    int x[4], st[4];
+    const int site = eo_site(g, h, 0, x, st);
+    const double2 bv = source_value(g, site, m);
+    const float inv = 1.0f / site_diag<float>(g, site);
+    cplx<float> z[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) z[k] = k == comp ? cplx<float>{inv * (float)bv.x, inv * (float)bv.y}
+                                                   : cplx<float>{0.f, 0.f};
+    SpinorIO<PR32>::store(a.mid32, a.Vmax, slot, h, z);
+  }
+}
+
+template <int SPR, int NT>
+__global__ void __launch_bounds__(NT) k_eo_r0(WArgs a, int nslots) {
+  EO_PREAMBLE(MASK_FRESH)
+  typedef typename Real_of<SPR>::T RS;
+  const int comp = S->a, m = S->m;
+  const float kap = (float)g.kappa;
+  float acc1[1] = {0.f};
+  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+    const int h = tile * NT + threadIdx.x;
+    if (h >= nsite) continue;
+    int x[4], st[4];
+    const int site = eo_site(g, h, 1, x, st);
+    cplx<float> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = {0.f, 0.f};
+    eo_hop<PR32, PR32, 12, float>(g, a.mid32, a.Vmax, slot, site, x, st, kap, acc);
+    const double2 bv = source_value(g, site, m);
+    cplx<RS> rs[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      if (k == comp) {
+        acc[k].x += (float)bv.x;
+        acc[k].y += (float)bv.y;
+      }
+      rs[k] = {(RS)acc[k].x, (RS)acc[k].y};
+      acc1[0] += acc[k].x * acc[k].x + acc[k].y * acc[k].y;
+    }
+    SpinorIO<PR32>::store(a.rg, a.Vmax, slot, h, acc);
+    SpinorIO<SPR>::store(a.r, a.Vmax, slot, h, rs);
+    SpinorIO<SPR>::store(a.rh, a.Vmax, slot, h, rs);
+    SpinorIO<SPR>::store(a.p, a.Vmax, slot, h, rs);
+  }
+  reduce_partials<float, 1, NT>(acc1, part, a.gy);
+  if (last_block(a.cnt + slot, nparts)) {
+    double tot[1];
+    block_sum_partials<1, NT>(part, a.gy, nparts, tot);
+    if (threadIdx.x == 0) {
+      if (tot[0] > a.tol2 * S->bnorm2) {
+        S->restart = 0;
+        S->rnorm2 = S->rmax2 = S->rexact2 = tot[0];
+        S->rho = make_double2(tot[0], 0.0);
+        S->true_res2 = tot[0];
+      } else {
+        S->need_update = 2;   // still fresh: the exact steps start (or finish) this slot
+      }
       a.cnt[slot] = 0;
     }
   }
@@ -1501,22 +1585,28 @@ struct WilsonEngine {
     dim3 gr = stencil_grid(variant, nslots, gy);
     constexpr int LPR = LinkPrecOf<SPR>::v;
     if (which == 0) {
-      ProfScope ps(ctx, "k_eo_even");
-      k_eo_even<SPR, LPR, REC, SPR, NT, MASK_RUN><<<gr, NT, 0, ctx->stream>>>(a, a.p, a.mid, nslots);
+      {
+        ProfScope ps(ctx, "k_eo_even");
+        k_eo_even<SPR, LPR, REC, SPR, NT, MASK_RUN><<<gr, NT, 0, ctx->stream>>>(a, a.p, a.mid, nslots);
+      }
       HP_LAUNCH_CHECK();
-      ProfScope ps2(ctx, SPR == PR64 ? "k_eo_odd_v<fp64>" : SPR == PR32 ? "k_eo_odd_v<fp32>" : SPR == PR16 ? "k_eo_odd_v<fp16>" : "k_eo_odd_v<bf16>");
+      ProfScope ps(ctx, SPR == PR64 ? "k_eo_odd_v<fp64>" : SPR == PR32 ? "k_eo_odd_v<fp32>" : SPR == PR16 ? "k_eo_odd_v<fp16>" : "k_eo_odd_v<bf16>");
       k_eo_odd<SPR, SPR, LPR, REC, NT, EPI_V><<<gr, NT, 0, ctx->stream>>>(a, a.p, a.mid, a.v, nslots);
     } else if (which == 1) {
-      ProfScope ps(ctx, "k_eo_even");
-      k_eo_even<SPR, LPR, REC, SPR, NT, MASK_RUN><<<gr, NT, 0, ctx->stream>>>(a, a.s, a.mid, nslots);
+      {
+        ProfScope ps(ctx, "k_eo_even");
+        k_eo_even<SPR, LPR, REC, SPR, NT, MASK_RUN><<<gr, NT, 0, ctx->stream>>>(a, a.s, a.mid, nslots);
+      }
       HP_LAUNCH_CHECK();
-      ProfScope ps2(ctx, SPR == PR64 ? "k_eo_odd_t<fp64>" : SPR == PR32 ? "k_eo_odd_t<fp32>" : SPR == PR16 ? "k_eo_odd_t<fp16>" : "k_eo_odd_t<bf16>");
+      ProfScope ps(ctx, SPR == PR64 ? "k_eo_odd_t<fp64>" : SPR == PR32 ? "k_eo_odd_t<fp32>" : SPR == PR16 ? "k_eo_odd_t<fp16>" : "k_eo_odd_t<bf16>");
       k_eo_odd<SPR, SPR, LPR, REC, NT, EPI_T><<<gr, NT, 0, ctx->stream>>>(a, a.s, a.mid, a.t, nslots);
     } else if (SPR != PR64) {
-      ProfScope ps(ctx, "k_eo_even<grp>");
-      k_eo_even<EPR, PR32, 12, PR32, NT, MASK_GROUP><<<gr, NT, 0, ctx->stream>>>(a, a.e, a.mid32, nslots);
+      {
+        ProfScope ps(ctx, "k_eo_even<grp>");
+        k_eo_even<EPR, PR32, 12, PR32, NT, MASK_GROUP><<<gr, NT, 0, ctx->stream>>>(a, a.e, a.mid32, nslots);
+      }
       HP_LAUNCH_CHECK();
-      ProfScope ps2(ctx, "k_eo_odd<grp>");
+      ProfScope ps(ctx, "k_eo_odd<grp>");
       k_eo_odd<EPR, PR32, PR32, 12, NT, EPI_G><<<gr, NT, 0, ctx->stream>>>(a, a.e, a.mid32, a.rg, nslots);
     }
     HP_LAUNCH_CHECK();
@@ -1566,7 +1656,22 @@ struct WilsonEngine {
         k_eo_init<SPR, EPR, NT><<<grid(), NT, 0, ctx->stream>>>(a, nslots);
       }
       HP_LAUNCH_CHECK();
-      return eo_exact();   // x_e = d_e^-1 b_e and the initial residual of the Schur system
+      if (SPR != PR64) {
+        const dim3 gr = stencil_grid(variant, nslots, gy);
+        {
+          ProfScope ps(ctx, "k_eo_src");
+          k_eo_src<NT><<<gr, NT, 0, ctx->stream>>>(a, nslots);
+        }
+        HP_LAUNCH_CHECK();
+        {
+          ProfScope ps(ctx, "k_eo_r0");
+          k_eo_r0<SPR, NT><<<gr, NT, 0, ctx->stream>>>(a, nslots);
+        }
+        HP_LAUNCH_CHECK();
+      }
+      // FP64: x_e = d_e^-1 b_e and the initial residual of the Schur system; mixed: only slots
+      // whose FP32 start residual is already at the tolerance
+      return eo_exact();
     }
     {
       ProfScope ps(ctx, "k_bicg_init");

@@ -517,3 +517,18 @@ def test_even_odd_batch_and_config_sizes(ctx, hp):
     for a_, b_ in zip(eo, full):
         assert np.all(rel(a_, b_) <= TRACE_RTOL)
     assert st["max_true_residual"] <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp16", "fp32"])
+def test_even_odd_start_at_tolerance(ctx, hp, prec):
+    """A loose tolerance that the first residual already meets: the mixed solver hands its FP32
+    start to the exact steps, which certify it with no iteration -- the same estimate as the FP64
+    solver, whose start is exact."""
+    dims = (4, 4, 2, 4)
+    U = synth.gauge_links(dims, 0.3, 91)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.05, links_dev(U), None)
+    T, _, st = ctx.trace_inv(op, dims, 2, 0.9, ctx.make_opts(prec, z0_seed=8, even_odd=1))
+    T64, _, st64 = ctx.trace_inv(op, dims, 2, 0.9, ctx.make_opts("fp64", z0_seed=8, even_odd=1))
+    assert st["iterations_total"] == 0 and st64["iterations_total"] == 0
+    assert st["max_true_residual"] <= 0.9
+    assert np.all(rel(T, T64) <= 1e-12), (T, T64)
