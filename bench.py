@@ -140,9 +140,10 @@ def max_over_ranks(ws, value, device):
 
 # ------------------------------------------------------------------ algorithmic bytes
 def spinor_link_bytes(prec):
-    """(spinor bytes per site, link bytes per link as the stencil reads it, correction-field bytes
-    per site): fp16/bf16 spinors carry a 4-byte norm per site; the mixed modes read 18-real links."""
-    return {"fp64": (192, 144, 192), "fp32": (96, 72, 96), "fp16": (52, 36, 96), "bf16": (52, 36, 96)}[prec]
+    """(spinor bytes per site, link bytes per link as the stencil reads it, bytes per site of the
+    solution increment e): fp16/bf16 spinors carry a 4-byte norm per site, e is kept in the
+    iteration precision, the mixed modes read 18-real links."""
+    return {"fp64": (192, 144, 192), "fp32": (96, 72, 96), "fp16": (52, 36, 52), "bf16": (52, 36, 52)}[prec]
 
 
 def kernel_bytes(name, prec, V, c):

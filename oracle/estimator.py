@@ -106,12 +106,14 @@ def _dilute(w: np.ndarray, a: int) -> np.ndarray:
 
 
 def wilson_solutions(dims, U, kappa, W, tol=1e-13, mass=0.0, mass_field=None, method="bicgstab",
-                     dagger=False):
-    """x_{m,a} = D^-1 v_{m,a} (or D^-H v_{m,a}); returns complex [count, 12, V, 4, 3]."""
+                     dagger=False, csw=0.0):
+    """x_{m,a} = D^-1 v_{m,a} (or D^-H v_{m,a}); returns complex [count, 12, V, 4, 3].
+    csw != 0 adds the clover term C(x) of operators.clover_term."""
     count, V = W.shape
     X = np.empty((count, 12, V, 4, 3), dtype=complex)
+    clover = ops.clover_term(U, dims, kappa, csw) if csw else None
     if method == "dense":
-        D = ops.wilson_dense(U, dims, kappa, mass, mass_field)
+        D = ops.wilson_dense(U, dims, kappa, mass, mass_field, clover=clover)
         if dagger:
             D = np.conj(D).T
         B = np.zeros((12 * V, 12 * count), dtype=complex)
@@ -125,7 +127,7 @@ def wilson_solutions(dims, U, kappa, W, tol=1e-13, mass=0.0, mass_field=None, me
         return X
 
     def apply(v):
-        return ops.wilson_apply(v, U, dims, kappa, mass, mass_field, dagger=dagger)
+        return ops.wilson_apply(v, U, dims, kappa, mass, mass_field, dagger=dagger, clover=clover)
 
     for m in range(count):
         for a in range(12):
@@ -134,10 +136,10 @@ def wilson_solutions(dims, U, kappa, W, tol=1e-13, mass=0.0, mass_field=None, me
 
 
 def wilson_quadratures(dims, U, kappa, first, count, z0_seed, tol=1e-13, mass=0.0,
-                       mass_field=None, method="bicgstab", loc=None):
+                       mass_field=None, method="bicgstab", loc=None, csw=0.0):
     """q_m = sum_a v_{m,a}^H D^-1 v_{m,a} with full spin-colour dilution."""
     W = probe_vectors(dims, first, count, z0_seed, loc=loc)
-    X = wilson_solutions(dims, U, kappa, W, tol, mass, mass_field, method)
+    X = wilson_solutions(dims, U, kappa, W, tol, mass, mass_field, method, csw=csw)
     V = W.shape[1]
     q = np.zeros(count, dtype=complex)
     for m in range(count):
@@ -147,10 +149,10 @@ def wilson_quadratures(dims, U, kappa, first, count, z0_seed, tol=1e-13, mass=0.
 
 
 def wilson_grad_mass_field(dims, U, kappa, s, z0_seed, tol=1e-13, mass=0.0, mass_field=None,
-                           method="bicgstab"):
+                           method="bicgstab", csw=0.0):
     """dT_s/dmu(x) = -(1/s) sum_{m<s,a} sum_c conj(y(x,c)) x(x,c), y = D^-H v solved explicitly."""
     W = probe_vectors(dims, 0, s, z0_seed)
-    X = wilson_solutions(dims, U, kappa, W, tol, mass, mass_field, method)
-    Y = wilson_solutions(dims, U, kappa, W, tol, mass, mass_field, method, dagger=True)
+    X = wilson_solutions(dims, U, kappa, W, tol, mass, mass_field, method, csw=csw)
+    Y = wilson_solutions(dims, U, kappa, W, tol, mass, mass_field, method, dagger=True, csw=csw)
     g = np.sum(np.conj(Y) * X, axis=(0, 1, 3, 4))
     return -g / s

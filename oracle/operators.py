@@ -7,12 +7,20 @@ Oracle (test infrastructure only).
   per-site mass field mu(x) on the diagonal.
 * Wilson-Dirac matrix (Section 1.1.1: a sparse matrix on a periodic 4-D
   lattice with 12 = 4 spin x 3 colour unknowns per site; Section 5.3 uses its
-  clover variant).  Plain Wilson form in kappa normalisation:
-      (D psi)(x) = (1 + m + mu(x)) psi(x)
+  clover variant).  Wilson form in kappa normalisation:
+      (D psi)(x) = (1 + m + mu(x)) psi(x) + C(x) psi(x)
                    - kappa sum_mu [ (1 - g_mu) U_mu(x)        psi(x + mu)
                                   + (1 + g_mu) U_mu(x - mu)^H psi(x - mu) ]
   with explicit 4x4 gamma matrices (chiral basis, gamma_5 diagonal) and full
-  3x3 link products: no spin projection, no link reconstruction.
+  3x3 link products: no spin projection, no link reconstruction.  C(x) is the
+  Sheikholeslami-Wohlert (clover) term the paper's Section 5.3 operator
+  carries (it only names the discretisation; the form used is the standard
+  clover-leaf one):
+      C(x) = -c_sw kappa sum_{mu<nu} sigma_{mu nu} (x) F_{mu nu}(x),
+      sigma_{mu nu} = (i/2) [g_mu, g_nu],
+      F_{mu nu}(x) = traceless part of (Q_{mu nu}(x) - Q_{mu nu}(x)^H) / (8 i),
+  Q_{mu nu}(x) the sum of the four plaquettes of the mu-nu plane that start and
+  end at x, each run mu-then-nu (counter-clockwise).  c_sw = 0 is plain Wilson.
 
 Field layout: arrays indexed by the lexicographic site (x_1 fastest); a spinor
 is complex128 [V, 4, 3] (spin, colour); a gauge field is complex128
@@ -94,15 +102,84 @@ def gamma_matrices() -> list:
     return g
 
 
+# ------------------------------------------------------------------ clover term
+def sigma_munu(mu: int, nu: int) -> np.ndarray:
+    """sigma_{mu nu} = (i/2) [g_mu, g_nu], a Hermitian 4x4 matrix (mu, nu 0-based)."""
+    g = gamma_matrices()
+    return 0.5j * (g[mu] @ g[nu] - g[nu] @ g[mu])
+
+
+def _site_index(x: Sequence[int], dims: Sequence[int]) -> int:
+    i, stride = 0, 1
+    for j in range(len(dims)):
+        i += (x[j] % dims[j]) * stride
+        stride *= dims[j]
+    return i
+
+
+def clover_leaves(U: np.ndarray, dims: Sequence[int], mu: int, nu: int) -> np.ndarray:
+    """Q_{mu nu}(x) for every site: the four plaquettes of the mu-nu plane starting and ending at
+    x, each run mu-then-nu, as products of 3x3 links, site by site; complex [V, 3, 3]."""
+    V = int(np.prod(dims))
+    strides = [int(np.prod(dims[:j])) for j in range(len(dims))]
+    Q = np.zeros((V, 3, 3), dtype=complex)
+
+    def link(x, d):
+        return U[_site_index(x, dims), d]
+
+    def step(x, d, n):
+        y = list(x)
+        y[d] += n
+        return y
+
+    H = lambda A: np.conj(A).T
+    for i in range(V):
+        x = [(i // strides[j]) % dims[j] for j in range(len(dims))]
+        xm, xn = step(x, mu, -1), step(x, nu, -1)
+        xmn = step(xm, nu, -1)
+        # x -> x+mu -> x+mu+nu -> x+nu -> x
+        Q[i] += link(x, mu) @ link(step(x, mu, 1), nu) @ H(link(step(x, nu, 1), mu)) @ H(link(x, nu))
+        # x -> x+nu -> x+nu-mu -> x-mu -> x
+        Q[i] += link(x, nu) @ H(link(step(xm, nu, 1), mu)) @ H(link(xm, nu)) @ link(xm, mu)
+        # x -> x-mu -> x-mu-nu -> x-nu -> x
+        Q[i] += H(link(xm, mu)) @ H(link(xmn, nu)) @ link(xmn, mu) @ link(xn, nu)
+        # x -> x-nu -> x-nu+mu -> x+mu -> x
+        Q[i] += H(link(xn, nu)) @ link(xn, mu) @ link(step(xn, mu, 1), nu) @ H(link(x, mu))
+    return Q
+
+
+def clover_field(U: np.ndarray, dims: Sequence[int], mu: int, nu: int) -> np.ndarray:
+    """F_{mu nu}(x) = traceless part of (Q - Q^H) / (8 i); Hermitian, complex [V, 3, 3]."""
+    Q = clover_leaves(U, dims, mu, nu)
+    F = (Q - np.conj(np.transpose(Q, (0, 2, 1)))) / 8j
+    tr = np.trace(F, axis1=1, axis2=2)
+    return F - tr[:, None, None] * np.eye(3)[None] / 3.0
+
+
+def clover_term(U: np.ndarray, dims: Sequence[int], kappa: float, csw: float) -> np.ndarray:
+    """C(x) = -c_sw kappa sum_{mu<nu} sigma_{mu nu} (x) F_{mu nu}(x) as 12x12 matrices indexed
+    (3 s + c, 3 t + d); complex [V, 12, 12]."""
+    V = int(np.prod(dims))
+    C = np.zeros((V, 12, 12), dtype=complex)
+    for mu in range(4):
+        for nu in range(mu + 1, 4):
+            F = clover_field(U, dims, mu, nu)
+            s = sigma_munu(mu, nu)
+            for i in range(V):
+                C[i] += np.kron(s, F[i])
+    return -csw * kappa * C
+
+
 # ------------------------------------------------------------------ Wilson
 def wilson_apply(psi: np.ndarray, U: np.ndarray, dims: Sequence[int], kappa: float,
                  mass: float = 0.0, mass_field: np.ndarray | None = None,
-                 dagger: bool = False) -> np.ndarray:
-    """D psi (or D^H psi when ``dagger``) for psi [V, 4, 3] complex.
+                 dagger: bool = False, clover: np.ndarray | None = None) -> np.ndarray:
+    """D psi (or D^H psi when ``dagger``) for psi [V, 4, 3] complex; ``clover`` = the site
+    matrices C(x) of clover_term (None: plain Wilson).
 
     D^H follows from transposing the blocks of D: the hopping term to x + mu
     becomes (1 + g_mu) U_mu(x) and the one to x - mu becomes
-    (1 - g_mu) U_mu(x - mu)^H (the projectors are Hermitian).
+    (1 - g_mu) U_mu(x - mu)^H (the projectors are Hermitian); C(x) is Hermitian.
     """
     g = gamma_matrices()
     I4 = np.eye(4, dtype=complex)
@@ -110,6 +187,9 @@ def wilson_apply(psi: np.ndarray, U: np.ndarray, dims: Sequence[int], kappa: flo
     out = diag * psi
     if mass_field is not None:
         out = out + mass_field[:, None, None] * psi
+    if clover is not None:
+        Cx = np.conj(np.transpose(clover, (0, 2, 1))) if dagger else clover
+        out = out + np.einsum("xij,xj->xi", Cx, psi.reshape(-1, 12)).reshape(psi.shape)
     hop = np.zeros_like(psi)
     for mu in range(4):
         P_fwd = I4 - g[mu] if not dagger else I4 + g[mu]
@@ -126,7 +206,7 @@ def wilson_apply(psi: np.ndarray, U: np.ndarray, dims: Sequence[int], kappa: flo
 
 
 def wilson_dense(U: np.ndarray, dims: Sequence[int], kappa: float, mass: float = 0.0,
-                 mass_field: np.ndarray | None = None) -> np.ndarray:
+                 mass_field: np.ndarray | None = None, clover: np.ndarray | None = None) -> np.ndarray:
     """D as a dense 12V x 12V matrix, block by block from its definition."""
     g = gamma_matrices()
     I4 = np.eye(4, dtype=complex)
@@ -137,6 +217,8 @@ def wilson_dense(U: np.ndarray, dims: Sequence[int], kappa: float, mass: float =
     for i in range(V):
         m_i = mass + (0.0 if mass_field is None else mass_field[i])
         D[12 * i:12 * i + 12, 12 * i:12 * i + 12] += (1.0 + m_i) * np.eye(12)
+        if clover is not None:
+            D[12 * i:12 * i + 12, 12 * i:12 * i + 12] += clover[i]
         x = [(i // strides[j]) % dims[j] for j in range(d)]
         for mu in range(d):
             y = list(x)

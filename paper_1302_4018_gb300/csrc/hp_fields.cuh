@@ -65,6 +65,14 @@ __device__ __forceinline__ ffl& operator-=(ffl& a, ffl b) {
   return a;
 }
 __device__ __forceinline__ double ffl_to_double(ffl a) { return (double)a.hi + (double)a.lo; }
+template <typename T>
+struct is_ffl {
+  static constexpr bool value = false;
+};
+template <>
+struct is_ffl<ffl> {
+  static constexpr bool value = true;
+};
 
 template <int PR>
 struct Real_of {
@@ -566,12 +574,116 @@ __device__ __forceinline__ void site_coords(const LatGeom& g, int site, int (&x)
   }
 }
 
+// ---- the float-float hop ----
+// Lazily normalised float-float numbers for the hop sums: the high parts are added with TwoSum
+// and products of high parts split exactly with an FMA (TwoProduct), while every rounding error
+// and cross term collects in the low part without renormalising after each operation (the low
+// part stays within a few ulp of the high part over the ~200 terms of a hop, so hi + lo keeps a
+// 46-bit significand).  One renormalisation per result.
+struct ffz {
+  float hi, lo;
+  __device__ __forceinline__ ffz() {}
+  __device__ __forceinline__ ffz(float h, float l) : hi(h), lo(l) {}
+  __device__ __forceinline__ ffz(int i) : hi((float)i), lo(0.f) {}
+};
+__device__ __forceinline__ ffz operator-(ffz a) { return ffz(-a.hi, -a.lo); }
+__device__ __forceinline__ ffz operator+(ffz a, ffz b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return ffz(s, __fadd_rn(__fadd_rn(a.lo, b.lo), e));
+}
+__device__ __forceinline__ ffz operator-(ffz a, ffz b) { return a + (-b); }
+__device__ __forceinline__ ffz fma(ffz a, ffz b, ffz c) {   // c + a b
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const float s = __fadd_rn(c.hi, p);
+  const float bb = __fsub_rn(s, c.hi);
+  const float t = __fadd_rn(__fsub_rn(c.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  return ffz(s, __fadd_rn(__fadd_rn(c.lo, e), t));
+}
+__device__ __forceinline__ ffl ffl_of(ffz a) {   // renormalise (TwoSum: no ordering of |hi|, |lo| assumed)
+  const float s = __fadd_rn(a.hi, a.lo);
+  const float bb = __fsub_rn(s, a.hi);
+  return ffl(s, __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(a.lo, bb)));
+}
+
+__device__ __forceinline__ int sel4(const int (&v)[4], int mu) {
+  return mu == 0 ? v[0] : mu == 1 ? v[1] : mu == 2 ? v[2] : v[3];
+}
+
+// out = hop(in) at `site` in float-float (in: float-float field, HALF: one parity indexed
+// site >> 1).  The eight directions run in a loop that is not unrolled: one copy of the SU(3)
+// product serves all of them (a backward link enters as its adjoint, formed in registers),
+// since the fully unrolled float-float hop overflows the instruction cache.
+template <int SPR, int LPR, int REC, bool HALF>
+__device__ __forceinline__ void hop_ff(const LatGeom& g, FieldPtr in, int Vmax, int slot, int site,
+                                       const int (&x)[4], const int (&st)[4], cplx<ffl> (&out)[12]) {
+  static_assert(SPR == PRFF && LPR == PRFF, "float-float field and links");
+  cplx<ffz> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = {ffz(0), ffz(0)};
+  int L4[4] = {g.L[0], g.L[1], g.L[2], g.L[3]};
+#pragma unroll 1
+  for (int d = 0; d < 8; ++d) {
+    const int mu = d >> 1;
+    const bool fwd = (d & 1) == 0;
+    const int xm = sel4(x, mu), sm = sel4(st, mu), L = sel4(L4, mu);
+    const int nb = fwd ? ((xm + 1 == L) ? site - (L - 1) * sm : site + sm)
+                       : ((xm == 0) ? site + (L - 1) * sm : site - sm);
+    cplx<ffz> u[9], psi[12], h[6], w[6];
+    {
+      cplx<ffl> ul[9], pl[12];
+      LinkIO<LPR, REC>::load(g, mu, fwd ? site : nb, ul);
+      SpinorIO<SPR>::load_nc(in, Vmax, slot, HALF ? nb >> 1 : nb, pl);
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const cplx<ffl> e = fwd ? ul[3 * r + c] : ul[3 * c + r];   // U or U^dagger
+          u[3 * r + c] = {ffz(e.x.hi, e.x.lo), fwd ? ffz(e.y.hi, e.y.lo) : ffz(-e.y.hi, -e.y.lo)};
+        }
+#pragma unroll
+      for (int k = 0; k < 12; ++k) psi[k] = {ffz(pl[k].x.hi, pl[k].x.lo), ffz(pl[k].y.hi, pl[k].y.lo)};
+    }
+    switch (d) {
+      case 0: project<0, -1>(psi, h); break;
+      case 1: project<0, 1>(psi, h); break;
+      case 2: project<1, -1>(psi, h); break;
+      case 3: project<1, 1>(psi, h); break;
+      case 4: project<2, -1>(psi, h); break;
+      case 5: project<2, 1>(psi, h); break;
+      case 6: project<3, -1>(psi, h); break;
+      default: project<3, 1>(psi, h); break;
+    }
+    su3_mul<ffz, false>(u, h, w);
+    switch (d) {
+      case 0: accumulate<0, -1>(acc, w); break;
+      case 1: accumulate<0, 1>(acc, w); break;
+      case 2: accumulate<1, -1>(acc, w); break;
+      case 3: accumulate<1, 1>(acc, w); break;
+      case 4: accumulate<2, -1>(acc, w); break;
+      case 5: accumulate<2, 1>(acc, w); break;
+      case 6: accumulate<3, -1>(acc, w); break;
+      default: accumulate<3, 1>(acc, w); break;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) out[k] = {ffl_of(acc[k].x), ffl_of(acc[k].y)};
+}
+
 // hop = sum_mu [(1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^H psi(x-mu)]
 template <int SPR, int LPR, typename R>
 __device__ __forceinline__ void wilson_hop(const LatGeom& g, FieldPtr in, int Vmax, int slot, int site,
                                            const int (&x)[4], const int (&st)[4], cplx<R> (&acc)[12]) {
 #pragma unroll
   for (int k = 0; k < 12; ++k) acc[k] = {0, 0};
+  if constexpr (is_ffl<R>::value) {
+    hop_ff<SPR, LPR, 12, false>(g, in, Vmax, slot, site, x, st, acc);
+    return;
+  }
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
     const int L = g.L[mu];

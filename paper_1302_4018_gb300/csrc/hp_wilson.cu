@@ -774,7 +774,7 @@ __device__ __forceinline__ void ru_finalize(WArgs& a, SlotState* S, const double
 // float-float links, solution and arithmetic on the FP32 pipes (48-bit significand: the
 // rounding error of b - D x is ~1e-14 ||b||, far below any tolerance the solver certifies).
 template <int SPR, int NT>
-__global__ void __launch_bounds__(NT) k_ru_residual(WArgs a) {
+__global__ void __launch_bounds__(NT, 3) k_ru_residual(WArgs a) {
   SLOT_PREAMBLE(S->need_update == 2)
   typedef typename Real_of<SPR>::T R;
   const int comp = S->a, m = S->m;
@@ -973,6 +973,16 @@ __device__ __forceinline__ int eo_site(const LatGeom& g, int h, int par, int (&x
 template <int SPR, int LPR, int REC, typename R>
 __device__ __forceinline__ void eo_hop(const LatGeom& g, FieldPtr in, int Vs, int slot, int site, const int (&x)[4],
                                        const int (&st)[4], R sc, cplx<R> (&acc)[12]) {
+  if constexpr (is_ffl<R>::value) {   // float-float fields (norm 1): acc += sc hop
+    cplx<ffl> t[12];
+    hop_ff<SPR, LPR, REC, true>(g, in, Vs, slot, site, x, st, t);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      acc[k].x = fma(sc, t[k].x, acc[k].x);
+      acc[k].y = fma(sc, t[k].y, acc[k].y);
+    }
+    return;
+  }
 #pragma unroll
   for (int mu = 0; mu < 4; ++mu) {
     const int L = g.L[mu];
@@ -1047,8 +1057,11 @@ __global__ void __launch_bounds__(NT) k_eo_even(WArgs a, FieldPtr in, FieldPtr m
 //   EPI_G: group update r_g -= S e, r = r_g, (r^, r_g), ||r_g||^2   (in = e, mid FP32)
 enum { EPI_G = 3 };
 
+// at least five resident blocks of 128 threads (<= 102 registers): the odd-site kernels are
+// latency-bound, and the register count the compiler picks unconstrained halves the warps an SM holds
+#define EO_ODD_MINB 5
 template <int SIN, int SMID, int LPR, int REC, int NT, int EPI>
-__global__ void __launch_bounds__(NT) k_eo_odd(WArgs a, FieldPtr in, FieldPtr mid, FieldPtr out, int nslots) {
+__global__ void __launch_bounds__(NT, EO_ODD_MINB) k_eo_odd(WArgs a, FieldPtr in, FieldPtr mid, FieldPtr out, int nslots) {
   EO_PREAMBLE(EPI == EPI_G ? MASK_GROUP : MASK_RUN)
   typedef float R;
   constexpr int NQ = EPI == EPI_V ? 2 : 3;
@@ -1141,9 +1154,11 @@ __global__ void __launch_bounds__(NT) k_eo_odd(WArgs a, FieldPtr in, FieldPtr mi
   }
 }
 
+// the exact steps: at least EO_X_MINB resident blocks of 128 threads (register cap)
+#define EO_X_MINB 3
 // ---- exact step 1: x_e = d_e^-1 (b_e + k hop(x_o))   (FP64 or float-float)
 template <int PX, int NT>
-__global__ void __launch_bounds__(NT) k_eo_x1(WArgs a, int nslots) {
+__global__ void __launch_bounds__(NT, EO_X_MINB) k_eo_x1(WArgs a, int nslots) {
   EO_PREAMBLE(MASK_EXACT)
   typedef typename Real_of<PX>::T R;
   const int comp = S->a, m = S->m;
@@ -1176,7 +1191,7 @@ __global__ void __launch_bounds__(NT) k_eo_x1(WArgs a, int nslots) {
 
 // ---- exact step 2: r_o = b_o - d_o x_o + k hop(x_e); a fresh slot also sets r^ = p = r
 template <int SPR, int PX, int NT>
-__global__ void __launch_bounds__(NT) k_eo_x2(WArgs a, int nslots) {
+__global__ void __launch_bounds__(NT, EO_X_MINB) k_eo_x2(WArgs a, int nslots) {
   EO_PREAMBLE(MASK_EXACT)
   typedef typename Real_of<PX>::T R;
   typedef typename Real_of<SPR>::T RS;
@@ -1503,6 +1518,7 @@ struct WilsonEngine {
   // stencil kernels: one block per tile (gy) so that the lattice is swept once in site order
   dim3 grid() const { return dim3(nslots, gyb); }
   dim3 grid_stencil() const { return dim3(nslots, gy); }
+  // slots refilled together (the right-hand sides one thread carries must share a lattice)
   int group() const { return rpt; }
 
   hp_status setup(int ns, int Vmax, const LatGeom* lats_dev, SlotState* st, const hp_solver_opts& o, double tol,
@@ -1580,9 +1596,11 @@ struct WilsonEngine {
     return HP_OK;
   }
   // ---- even-odd steps
+  // grid of the even-odd kernels: one slot per block along x/z, tiles of NT sites along y
+  dim3 eo_grid() const { return stencil_grid(variant, nslots, gy); }
   template <int REC>
   hp_status eo_schur(int which) {   // which: 0 v = S p, 1 t = S s, 2 group update with e
-    dim3 gr = stencil_grid(variant, nslots, gy);
+    dim3 gr = eo_grid();
     constexpr int LPR = LinkPrecOf<SPR>::v;
     if (which == 0) {
       {
@@ -1617,7 +1635,7 @@ struct WilsonEngine {
     return full ? eo_schur<18>(which) : eo_schur<12>(which);
   }
   hp_status eo_exact() {
-    dim3 gr = stencil_grid(variant, nslots, gy);
+    dim3 gr = eo_grid();
     {
       ProfScope ps(ctx, PX == PR64 ? "k_eo_x1<fp64>" : "k_eo_x1<ff>");
       k_eo_x1<PX, NT><<<gr, NT, 0, ctx->stream>>>(a, nslots);
@@ -1657,7 +1675,7 @@ struct WilsonEngine {
       }
       HP_LAUNCH_CHECK();
       if (SPR != PR64) {
-        const dim3 gr = stencil_grid(variant, nslots, gy);
+        const dim3 gr = eo_grid();
         {
           ProfScope ps(ctx, "k_eo_src");
           k_eo_src<NT><<<gr, NT, 0, ctx->stream>>>(a, nslots);

@@ -451,16 +451,25 @@ def test_mixed_precision_true_residual_reaches_1e12(ctx, hp, prec):
 
 
 # ------------------------------------------------------------------ even-odd (Schur complement) iteration
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
-def test_even_odd_trace_parity(ctx, hp, prec):
-    dims = (4, 4, 4, 4)
+_ORACLE_CACHE = {}
+
+
+# variant 0: the default (slot groups of 4, 18-real links); 4001: 12-real links (row 3 rebuilt);
+# 2101: slot groups of 2
+@pytest.mark.parametrize("prec,variant", [("fp64", 0), ("fp32", 0), ("fp16", 0), ("bf16", 0), ("fp16", 4001),
+                                          ("fp32", 4001), ("bf16", 2101)])
+def test_even_odd_trace_parity(ctx, hp, prec, variant):
+    dims = (4, 4, 6, 4)   # 384 sites, 192 per parity: the second 128-site tile is ragged
     U = synth.gauge_links(dims, 0.3, 1002)
     mf = synth.mass_field(dims, 0.01, 77)
     op = ctx.make_operator(hp.OP_WILSON, 0.01, 0.115, links_dev(U), dev(mf))
     s = 6
-    T, _, st = ctx.trace_inv(op, dims, s, 1e-10, ctx.make_opts(prec, z0_seed=2002, rhs_block=24, even_odd=1))
-    T_ref = E.trace_prefix(E.wilson_quadratures(dims, U, 0.115, 0, s, 2002, mass=0.01, mass_field=mf,
-                                                method="dense"))
+    T, _, st = ctx.trace_inv(op, dims, s, 1e-10, ctx.make_opts(prec, z0_seed=2002, rhs_block=24, even_odd=1,
+                                                               rhs_per_thread=variant))
+    if "eo_parity" not in _ORACLE_CACHE:
+        _ORACLE_CACHE["eo_parity"] = E.trace_prefix(E.wilson_quadratures(dims, U, 0.115, 0, s, 2002, mass=0.01,
+                                                                         mass_field=mf, method="dense"))
+    T_ref = _ORACLE_CACHE["eo_parity"]
     assert np.all(rel(T, T_ref) <= TRACE_RTOL), (T, T_ref)
     assert st["max_true_residual"] <= 1e-10 and st["rhs_solved"] == 12 * s
 

@@ -89,3 +89,92 @@ def test_problem_size_golden():
     rows = {r[0]: int(r[1]) for r in read_golden("problem_size.txt")}
     n = 3 * 4 * rows["Ls"] ** 3 * rows["Lt"]
     assert n == 25165824 and round(n / 2 ** 20) == rows["approx_millions"]
+
+
+# ------------------------------------------------------------------ clover term
+def test_sigma_munu_closed_forms():
+    """sigma_{mu nu} = (i/2)[g_mu, g_nu] in the chiral basis, worked out by hand from the gammas:
+    sigma_jk = -eps_jkl diag(s_l, s_l) and sigma_k4 = diag(s_k, -s_k) (k, j, l spatial)."""
+    s = O.pauli()
+    Z = np.zeros((2, 2), dtype=complex)
+    blk = lambda a, b: np.block([[a, Z], [Z, b]])
+    eps = {(0, 1, 2): 1, (1, 2, 0): 1, (2, 0, 1): 1, (1, 0, 2): -1, (2, 1, 0): -1, (0, 2, 1): -1}
+    for (j, k, l), e in eps.items():
+        assert np.allclose(O.sigma_munu(j, k), -e * blk(s[l], s[l]), atol=1e-15)
+    for k in range(3):
+        assert np.allclose(O.sigma_munu(k, 3), blk(s[k], -s[k]), atol=1e-15)
+        assert np.allclose(O.sigma_munu(3, k), -blk(s[k], -s[k]), atol=1e-15)
+    g5 = O.gamma_matrices()[4]
+    for mu in range(4):
+        for nu in range(4):
+            sm = O.sigma_munu(mu, nu)
+            assert np.allclose(sm, np.conj(sm).T) and np.allclose(sm @ g5, g5 @ sm)
+
+
+def test_clover_field_of_constant_abelian_field():
+    """U_1(x) = exp(i b x_2 lam), lam = diag(1, -1, 0), b = 2 pi / L_2, all other links 1: every
+    plaquette of the 1-2 plane is exp(-i b lam), so F_12 = -sin(b lam) everywhere, F_21 = -F_12,
+    and the other planes carry no field."""
+    dims = (3, 6, 2, 2)
+    V = int(np.prod(dims))
+    b = 2 * np.pi / dims[1]
+    lam = np.array([1.0, -1.0, 0.0])
+    U = np.broadcast_to(np.eye(3, dtype=complex), (V, 4, 3, 3)).copy()
+    for i in range(V):
+        x2 = (i // dims[0]) % dims[1]
+        U[i, 0] = np.diag(np.exp(1j * b * x2 * lam))
+    F = O.clover_field(U, dims, 0, 1)
+    assert np.allclose(F, np.diag(-np.sin(b * lam))[None], atol=1e-14)
+    assert np.allclose(O.clover_field(U, dims, 1, 0), -F, atol=1e-14)
+    for mu, nu in [(0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]:
+        assert np.allclose(O.clover_field(U, dims, mu, nu), 0, atol=1e-14)
+    C = O.clover_term(U, dims, 0.12, 1.5)
+    assert np.allclose(C, -1.5 * 0.12 * np.kron(O.sigma_munu(0, 1), np.diag(-np.sin(b * lam)))[None], atol=1e-14)
+
+
+def test_clover_field_is_gauge_covariant_and_hermitian():
+    """Under U'_mu(x) = g(x) U_mu(x) g(x+mu)^H every closed leaf turns into g(x) Q g(x)^H: a leaf
+    that is not a closed path through x breaks this."""
+    dims = (2, 4, 3, 2)
+    U = synth.gauge_links(dims, 0.5, 61)
+    Ug, g = synth.gauge_transform(U, dims, 62)
+    for mu, nu in [(0, 1), (0, 3), (1, 2), (2, 3)]:
+        F = O.clover_field(U, dims, mu, nu)
+        Fg = O.clover_field(Ug, dims, mu, nu)
+        assert np.allclose(Fg, g @ F @ np.conj(np.swapaxes(g, -1, -2)), atol=1e-13)
+        assert np.allclose(F, np.conj(np.swapaxes(F, -1, -2)), atol=1e-14)
+        assert np.allclose(np.trace(F, axis1=1, axis2=2), 0, atol=1e-14)
+        assert np.max(np.abs(F)) > 1e-3
+
+
+def test_clover_wilson_dense_apply_adjoint_and_gauge_invariant_trace():
+    dims = (2, 2, 2, 4)
+    V = int(np.prod(dims))
+    U = synth.gauge_links(dims, 0.6, 63)
+    C = O.clover_term(U, dims, 0.12, 1.3)
+    D = O.wilson_dense(U, dims, 0.12, 0.02, clover=C)
+    psi = synth.random_spinors(dims, 1, 64)[0]
+    assert np.allclose(D @ psi.reshape(-1), O.wilson_apply(psi, U, dims, 0.12, 0.02, clover=C).reshape(-1),
+                       atol=1e-13)
+    assert np.allclose(np.conj(D).T @ psi.reshape(-1),
+                       O.wilson_apply(psi, U, dims, 0.12, 0.02, dagger=True, clover=C).reshape(-1), atol=1e-13)
+    G5 = np.kron(np.eye(V), np.kron(O.gamma_matrices()[4], np.eye(3)))
+    assert np.allclose(np.conj(D).T, G5 @ D @ G5, atol=1e-14)          # gamma_5-hermiticity survives
+    Ug, _ = synth.gauge_transform(U, dims, 65)
+    Dg = O.wilson_dense(Ug, dims, 0.12, 0.02, clover=O.clover_term(Ug, dims, 0.12, 1.3))
+    t, tg = np.trace(np.linalg.inv(D)), np.trace(np.linalg.inv(Dg))
+    assert abs(t - tg) <= 1e-11 * abs(t)
+    assert abs(t - np.trace(np.linalg.inv(O.wilson_dense(U, dims, 0.12, 0.02)))) > 1e-6 * abs(t)
+
+
+def test_clover_vanishes_on_pure_gauge_links():
+    """A gauge transform of the free field has unit plaquettes: F = 0, and the clover-Wilson
+    trace keeps the free-field closed form."""
+    dims = (4, 2, 2, 4)
+    V = int(np.prod(dims))
+    Ufree = np.broadcast_to(np.eye(3, dtype=complex), (V, 4, 3, 3)).copy()
+    Ug, _ = synth.gauge_transform(Ufree, dims, 66)
+    assert np.allclose(O.clover_term(Ug, dims, 0.12, 1.7), 0, atol=1e-14)
+    D = O.wilson_dense(Ug, dims, 0.12, 0.0, clover=O.clover_term(Ug, dims, 0.12, 1.7))
+    exact = free_wilson_trace_inverse(dims, 0.12)
+    assert abs(np.trace(np.linalg.inv(D)).real - exact) <= 1e-10 * exact
