@@ -156,6 +156,9 @@ def kernel_bytes(name, prec, V, c):
     n, it, la = c["eo"], c["rhs_iters"], c["launches"]
     Vf = V // 2 if n else V                   # sites of the iterated vectors
     links = 4 * V * L * la
+    if c.get("clover") and (name.startswith("k_eo_even") or name.startswith("k_eo_odd") or name.startswith("k_bicg_v")
+                            or name.startswith("k_bicg_t")):
+        links += Vf * 288 * la                # the FP32 clover blocks of the sites written, once per launch
     if name.startswith("k_bicg_v"):
         return Vf * 3 * S * it + links
     if name.startswith("k_bicg_t"):
@@ -219,7 +222,7 @@ def run_ours(args):
         return first
 
     def step(first, links, precision=prec, probes=P, rhs_block=args.rhs_block):
-        op = ctx.make_operator(hprobe.OP_WILSON, 0.0, KAPPA, links, None)
+        op = ctx.make_operator(hprobe.OP_WILSON, 0.0, KAPPA, links, None, csw=args.csw)
         s_max = first + probes
         opts = ctx.make_opts(precision, z0_seed=Z0_SEED, first=first, rhs_block=rhs_block,
                              even_odd=1 if args.even_odd else 0)
@@ -298,7 +301,7 @@ def run_ours(args):
     peak, peak_kind = hbm_peak()
     dslash = None
     if not args.no_dslash:
-        op = ctx.make_operator(hprobe.OP_WILSON, 0.0, KAPPA, links_dev, None)
+        op = ctx.make_operator(hprobe.OP_WILSON, 0.0, KAPPA, links_dev, None, csw=args.csw)
         ds = ctx.dslash_bench(op, DIMS, prec, args.rhs_block, 20)
         ds64 = ctx.dslash_bench(op, DIMS, "fp64", 1, 5)
         dslash = {"precision": prec, "nrhs": args.rhs_block, "ms": ds["ms"], "GBps": ds["bytes"] / ds["ms"] / 1e6,
@@ -309,7 +312,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel of the timed steps (event-timed launches, algorithmic bytes)
     counts = {"rhs_iters": iters, "updates": updates, "exact": updates + (rhs if args.even_odd and prec == "fp64" else 0),
-              "groups": sum(s["group_updates"] for s in stats), "eo": bool(args.even_odd)}
+              "groups": sum(s["group_updates"] for s in stats), "eo": bool(args.even_odd), "clover": bool(args.csw)}
     kernels = {}
     for name, rec in prof.items():
         b = kernel_bytes(name, prec, V, dict(counts, launches=rec["launches"]))
@@ -329,8 +332,8 @@ def run_ours(args):
                 "mean_launch_ms": top_rec["ms"] / top_rec["launches"],
                 "traffic": trace_ncu}
 
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+    cpu = None   # (the oracle's clover term is a per-site Python loop: no sampled baseline with --csw)
+    if rank == 0 and not args.no_cpu_baseline and ws == 1 and not args.csw:
         cpu = cpu_baseline(FP64_ITERS_PER_SOLVE)
 
     out = {
@@ -339,10 +342,13 @@ def run_ours(args):
         "dtype": {"fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math",
                   "fp64": "f64"}[prec] + " + f64 reliable updates",
         "data": "synthetic: SU(3) links exp(i eps H), seeded (no gauge ensemble available)",
-        "config": {"workload": "%s Wilson-Dirac, kappa 0.12, eps 0.4, %d probes x 12 dilutions per step, "
-                               "BiCGStab %s%s, tol 1e-10" % ("x".join(map(str, DIMS)), P, prec,
+        "config": {"workload": "%s %s, kappa 0.12, eps 0.4, %d probes x 12 dilutions per step, "
+                               "BiCGStab %s%s, tol 1e-10" % ("x".join(map(str, DIMS)),
+                                                              "Clover-Wilson (c_sw %g)" % args.csw if args.csw
+                                                              else "Wilson-Dirac", P, prec,
                                                               " on the even-odd Schur complement"
                                                               if args.even_odd else ""),
+                   "csw": args.csw,
                    "even_odd": bool(args.even_odd),
                    "lattice": list(DIMS), "probes_per_step": P, "rhs_per_step": 12 * P, "rhs_block": args.rhs_block,
                    "precision": prec, "tol": TOL, "l2": "inputs larger than L2 (each field >= 100 MB)",
@@ -541,6 +547,8 @@ def main():
     ap.add_argument("--lattice", default=None,
                     help="L1,L2,L3,L4: another lattice for the headline path (profiling small cases; "
                          "not the benchmark workload)")
+    ap.add_argument("--csw", type=float, default=0.0,
+                    help="clover coefficient of the Clover-Wilson operator (0: plain Wilson, the headline)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
     args = ap.parse_args()

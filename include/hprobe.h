@@ -112,21 +112,29 @@ hp_status hp_probe_vectors(hp_ctx* ctx, const hp_lattice* lat, int64_t first, in
 typedef enum { HP_OP_LAPLACIAN = 0, HP_OP_WILSON = 1 } hp_op_kind;
 
 /* The operator A (Section 5: shifted periodic Laplacian; Section 1.1.1 and
- * 5.3: Wilson-Dirac matrix, here without the clover term).
+ * 5.3: Wilson-Dirac matrix, with the clover term of the Clover-Wilson
+ * discretisation Section 5.3 uses when csw != 0).
  *   Laplacian:  (A x)(s) = (8 + mass + mu(s)) x(s) - sum_mu [x(s+mu) + x(s-mu)]
- *   Wilson:     (D psi)(s) = (1 + mass + mu(s)) psi(s)
+ *   Wilson:     (D psi)(s) = (1 + mass + mu(s)) psi(s) + C(s) psi(s)
  *                 - kappa sum_mu [(1 - g_mu) U_mu(s) psi(s+mu) + (1 + g_mu) U_mu(s-mu)^H psi(s-mu)]
  *     chiral gamma basis: g_k = [[0, -i sigma_k], [i sigma_k, 0]] (k = 1..3),
  *     g_4 = [[0, 1], [1, 0]], g_5 = diag(1, 1, -1, -1); direction mu = k runs along x_k.
+ *     Clover (Sheikholeslami-Wohlert) term:
+ *       C(s) = -csw kappa sum_{mu<nu} sigma_{mu nu} (x) F_{mu nu}(s),  sigma_{mu nu} = (i/2)[g_mu, g_nu],
+ *       F_{mu nu} = traceless part of (Q_{mu nu} - Q_{mu nu}^H) / (8i), Q_{mu nu}(s) the four
+ *       plaquettes of the mu-nu plane that start and end at s, each run mu-then-nu.
  * links: Wilson only, complex128 [V][4][3][3] (row-major 3x3 per site and
  *        direction, real/imaginary interleaved), host or device, special unitary.
- * mass_field: optional mu(s), double[V], host or device; NULL means 0. */
+ * mass_field: optional mu(s), double[V], host or device; NULL means 0.
+ * csw: clover coefficient, Wilson only (0: plain Wilson; the Laplacian requires 0);
+ *      the 12x12 diagonal blocks 1 + mass + mu(s) + C(s) must be invertible. */
 typedef struct {
     int32_t kind;
     double mass;
     double kappa;
     const double* links;
     const double* mass_field;
+    double csw;
 } hp_operator;
 
 typedef enum {
@@ -234,7 +242,8 @@ hp_status hp_operator_apply(hp_ctx* ctx, const hp_operator* op, const hp_lattice
  * call on each device resolves the array's device address
  * (cudaGetSymbolAddress), so make it before any stream capture.
  * Errors: HP_EINVAL for a lattice above 20736 sites (12^4), ndim outside
- * [1, 4], nrhs < 1, host pointers or a non-Wilson operator. */
+ * [1, 4], nrhs < 1, host pointers, a non-Wilson operator or csw != 0 (the
+ * clover blocks would need workspace). */
 hp_status hp_operator_apply_noalloc(const hp_operator* op, const hp_lattice* lat, int64_t nrhs,
                                     const double* in_dev, double* out_dev, void* cuda_stream);
 

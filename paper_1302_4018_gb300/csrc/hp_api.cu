@@ -81,8 +81,12 @@ static hp_status operator_geom(hp_ctx* ctx, const hp_operator* op, const hp_latt
     hp_set_error("unknown operator kind %d", op->kind);
     return HP_EINVAL;
   }
-  if (!std::isfinite(op->mass) || !std::isfinite(op->kappa)) {
-    hp_set_error("operator mass / kappa not finite");
+  if (!std::isfinite(op->mass) || !std::isfinite(op->kappa) || !std::isfinite(op->csw)) {
+    hp_set_error("operator mass / kappa / csw not finite");
+    return HP_EINVAL;
+  }
+  if (op->kind == HP_OP_LAPLACIAN && op->csw != 0.0) {
+    hp_set_error("the clover term (csw != 0) belongs to the Wilson operator");
     return HP_EINVAL;
   }
   if (op->kind == HP_OP_WILSON && !op->links) {

@@ -715,7 +715,126 @@ __device__ __forceinline__ void wilson_hop(const LatGeom& g, FieldPtr in, int Vm
   }
 }
 
-// (D psi)(x) = (1 + m + mu(x)) psi(x) - kappa hop; psi(x) returned in `center`
+// ---- the clover diagonal A(x) (or A(x)^-1): two packed Hermitian 6x6 blocks per site
+template <typename R>
+struct ClovLoad;
+template <>
+struct ClovLoad<double> {
+  __device__ static __forceinline__ void load(const LatGeom& g, bool inv, int site, int b, double (&a)[36]) {
+    const double2* p = (inv ? g.Ai64 : g.A64) + (size_t)(18 * b) * g.V + site;
+#pragma unroll
+    for (int k = 0; k < 18; ++k) {
+      const double2 v = __ldg(p + (size_t)k * g.V);
+      a[2 * k] = v.x;
+      a[2 * k + 1] = v.y;
+    }
+  }
+};
+template <>
+struct ClovLoad<float> {
+  __device__ static __forceinline__ void load(const LatGeom& g, bool inv, int site, int b, float (&a)[36]) {
+    const float4* p = (inv ? g.Ai32 : g.A32) + (size_t)(9 * b) * g.V + site;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float4 v = __ldg(p + (size_t)k * g.V);
+      a[4 * k] = v.x;
+      a[4 * k + 1] = v.y;
+      a[4 * k + 2] = v.z;
+      a[4 * k + 3] = v.w;
+    }
+  }
+};
+template <>
+struct ClovLoad<ffl> {
+  __device__ static __forceinline__ void load(const LatGeom& g, bool inv, int site, int b, ffl (&a)[36]) {
+    const float4* p = (inv ? g.Ai32 : g.A32) + (size_t)(9 * b) * g.V + site;
+    const float4* q = (inv ? g.Ai32l : g.A32l) + (size_t)(9 * b) * g.V + site;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float4 v = __ldg(p + (size_t)k * g.V), w = __ldg(q + (size_t)k * g.V);
+      a[4 * k] = ffl(v.x, w.x);
+      a[4 * k + 1] = ffl(v.y, w.y);
+      a[4 * k + 2] = ffl(v.z, w.z);
+      a[4 * k + 3] = ffl(v.w, w.w);
+    }
+  }
+};
+
+// out = A(x) in (inv: A(x)^-1 in); block b acts on components 6b..6b+5 (spins 2b, 2b+1)
+template <typename R>
+__device__ __forceinline__ void clover_mul(const LatGeom& g, bool inv, int site, const cplx<R> (&in)[12],
+                                           cplx<R> (&out)[12]) {
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    R a[36];
+    ClovLoad<R>::load(g, inv, site, b, a);
+    cplx<R> y[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) y[i] = {a[i] * in[6 * b + i].x, a[i] * in[6 * b + i].y};
+    int k = 6;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = i + 1; j < 6; ++j) {
+        const R ax = a[k], ay = a[k + 1];
+        k += 2;
+        const cplx<R> xi = in[6 * b + i], xj = in[6 * b + j];
+        y[i].x = fma(ax, xj.x, y[i].x);   // y_i += A_ij x_j
+        y[i].x = fma(-ay, xj.y, y[i].x);
+        y[i].y = fma(ax, xj.y, y[i].y);
+        y[i].y = fma(ay, xj.x, y[i].y);
+        y[j].x = fma(ax, xi.x, y[j].x);   // y_j += conj(A_ij) x_i
+        y[j].x = fma(ay, xi.y, y[j].x);
+        y[j].y = fma(ax, xi.y, y[j].y);
+        y[j].y = fma(-ay, xi.x, y[j].y);
+      }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) out[6 * b + i] = y[i];
+  }
+}
+
+// float-float: the same products with lazily normalised sums (ffz), one renormalisation per entry
+template <>
+__device__ __forceinline__ void clover_mul<ffl>(const LatGeom& g, bool inv, int site, const cplx<ffl> (&in)[12],
+                                                cplx<ffl> (&out)[12]) {
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    ffz a[36];
+    {
+      ffl al[36];
+      ClovLoad<ffl>::load(g, inv, site, b, al);
+#pragma unroll
+      for (int k = 0; k < 36; ++k) a[k] = ffz(al[k].hi, al[k].lo);
+    }
+    cplx<ffz> x[6], y[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      x[i] = {ffz(in[6 * b + i].x.hi, in[6 * b + i].x.lo), ffz(in[6 * b + i].y.hi, in[6 * b + i].y.lo)};
+      y[i] = {fma(a[i], x[i].x, ffz(0)), fma(a[i], x[i].y, ffz(0))};
+    }
+    int k = 6;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = i + 1; j < 6; ++j) {
+        const ffz ax = a[k], ay = a[k + 1];
+        k += 2;
+        y[i].x = fma(ax, x[j].x, y[i].x);
+        y[i].x = fma(-ay, x[j].y, y[i].x);
+        y[i].y = fma(ax, x[j].y, y[i].y);
+        y[i].y = fma(ay, x[j].x, y[i].y);
+        y[j].x = fma(ax, x[i].x, y[j].x);
+        y[j].x = fma(ay, x[i].y, y[j].x);
+        y[j].y = fma(ax, x[i].y, y[j].y);
+        y[j].y = fma(-ay, x[i].x, y[j].y);
+      }
+#pragma unroll
+    for (int i = 0; i < 6; ++i) out[6 * b + i] = {ffl_of(y[i].x), ffl_of(y[i].y)};
+  }
+}
+
+// (D psi)(x) = (1 + m + mu(x)) psi(x) - kappa hop, or A(x) psi(x) - kappa hop with the clover
+// term; psi(x) returned in `center`
 template <int SPR, int LPR, typename R>
 __device__ __forceinline__ void wilson_site(const LatGeom& g, FieldPtr in, int Vmax, int slot, int site,
                                             cplx<R> (&out)[12], cplx<R> (&center)[12]) {
@@ -724,8 +843,18 @@ __device__ __forceinline__ void wilson_site(const LatGeom& g, FieldPtr in, int V
   cplx<R> hop[12];
   wilson_hop<SPR, LPR, R>(g, in, Vmax, slot, site, x, st, hop);
   SpinorIO<SPR>::load_nc(in, Vmax, slot, site, center);
-  R diag = (R)(1.0 + g.mass + (g.mass_field ? g.mass_field[site] : 0.0));
   R kap = (R)g.kappa;
+  if (g.clover) {   // A(x) psi(x) - kappa hop
+    cplx<R> ac[12];
+    clover_mul<R>(g, false, site, center, ac);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      out[k].x = ac[k].x - kap * hop[k].x;
+      out[k].y = ac[k].y - kap * hop[k].y;
+    }
+    return;
+  }
+  R diag = (R)(1.0 + g.mass + (g.mass_field ? g.mass_field[site] : 0.0));
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
     out[k].x = diag * center[k].x - kap * hop[k].x;

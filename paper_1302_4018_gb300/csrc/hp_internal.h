@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <map>
 #include <memory>
 #include <string>
@@ -75,6 +76,17 @@ struct LatGeom {
   const unsigned int* U16g;   // [4][V]     entry 8
   const float4* U32fl;        // [4][4][V]  low parts (u - (float)u) of entries 0-7, float-float links
   const float2* U32gl;        // [4][V]     low part of entry 8
+  // clover term: A(x) = (1 + m + mu(x)) + C(x) (Wilson diagonal plus the Sheikholeslami-Wohlert
+  // term) as two Hermitian 6x6 blocks per site (spins 0-1 and 2-3: C commutes with gamma_5),
+  // each packed as 6 real diagonal entries then the 15 entries above the diagonal (row-major)
+  // as (re, im): 36 reals per block, 72 per site; Ai* hold A(x)^-1 in the same form.
+  int clover;                 // 1: the diagonal is A(x) (arrays below), 0: 1 + m + mu(x)
+  const double2* A64;         // [36][V]
+  const float4* A32;          // [18][V]
+  const float4* A32l;         // [18][V] low parts (float-float)
+  const double2* Ai64;
+  const float4* Ai32;
+  const float4* Ai32l;
   int dof;                    // unknowns per site that carry a source (12 Wilson, 1 Laplacian)
   int parts;                  // Laplacian: 2 when probes are complex (re, im solved apart)
 };
@@ -123,6 +135,15 @@ struct hp_ctx {
   std::vector<cudaEvent_t> event_pool;
   std::map<std::string, int> autotune;       // key -> threads per block
   long long launches = 0;                    // kernels launched (graph replays included)
+  // clover blocks kept per workspace tag: rebuilt only when the links, mass field or
+  // coefficients they came from change (a 64-bit hash of the input bits is compared)
+  struct CloverKey {
+    unsigned long long hash = 0;
+    double csw = 0, kappa = 0, mass = 0;
+    int V = 0;
+    const void* buf = nullptr;
+  };
+  std::map<std::string, CloverKey> clover_keys;
 };
 
 // workspace
@@ -143,6 +164,13 @@ struct ProfScope {
   ~ProfScope() { hp_prof_end(ctx, name, a); }
 };
 
+// grid-stride launches: enough blocks for n items, at most 16 per SM
+static inline int blocks_for(hp_ctx* ctx, long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  long long cap = (long long)ctx->num_sms * 16;
+  return (int)std::max(1LL, std::min(b, cap));
+}
+
 // lattice setup (hp_core.cu)
 hp_status hp_validate_lattice(const hp_lattice* lat, int max_nd, std::vector<int64_t>* dims);
 hp_status hp_get_lattice(hp_ctx* ctx, const std::vector<int64_t>& dims, LatticeSetup** out);
@@ -156,6 +184,8 @@ bool hp_is_device_ptr(const void* p);
 // layouts of `geom` (allocated in workspace under `tag`)
 hp_status hp_prepare_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom* geom, const char* tag, int need_prec);
 hp_status hp_prepare_mass(hp_ctx* ctx, const hp_operator* op, LatGeom* geom, const char* tag);
+// clover blocks A and A^-1 (hp_clover.cu); needs the FP64 links U64 and the mass field of `geom`
+hp_status hp_prepare_clover(hp_ctx* ctx, const hp_operator* op, LatGeom* geom, const char* tag);
 
 // ------------------------------------------------------------- solver API
 struct SolveProblem {

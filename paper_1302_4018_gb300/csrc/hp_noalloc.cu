@@ -138,6 +138,10 @@ extern "C" hp_status hp_operator_apply_noalloc(const hp_operator* op, const hp_l
     hp_set_error("hp_operator_apply_noalloc: a Wilson operator with links is required");
     return HP_EINVAL;
   }
+  if (op->csw != 0.0) {
+    hp_set_error("hp_operator_apply_noalloc: plain Wilson only (csw = 0): the clover blocks need workspace");
+    return HP_EINVAL;
+  }
   if (lat->ndim < 1 || lat->ndim > 4) {
     hp_set_error("hp_operator_apply_noalloc: ndim = %d outside [1, 4]", lat->ndim);
     return HP_EINVAL;

@@ -71,12 +71,6 @@ __global__ void k_links_convert(const double2* __restrict__ in, int V, double2* 
   }
 }
 
-static int blocks_for(hp_ctx* ctx, long long n, int threads) {
-  long long b = (n + threads - 1) / threads;
-  long long cap = (long long)ctx->num_sms * 16;
-  return (int)std::max(1LL, std::min(b, cap));
-}
-
 __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = (float)in[i];
 }
@@ -145,7 +139,7 @@ hp_status hp_prepare_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom* g, cons
   g->U16g = (const unsigned int*)u16g;
   g->U32fl = (const float4*)u32fl;
   g->U32gl = (const float2*)u32gl;
-  return HP_OK;
+  return hp_prepare_clover(ctx, op, g, tag);
 }
 
 template <int SPR>
@@ -296,6 +290,29 @@ __device__ __forceinline__ double site_diag<double>(const LatGeom& g, int site) 
   return 1.0 + g.mass + (g.mass_field ? g.mass_field[site] : 0.0);
 }
 
+// acc += n * (diagonal term) c: (1 + m + mu(x)) n c, or n A(x) c with the clover term (CL = false:
+// the caller knows there is none)
+template <typename R, bool CL = true>
+__device__ __forceinline__ void add_diag(const LatGeom& g, int site, const cplx<R> (&c)[12], R n,
+                                         cplx<R> (&acc)[12]) {
+  if (CL && g.clover) {
+    cplx<R> ac[12];
+    clover_mul<R>(g, false, site, c, ac);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      acc[k].x = fma(n, ac[k].x, acc[k].x);
+      acc[k].y = fma(n, ac[k].y, acc[k].y);
+    }
+    return;
+  }
+  const R dn = site_diag<R>(g, site) * n;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    acc[k].x = fma(dn, c[k].x, acc[k].x);
+    acc[k].y = fma(dn, c[k].y, acc[k].y);
+  }
+}
+
 // ---- the stencil on RPT right-hand sides per thread
 // Thread = one site; it loads (and reconstructs) each of the 8 links of the
 // site once and applies it to RPT slots of the same lattice.  Epilogues:
@@ -404,19 +421,13 @@ __global__ void __launch_bounds__(NT) k_wds(WArgs a, FieldPtr in, FieldPtr out, 
         if (mu == 3) accumulate_s<3, 1>(acc[r], w, sc);
       }
     }
-    const R diag = site_diag<R>(g, site);
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       if (!act[r]) continue;
       cplx<R> c[12];
       R nc;
       SpinorIO<SPR>::load_nc_raw(in, a.Vmax, slot0 + r, site, c, nc);
-      const R dn = diag * nc;
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        acc[r][k].x = fma(dn, c[k].x, acc[r][k].x);
-        acc[r][k].y = fma(dn, c[k].y, acc[r][k].y);
-      }
+      add_diag<R>(g, site, c, nc, acc[r]);
       SpinorIO<SPR>::store(out, a.Vmax, slot0 + r, site, acc[r]);
       if (EPI == EPI_V) {
         cplx<R> rh[12];
@@ -1033,9 +1044,11 @@ __device__ __forceinline__ double leading_part(ffl v) { return (double)v.hi; }
   (void)nparts;                                                           \
   (void)part;
 
-// ---- even sites: mid = d_e^-1 hop(in_o)
-template <int SIN, int LPR, int REC, int SOUT, int NT, int MASK>
-__global__ void __launch_bounds__(NT) k_eo_even(WArgs a, FieldPtr in, FieldPtr mid, int nslots) {
+// ---- even sites: mid = d_e^-1 hop(in_o)  (register caps: six resident blocks, <= 85 registers, for
+// the iteration's launches -- left alone the compiler takes 160 and halves the warps; four for the
+// group update)
+template <int SIN, int LPR, int REC, int SOUT, int NT, int MASK, bool CL>
+__global__ void __launch_bounds__(NT, MASK == MASK_RUN ? 6 : 4) k_eo_even(WArgs a, FieldPtr in, FieldPtr mid, int nslots) {
   EO_PREAMBLE(MASK)
   typedef float R;
   for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
@@ -1043,6 +1056,17 @@ __global__ void __launch_bounds__(NT) k_eo_even(WArgs a, FieldPtr in, FieldPtr m
     if (h >= nsite) continue;
     int x[4], st[4];
     const int site = eo_site(g, h, 0, x, st);
+    if constexpr (CL) {
+      if (g.clover) {   // A_e(x)^-1 hop
+        cplx<R> acc[12], t[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = {(R)0, (R)0};
+        eo_hop<SIN, LPR, REC, R>(g, in, a.Vmax, slot, site, x, st, (R)1, acc);
+        clover_mul<R>(g, true, site, acc, t);
+        SpinorIO<SOUT>::store(mid, a.Vmax, slot, h, t);
+        continue;
+      }
+    }
     const R inv = (R)1 / site_diag<R>(g, site);
     cplx<R> acc[12];
 #pragma unroll
@@ -1060,7 +1084,7 @@ enum { EPI_G = 3 };
 // at least five resident blocks of 128 threads (<= 102 registers): the odd-site kernels are
 // latency-bound, and the register count the compiler picks unconstrained halves the warps an SM holds
 #define EO_ODD_MINB 5
-template <int SIN, int SMID, int LPR, int REC, int NT, int EPI>
+template <int SIN, int SMID, int LPR, int REC, int NT, int EPI, bool CL>
 __global__ void __launch_bounds__(NT, EO_ODD_MINB) k_eo_odd(WArgs a, FieldPtr in, FieldPtr mid, FieldPtr out, int nslots) {
   EO_PREAMBLE(EPI == EPI_G ? MASK_GROUP : MASK_RUN)
   typedef float R;
@@ -1080,12 +1104,7 @@ __global__ void __launch_bounds__(NT, EO_ODD_MINB) k_eo_odd(WArgs a, FieldPtr in
     eo_hop<SMID, LPR, REC, R>(g, mid, a.Vmax, slot, site, x, st, mk2, acc);
     R nc;
     SpinorIO<SIN>::load_nc_raw(in, a.Vmax, slot, h, c, nc);
-    const R dn = site_diag<R>(g, site) * nc;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      acc[k].x = fma(dn, c[k].x, acc[k].x);
-      acc[k].y = fma(dn, c[k].y, acc[k].y);
-    }
+    add_diag<R, CL>(g, site, c, nc, acc);
     if (EPI == EPI_G) {
       cplx<R> rg[12], rh[12];
       SpinorIO<PR32>::load(a.rg, a.Vmax, slot, h, rg);
@@ -1175,13 +1194,21 @@ __global__ void __launch_bounds__(NT, EO_X_MINB) k_eo_x1(WArgs a, int nslots) {
     for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
     eo_hop<PX, PX, 12, R>(g, xo, a.Vmax, slot, site, x, st, kap, acc);
     const double2 bv = source_value(g, site, m);
-    const R inv = R(1.0 / (1.0 + g.mass + (g.mass_field ? g.mass_field[site] : 0.0)));
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
+    for (int k = 0; k < 12; ++k)
       if (k == comp) {
         acc[k].x = acc[k].x + R(bv.x);
         acc[k].y = acc[k].y + R(bv.y);
       }
+    if (g.clover) {   // A_e(x)^-1 (b_e + k hop)
+      cplx<R> t[12];
+      clover_mul<R>(g, true, site, acc, t);
+      SpinorIO<PX>::store(xe, a.Vmax, slot, h, t);
+      continue;
+    }
+    const R inv = R(1.0 / (1.0 + g.mass + (g.mass_field ? g.mass_field[site] : 0.0)));
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
       acc[k].x = inv * acc[k].x;
       acc[k].y = inv * acc[k].y;
     }
@@ -1212,7 +1239,13 @@ __global__ void __launch_bounds__(NT, EO_X_MINB) k_eo_x2(WArgs a, int nslots) {
     for (int k = 0; k < 12; ++k) acc[k] = {R(0), R(0)};
     eo_hop<PX, PX, 12, R>(g, xe, a.Vmax, slot, site, x, st, kap, acc);
     SpinorIO<PX>::load_nc(xo, a.Vmax, slot, h, c);
-    const R d = R(1.0 + g.mass + (g.mass_field ? g.mass_field[site] : 0.0));
+    if (g.clover) {   // c := A_o(x) x_o, subtracted below with d = 1
+      cplx<R> t[12];
+      clover_mul<R>(g, false, site, c, t);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) c[k] = t[k];
+    }
+    const R d = g.clover ? R(1.0) : R(1.0 + g.mass + (g.mass_field ? g.mass_field[site] : 0.0));
     const double2 bv = source_value(g, site, m);
     cplx<RS> rs[12];
     cplx<float> rf[12];
@@ -1360,11 +1393,17 @@ __global__ void __launch_bounds__(NT) k_eo_src(WArgs a, int nslots) {
     int x[4], st[4];
     const int site = eo_site(g, h, 0, x, st);
     const double2 bv = source_value(g, site, m);
-    const float inv = 1.0f / site_diag<float>(g, site);
+    const float inv = g.clover ? 1.0f : 1.0f / site_diag<float>(g, site);
     cplx<float> z[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) z[k] = k == comp ? cplx<float>{inv * (float)bv.x, inv * (float)bv.y}
                                                    : cplx<float>{0.f, 0.f};
+    if (g.clover) {   // A_e(x)^-1 b_e
+      cplx<float> t[12];
+      clover_mul<float>(g, true, site, z, t);
+      SpinorIO<PR32>::store(a.mid32, a.Vmax, slot, h, t);
+      continue;
+    }
     SpinorIO<PR32>::store(a.mid32, a.Vmax, slot, h, z);
   }
 }
@@ -1511,6 +1550,7 @@ struct WilsonEngine {
   static constexpr int PX = SPR == PR64 ? PR64 : PRFF;   // arithmetic of the true residual
   hp_ctx* ctx;
   bool eo = false;     // even-odd (Schur complement) iteration; set before setup
+  bool clover = false; // some lattice of the problem carries the clover term; set before setup
   WArgs a;
   int nslots, gy, gyb, rpt = 1, variant = 10;
   int kernels_per_iteration() const { return eo ? (SPR == PR64 ? 10 : 12) : (SPR == PR64 ? 7 : 8); }
@@ -1598,41 +1638,42 @@ struct WilsonEngine {
   // ---- even-odd steps
   // grid of the even-odd kernels: one slot per block along x/z, tiles of NT sites along y
   dim3 eo_grid() const { return stencil_grid(variant, nslots, gy); }
-  template <int REC>
+  template <int REC, bool CL>
   hp_status eo_schur(int which) {   // which: 0 v = S p, 1 t = S s, 2 group update with e
     dim3 gr = eo_grid();
     constexpr int LPR = LinkPrecOf<SPR>::v;
     if (which == 0) {
       {
         ProfScope ps(ctx, "k_eo_even");
-        k_eo_even<SPR, LPR, REC, SPR, NT, MASK_RUN><<<gr, NT, 0, ctx->stream>>>(a, a.p, a.mid, nslots);
+        k_eo_even<SPR, LPR, REC, SPR, NT, MASK_RUN, CL><<<gr, NT, 0, ctx->stream>>>(a, a.p, a.mid, nslots);
       }
       HP_LAUNCH_CHECK();
       ProfScope ps(ctx, SPR == PR64 ? "k_eo_odd_v<fp64>" : SPR == PR32 ? "k_eo_odd_v<fp32>" : SPR == PR16 ? "k_eo_odd_v<fp16>" : "k_eo_odd_v<bf16>");
-      k_eo_odd<SPR, SPR, LPR, REC, NT, EPI_V><<<gr, NT, 0, ctx->stream>>>(a, a.p, a.mid, a.v, nslots);
+      k_eo_odd<SPR, SPR, LPR, REC, NT, EPI_V, CL><<<gr, NT, 0, ctx->stream>>>(a, a.p, a.mid, a.v, nslots);
     } else if (which == 1) {
       {
         ProfScope ps(ctx, "k_eo_even");
-        k_eo_even<SPR, LPR, REC, SPR, NT, MASK_RUN><<<gr, NT, 0, ctx->stream>>>(a, a.s, a.mid, nslots);
+        k_eo_even<SPR, LPR, REC, SPR, NT, MASK_RUN, CL><<<gr, NT, 0, ctx->stream>>>(a, a.s, a.mid, nslots);
       }
       HP_LAUNCH_CHECK();
       ProfScope ps(ctx, SPR == PR64 ? "k_eo_odd_t<fp64>" : SPR == PR32 ? "k_eo_odd_t<fp32>" : SPR == PR16 ? "k_eo_odd_t<fp16>" : "k_eo_odd_t<bf16>");
-      k_eo_odd<SPR, SPR, LPR, REC, NT, EPI_T><<<gr, NT, 0, ctx->stream>>>(a, a.s, a.mid, a.t, nslots);
+      k_eo_odd<SPR, SPR, LPR, REC, NT, EPI_T, CL><<<gr, NT, 0, ctx->stream>>>(a, a.s, a.mid, a.t, nslots);
     } else if (SPR != PR64) {
       {
         ProfScope ps(ctx, "k_eo_even<grp>");
-        k_eo_even<EPR, PR32, 12, PR32, NT, MASK_GROUP><<<gr, NT, 0, ctx->stream>>>(a, a.e, a.mid32, nslots);
+        k_eo_even<EPR, PR32, 12, PR32, NT, MASK_GROUP, CL><<<gr, NT, 0, ctx->stream>>>(a, a.e, a.mid32, nslots);
       }
       HP_LAUNCH_CHECK();
       ProfScope ps(ctx, "k_eo_odd<grp>");
-      k_eo_odd<EPR, PR32, PR32, 12, NT, EPI_G><<<gr, NT, 0, ctx->stream>>>(a, a.e, a.mid32, a.rg, nslots);
+      k_eo_odd<EPR, PR32, PR32, 12, NT, EPI_G, CL><<<gr, NT, 0, ctx->stream>>>(a, a.e, a.mid32, a.rg, nslots);
     }
     HP_LAUNCH_CHECK();
     return HP_OK;
   }
   hp_status eo_step(int which) {
     const bool full = variant_rec(variant) == 18 && SPR != PR64;
-    return full ? eo_schur<18>(which) : eo_schur<12>(which);
+    if (clover) return full ? eo_schur<18, true>(which) : eo_schur<12, true>(which);
+    return full ? eo_schur<18, false>(which) : eo_schur<12, false>(which);
   }
   hp_status eo_exact() {
     dim3 gr = eo_grid();
@@ -1990,28 +2031,34 @@ hp_status hp_bench_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int pre
 hp_status hp_solve_wilson(hp_ctx* ctx, SolveProblem& pb, SolveResult& res) {
   const int prec = pb.opts.precision;
   double delta = pb.opts.delta;
-  bool eo = pb.opts.even_odd != 0;
-  for (auto& g : pb.lats)
+  bool eo = pb.opts.even_odd != 0, clover = false;
+  for (auto& g : pb.lats) {
     if (g.L[0] % 2) eo = false;   // parity numbering by site >> 1 needs L_1 even
+    clover = clover || g.clover;
+  }
   switch (prec) {
     case HP_PREC_FP64: {
       WilsonEngine<PR64> e{ctx};
       e.eo = eo;
+      e.clover = clover;
       return run_schedule(ctx, e, pb, res, 12, delta > 0 ? delta : 0.0);
     }
     case HP_PREC_MIXED_FP32: {
       WilsonEngine<PR32> e{ctx};
       e.eo = eo;
+      e.clover = clover;
       return run_schedule(ctx, e, pb, res, 12, delta > 0 ? delta : 0.01);
     }
     case HP_PREC_MIXED_FP16: {
       WilsonEngine<PR16> e{ctx};
       e.eo = eo;
+      e.clover = clover;
       return run_schedule(ctx, e, pb, res, 12, delta > 0 ? delta : 0.1);
     }
     case HP_PREC_MIXED_BF16: {
       WilsonEngine<PRB16> e{ctx};
       e.eo = eo;
+      e.clover = clover;
       return run_schedule(ctx, e, pb, res, 12, delta > 0 ? delta : 0.1);
     }
   }

@@ -57,7 +57,7 @@ class Basis(C.Structure):
 
 class Operator(C.Structure):
     _fields_ = [("kind", C.c_int32), ("mass", C.c_double), ("kappa", C.c_double),
-                ("links", C.c_void_p), ("mass_field", C.c_void_p)]
+                ("links", C.c_void_p), ("mass_field", C.c_void_p), ("csw", C.c_double)]
 
 
 class SolverOpts(C.Structure):
@@ -214,15 +214,17 @@ class Context:
 
     # ---------------------------------------------------------------- operators
     @staticmethod
-    def make_operator(kind: int, mass: float = 0.0, kappa: float = 0.0, links=None, mass_field=None) -> Operator:
+    def make_operator(kind: int, mass: float = 0.0, kappa: float = 0.0, links=None, mass_field=None,
+                      csw: float = 0.0) -> Operator:
         """The operator struct; it keeps the link and mass-field arrays alive (the C struct only
-        holds their addresses)."""
+        holds their addresses).  csw != 0 adds the clover term (Wilson only)."""
         op = Operator()
         op.kind = kind
         op.mass = float(mass)
         op.kappa = float(kappa)
         op.links = _ptr(links)
         op.mass_field = _ptr(mass_field)
+        op.csw = float(csw)
         op._keep = (links, mass_field)
         return op
 

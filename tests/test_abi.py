@@ -88,3 +88,18 @@ def test_no_oracle_in_product_path():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_noalloc_rejects_clover_without_gpu():
+    """The allocation-free stencil is plain Wilson: a clover coefficient is an argument error,
+    reported before any device work."""
+    from paper_1302_4018_gb300 import hprobe
+
+    lib = hprobe.lib()
+    op = hprobe.Context.make_operator(hprobe.OP_WILSON, 0.0, 0.12, np.zeros(72 * 16), None, csw=1.0)
+    lat = hprobe.make_lattice((2, 2, 2, 2))
+    buf = np.zeros(24 * 16)
+    st = lib.hp_operator_apply_noalloc(ctypes.byref(op), ctypes.byref(lat), 1, buf.ctypes.data, buf.ctypes.data,
+                                       None)
+    assert st == hprobe.HP_EINVAL
+    assert "csw" in lib.hp_last_error().decode()

@@ -541,3 +541,70 @@ def test_even_odd_start_at_tolerance(ctx, hp, prec):
     assert st["iterations_total"] == 0 and st64["iterations_total"] == 0
     assert st["max_true_residual"] <= 0.9
     assert np.all(rel(T, T64) <= 1e-12), (T, T64)
+
+
+# ------------------------------------------------------------------ clover term (Section 5.3 operator)
+CSW = 1.3
+
+
+@pytest.mark.parametrize("dims,nrhs", [((4, 4, 2, 6), 1), ((3, 4, 2, 2), 5), ((2, 2, 2, 2), 2)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16", "bf16"])
+def test_clover_apply_parity(ctx, hp, dims, prec, nrhs):
+    U = synth.gauge_links(dims, 0.5, 17)
+    mf = synth.mass_field(dims, 0.01, 18)
+    psi = synth.random_spinors(dims, nrhs, 19)
+    op = ctx.make_operator(hp.OP_WILSON, 0.02, 0.12, links_dev(U), dev(mf), csw=CSW)
+    out = torch.empty(psi.size * 2, dtype=torch.float64, device="cuda:0")
+    ctx.operator_apply(op, dims, nrhs, prec, dev(psi.view(np.float64).reshape(-1)), out)
+    got = out.cpu().numpy().view(np.complex128).reshape(psi.shape)
+    C = O.clover_term(U, dims, 0.12, CSW)
+    for r in range(nrhs):
+        ref = O.wilson_apply(psi[r], U, dims, 0.12, 0.02, mf, clover=C)
+        err = np.linalg.norm(got[r] - ref) / np.linalg.norm(ref)
+        assert err <= WILSON_TOL[prec], err
+    if prec in ("fp64", "fp32"):   # the clover term is far above the comparison tolerance
+        plain = O.wilson_apply(psi[0], U, dims, 0.12, 0.02, mf)
+        assert np.linalg.norm(got[0] - plain) > 100 * WILSON_TOL[prec] * np.linalg.norm(plain)
+
+
+@pytest.mark.parametrize("prec,eo", [("fp64", 0), ("fp64", 1), ("fp16", 1), ("fp32", 1), ("bf16", 1), ("fp16", 0)])
+def test_clover_trace_parity(ctx, hp, prec, eo):
+    dims = (4, 4, 2, 6)
+    U = synth.gauge_links(dims, 0.4, 1004)
+    mf = synth.mass_field(dims, 0.01, 78)
+    op = ctx.make_operator(hp.OP_WILSON, 0.01, 0.115, links_dev(U), dev(mf), csw=CSW)
+    s = 4
+    T, _, st = ctx.trace_inv(op, dims, s, 1e-10, ctx.make_opts(prec, z0_seed=2004, rhs_block=24, even_odd=eo))
+    if "clover_trace" not in _ORACLE_CACHE:
+        _ORACLE_CACHE["clover_trace"] = E.trace_prefix(E.wilson_quadratures(dims, U, 0.115, 0, s, 2004, mass=0.01,
+                                                                            mass_field=mf, method="dense", csw=CSW))
+    T_ref = _ORACLE_CACHE["clover_trace"]
+    assert np.all(rel(T, T_ref) <= TRACE_RTOL), (T, T_ref)
+    assert st["max_true_residual"] <= 1e-10 and st["rhs_solved"] == 12 * s
+
+
+def test_clover_full_sequence_on_pure_gauge_links_is_free_closed_form(ctx, hp):
+    """Pure-gauge links have unit plaquettes, so the clover term vanishes and the full probing
+    sequence (s = V) must give the free-field trace in closed form."""
+    from pins import free_wilson_trace_inverse
+
+    dims = (4, 4, 2, 4)
+    V = int(np.prod(dims))
+    Ufree = np.broadcast_to(np.eye(3, dtype=complex), (V, 4, 3, 3)).copy()
+    Ug, _ = synth.gauge_transform(Ufree, dims, 79)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.12, links_dev(Ug), None, csw=1.7)
+    T, _, _ = ctx.trace_inv(op, dims, V, 1e-11, ctx.make_opts("fp16", z0_seed=6, even_odd=1))
+    exact = free_wilson_trace_inverse(dims, 0.12)
+    assert abs(T[-1].real - exact) <= 1e-9 * exact
+
+
+def test_clover_gradient_vs_oracle(ctx, hp):
+    dims = (4, 4, 2, 4)
+    U = synth.gauge_links(dims, 0.3, 23)
+    mf = synth.mass_field(dims, 0.01, 5001)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.118, links_dev(U), dev(mf), csw=CSW)
+    g = np.zeros(128)
+    T, dTdm, st = ctx.trace_inv_grad(op, dims, 3, 1e-12, ctx.make_opts("fp16", z0_seed=7, even_odd=1), g)
+    g_ref = E.wilson_grad_mass_field(dims, U, 0.118, 3, 7, mass_field=mf, method="dense", csw=CSW).real
+    assert st["max_true_residual"] <= 1e-12
+    assert np.allclose(g, g_ref, rtol=1e-7, atol=1e-9)
