@@ -144,6 +144,23 @@ typedef enum {
     HP_PREC_MIXED_BF16 = 3   /* BF16 storage (per-site norm) with FP32 arithmetic inside */
 } hp_precision;
 
+/* The probing sequence: hierarchical probing (Sections 2-4, the default) or one of the two
+ * sequences Section 5.2 compares it with: Hadamard vectors in natural order, z_m(s) = H_V(s, m)
+ * (Sylvester matrix, lexicographic sites, V a power of two, bias removed with z_0 as for
+ * hierarchical probing), and independent Z_2 noise vectors, z_m(s) = -1 iff the top bit of
+ * output number m V + s of SplitMix64 seeded with z0_seed is set (the standard Monte Carlo
+ * estimator of Section 1.1.2).  Errors: HP_EUNSUPPORTED for natural order on a V that is not a
+ * power of two; HP_EINVAL for an unknown kind. */
+typedef enum { HP_PROBE_HIERARCHICAL = 0, HP_PROBE_NATURAL = 1, HP_PROBE_Z2 = 2 } hp_probe_kind;
+
+/* hp_probe_vectors for any hp_probe_kind (kind 0 is hp_probe_vectors itself): the phases of
+ * v_m, m = first .. first+count-1, as uint16[count][V] on the device with P = *period_out (the
+ * lattice's period; the natural and Z_2 sequences use the phases 0 and P/2 only).
+ * Errors as hp_probe_vectors, plus HP_EINVAL for an unknown kind and HP_EUNSUPPORTED for
+ * natural order on a V that is not a power of two. */
+hp_status hp_probe_sequence(hp_ctx* ctx, const hp_lattice* lat, int32_t kind, int64_t first, int64_t count,
+                            uint64_t z0_seed, uint16_t* phase_dev, int32_t* period_out);
+
 typedef struct {
     int32_t precision;      /* hp_precision                                              */
     int32_t rhs_block;      /* right-hand sides solved concurrently (0: automatic)       */
@@ -151,7 +168,8 @@ typedef struct {
     int32_t dilution;       /* 12 for Wilson (full spin-colour dilution), 1 for Laplacian; 0: default */
     uint64_t z0_seed;       /* bias-removal vector, 0 = none (Section 4)                 */
     int64_t first;          /* first probe to solve; q of probes < first come from q_inout */
-    double delta;           /* reliable-update threshold on ||r||/max||r|| (0: per precision) */
+    double delta;           /* group-update threshold on ||r||/max||r|| (0: per precision:
+                               0.001 FP32, 0.03 FP16/BF16, measured on the 32^3x64 workload) */
     int32_t check_every;    /* iterations between host scheduling steps (0: automatic)   */
     int32_t use_graph;      /* 1: replay the iteration chunk from a captured CUDA graph  */
     int32_t block_threads;  /* reserved for the stencil block size (0)                    */
@@ -161,7 +179,8 @@ typedef struct {
     int32_t even_odd;       /* Wilson: 1 = iterate on the odd-site Schur complement
                                d_o - kappa^2 H_oe d_e^-1 H_eo (needs L_1 even; the certified
                                residual is still that of the full system)                   */
-    int32_t reserved[3];
+    int32_t probe_kind;     /* hp_probe_kind: the probing sequence (0: hierarchical probing) */
+    int32_t reserved[2];
 } hp_solver_opts;
 
 typedef struct {

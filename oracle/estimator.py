@@ -23,14 +23,34 @@ import numpy as np
 
 from . import operators as ops
 from . import solvers
+from . import probing as Pr
 from .probing import probe_phases, probe_values
 
 
 def probe_vectors(dims: Sequence[int], first: int, count: int, z0_seed: int,
-                  loc: Sequence[int] | None = None) -> np.ndarray:
-    """v_m = z_0 (.) z_m as complex [count, V] (correctly rounded entries)."""
+                  loc: Sequence[int] | None = None, kind: str = "hp") -> np.ndarray:
+    """v_m = z_0 (.) z_m as complex [count, V] (correctly rounded entries).  kind: "hp"
+    (hierarchical probing), "natural" (Hadamard vectors in natural order, bias removed), "z2"
+    (independent Z_2 noise vectors, seeded by z0_seed)."""
+    if kind == "natural":
+        return probe_values(Pr.probe_phases_natural(int(np.prod(dims)), first, count, z0_seed), 2)
+    if kind == "z2":
+        return probe_values(Pr.probe_phases_z2(int(np.prod(dims)), first, count, z0_seed), 2)
     ph, P = probe_phases(dims, first, count, z0_seed, loc=loc)
     return probe_values(ph, P)
+
+
+def z0_variance(B: np.ndarray, Z: np.ndarray, s: int) -> float:
+    """Exact variance over the Z_2 vector z_0 of T_s = (1/s) sum_{m<s} (z_0 (.) z_m)^H B (z_0 (.) z_m)
+    for real +-1 probing vectors z_m (rows of Z): writing C = sum_{m<s} z_m z_m^T,
+    T_s = (1/s) sum_{i,j} z0_i z0_j B_ij C_ij, whose diagonal part is Tr B for every z_0 and whose
+    pairs i < j are uncorrelated with unit variance, so
+        Var(T_s) = (1/s^2) sum_{i<j} |B_ij + B_ji|^2 C_ij^2
+    (Section 1.1.2's variance of the Z_2 estimator, 2 sum_{i!=j} B_ij^2 for s = 1 and symmetric B)."""
+    Zs = np.asarray(Z[:s], dtype=float)
+    C = Zs.T @ Zs
+    W = np.abs(B + B.T) ** 2 * C ** 2
+    return float(np.sum(np.triu(W, 1))) / s ** 2
 
 
 # ------------------------------------------------------------------ prefix
@@ -78,9 +98,9 @@ def laplacian_solutions(dims, mass, W, tol=1e-13, mass_field=None, method="cg"):
 
 
 def laplacian_quadratures(dims, mass, first, count, z0_seed, tol=1e-13, mass_field=None,
-                          method="cg", loc=None):
-    """q_m = v_m^H A^-1 v_m, m = first..first+count-1."""
-    W = probe_vectors(dims, first, count, z0_seed, loc=loc)
+                          method="cg", loc=None, kind="hp"):
+    """q_m = v_m^H A^-1 v_m, m = first..first+count-1 (kind: the probing sequence, see probe_vectors)."""
+    W = probe_vectors(dims, first, count, z0_seed, loc=loc, kind=kind)
     if np.all(W.imag == 0):
         W = W.real
     X = laplacian_solutions(dims, mass, W, tol, mass_field, method)

@@ -209,6 +209,33 @@ def probe_phases_hadamard(dims: Sequence[int], first: int, count: int, loc: Sequ
     return out
 
 
+# ------------------------------------------------ the comparison sequences of Section 5
+def probe_phases_natural(V: int, first: int, count: int, z0_seed: int) -> np.ndarray:
+    """Hadamard vectors in natural order (Section 5.2): z_m(i) = H_V(i, m), the Sylvester
+    Hadamard matrix with rows (lexicographic sites) and columns both in natural order, bias
+    removed by z_0 as for hierarchical probing; V a power of two.  Phases 0/1 of P = 2."""
+    if V & (V - 1) or first < 0 or count < 0 or first + count > V:
+        raise ValueError("natural-order Hadamard vectors need V a power of two and m < V")
+    z0 = z0_signs(z0_seed, V)
+    out = np.empty((count, V), dtype=np.int64)
+    for t in range(count):
+        m = first + t
+        col = np.array([0 if hadamard_element(i + 1, m + 1, V) == 1 else 1 for i in range(V)], dtype=np.int64)
+        out[t] = (col + (z0 < 0)) % 2
+    return out
+
+
+def probe_phases_z2(V: int, first: int, count: int, seed: int) -> np.ndarray:
+    """The Z_2 noise vectors of the standard Monte Carlo estimator (Sections 1.1.2, 5.2): entry i
+    of vector m is -1 iff the top bit of SplitMix64 output number m V + i (seeded with ``seed``)
+    is set.  Phases 0/1 of P = 2."""
+    out = np.empty((count, V), dtype=np.int64)
+    for t in range(count):
+        m = first + t
+        out[t] = [splitmix64_output(seed, m * V + i) >> 63 for i in range(V)]
+    return out
+
+
 # ------------------------------------------------------ correctly rounded values
 def _pi_decimal(prec: int) -> Decimal:
     """pi by Machin's formula pi = 16 atan(1/5) - 4 atan(1/239), in Decimal."""

@@ -137,6 +137,27 @@ static hp_status check_solver_args(int64_t s_max, double tol, const hp_solver_op
   return HP_OK;
 }
 
+// the probing sequence of opts on lattice g: range checks and the geometry fields it needs
+static hp_status set_probe_kind(const hp_solver_opts* opts, int64_t s_max, LatGeom* g) {
+  g->z0_seed = opts->z0_seed;
+  g->probe_kind = opts->probe_kind;
+  if (opts->probe_kind == HP_PROBE_HIERARCHICAL) return HP_OK;
+  if (opts->probe_kind != HP_PROBE_NATURAL && opts->probe_kind != HP_PROBE_Z2) {
+    hp_set_error("unknown probe kind %d", opts->probe_kind);
+    return HP_EINVAL;
+  }
+  if (opts->probe_kind == HP_PROBE_NATURAL && (g->V & (g->V - 1))) {
+    hp_set_error("Hadamard vectors in natural order need V a power of two (V = %d)", g->V);
+    return HP_EUNSUPPORTED;
+  }
+  if (s_max > g->V) {
+    hp_set_error("s_max = %lld exceeds V = %d", (long long)s_max, g->V);
+    return HP_EINVAL;
+  }
+  g->parts = 1;   // real +-1 vectors: one solve per vector for the Laplacian
+  return HP_OK;
+}
+
 static int need_mask(int prec) {
   int m = 1 << PR64;
   if (prec == HP_PREC_MIXED_FP32) m |= 1 << PR32;
@@ -197,7 +218,8 @@ static hp_status trace_common(hp_ctx* ctx, const hp_operator* op, const hp_latti
   LatGeom g;
   LatticeSetup* ls = nullptr;
   HP_TRY(operator_geom(ctx, op, lat, &g, &ls));
-  HP_TRY(check_solver_args(s_max, tol, opts, ls->n_vectors, g.V));
+  HP_TRY(check_solver_args(s_max, tol, opts, opts->probe_kind ? g.V : ls->n_vectors, g.V));
+  HP_TRY(set_probe_kind(opts, s_max, &g));
   if (!trace_prefix) {
     hp_set_error("trace_prefix is NULL");
     return HP_EINVAL;
@@ -215,7 +237,6 @@ static hp_status trace_common(hp_ctx* ctx, const hp_operator* op, const hp_latti
     hp_set_error("dilution %d not supported (Wilson: 12, Laplacian: 1)", opts->dilution);
     return HP_EINVAL;
   }
-  g.z0_seed = opts->z0_seed;
   HP_TRY(prepare_operator(ctx, op, &g, opts->precision, "op0"));
   SolveProblem pb;
   pb.lats.push_back(g);
@@ -298,12 +319,12 @@ extern "C" hp_status hp_trace_inv_batch(hp_ctx* ctx, int32_t nlat, const hp_oper
     LatGeom g;
     LatticeSetup* ls = nullptr;
     HP_TRY(operator_geom(ctx, &ops[i], &lats[i], &g, &ls));
-    HP_TRY(check_solver_args(s_max[i], tol, opts, ls->n_vectors, g.V));
+    HP_TRY(check_solver_args(s_max[i], tol, opts, opts->probe_kind ? g.V : ls->n_vectors, g.V));
+    HP_TRY(set_probe_kind(opts, s_max[i], &g));
     if (!trace_prefix[i]) {
       hp_set_error("trace_prefix[%d] is NULL", i);
       return HP_EINVAL;
     }
-    g.z0_seed = opts->z0_seed;
     char tag[32];
     snprintf(tag, sizeof(tag), "op%d", i);
     HP_TRY(prepare_operator(ctx, &ops[i], &g, opts->precision, tag));

@@ -578,8 +578,17 @@ extern "C" hp_status hp_permutation(hp_ctx* ctx, const hp_lattice* lat, uint32_t
 
 extern "C" hp_status hp_probe_vectors(hp_ctx* ctx, const hp_lattice* lat, int64_t first, int64_t count,
                                       uint64_t z0_seed, uint16_t* phase_dev, int32_t* period_out) {
+  return hp_probe_sequence(ctx, lat, HP_PROBE_HIERARCHICAL, first, count, z0_seed, phase_dev, period_out);
+}
+
+extern "C" hp_status hp_probe_sequence(hp_ctx* ctx, const hp_lattice* lat, int32_t kind, int64_t first,
+                                       int64_t count, uint64_t z0_seed, uint16_t* phase_dev, int32_t* period_out) {
   if (!ctx) {
     hp_set_error("hp_probe_vectors: NULL context");
+    return HP_EINVAL;
+  }
+  if (kind != HP_PROBE_HIERARCHICAL && kind != HP_PROBE_NATURAL && kind != HP_PROBE_Z2) {
+    hp_set_error("unknown probe kind %d", kind);
     return HP_EINVAL;
   }
   std::vector<int64_t> dims;
@@ -591,9 +600,13 @@ extern "C" hp_status hp_probe_vectors(hp_ctx* ctx, const hp_lattice* lat, int64_
     hp_set_error("probe range [%lld, %lld) outside [0, V = %d]", (long long)first, (long long)(first + count), ls->g.V);
     return HP_EINVAL;
   }
-  if (first + count > ls->n_vectors) {
+  if (kind == HP_PROBE_HIERARCHICAL && first + count > ls->n_vectors) {
     hp_set_error("only %lld nested vectors exist for this lattice (unequal odd colour classes)",
                  (long long)ls->n_vectors);
+    return HP_EUNSUPPORTED;
+  }
+  if (kind == HP_PROBE_NATURAL && (ls->g.V & (ls->g.V - 1))) {
+    hp_set_error("Hadamard vectors in natural order need V a power of two (V = %d)", ls->g.V);
     return HP_EUNSUPPORTED;
   }
   if (period_out) *period_out = ls->g.P;
@@ -604,6 +617,7 @@ extern "C" hp_status hp_probe_vectors(hp_ctx* ctx, const hp_lattice* lat, int64_
   }
   LatGeom g = ls->g;
   g.z0_seed = z0_seed;
+  g.probe_kind = kind;
   {
     ProfScope ps(ctx, "k_probe_phases");
     k_probe_phases<<<grid_for(ctx, count * (long long)g.V, 256), 256, 0, ctx->stream>>>(g, (uint32_t)first,

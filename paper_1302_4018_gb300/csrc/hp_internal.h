@@ -58,6 +58,7 @@ struct LatGeom {
   int Q, R, P;            // odd block size, final level size (0: unequal), period
   int qstride[8];         // strides of the q-torus (sizes p_j)
   unsigned long long z0_seed;
+  int probe_kind;         // hp_probe_kind: hierarchical (0), natural-order Hadamard (1), Z_2 noise (2)
   const uint32_t* loc;    // [V] hierarchical position of each site
   const int32_t* wtab;    // [Q] position inside the odd block of each q point
   const double2* ptab;    // [P] (cos, sin) of 2 pi k / P
@@ -211,7 +212,21 @@ hp_status hp_solve_laplace(hp_ctx* ctx, SolveProblem& pb, SolveResult& res);
 // -------------------------------------------------------- device helpers
 #ifdef __CUDACC__
 
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed, unsigned long long index) {
+  unsigned long long z = seed + (index + 1ull) * 0x9E3779B97F4A7C15ull;   // output number `index`
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 __device__ __forceinline__ int probe_phase(const LatGeom& g, uint32_t site, uint32_t m) {
+  if (g.probe_kind == HP_PROBE_Z2)   // independent Z_2 noise: top bit of output m V + site
+    return (splitmix64_at(g.z0_seed, (unsigned long long)m * (unsigned long long)g.V + site) >> 63) ? (g.P >> 1) : 0;
+  if (g.probe_kind == HP_PROBE_NATURAL) {   // Sylvester Hadamard H(site, m), natural order (V = 2^K)
+    int ph = (__popc(site & m) & 1) * (g.P >> 1);
+    if (g.z0_seed && (splitmix64_at(g.z0_seed, site) >> 63)) ph += g.P >> 1;
+    return ph % g.P;
+  }
   uint32_t loc = g.loc[site];
   uint32_t lb = loc, w = 0;
   if (g.Q > 1) {
@@ -232,13 +247,7 @@ __device__ __forceinline__ int probe_phase(const LatGeom& g, uint32_t site, uint
     ph += (g.P / 3) * (int)((C * e3) % 3u);
     ph += (g.P / g.R) * (int)((unsigned long long)r * ef % (unsigned long long)g.R);
   }
-  if (g.z0_seed) {
-    unsigned long long z = g.z0_seed + (unsigned long long)(site + 1ull) * 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z = z ^ (z >> 31);
-    if (z >> 63) ph += g.P >> 1;
-  }
+  if (g.z0_seed && (splitmix64_at(g.z0_seed, site) >> 63)) ph += g.P >> 1;
   return ph % g.P;
 }
 

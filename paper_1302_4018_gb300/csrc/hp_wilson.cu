@@ -2047,19 +2047,19 @@ hp_status hp_solve_wilson(hp_ctx* ctx, SolveProblem& pb, SolveResult& res) {
       WilsonEngine<PR32> e{ctx};
       e.eo = eo;
       e.clover = clover;
-      return run_schedule(ctx, e, pb, res, 12, delta > 0 ? delta : 0.01);
+      return run_schedule(ctx, e, pb, res, 12, delta > 0 ? delta : 0.001);
     }
     case HP_PREC_MIXED_FP16: {
       WilsonEngine<PR16> e{ctx};
       e.eo = eo;
       e.clover = clover;
-      return run_schedule(ctx, e, pb, res, 12, delta > 0 ? delta : 0.1);
+      return run_schedule(ctx, e, pb, res, 12, delta > 0 ? delta : 0.03);
     }
     case HP_PREC_MIXED_BF16: {
       WilsonEngine<PRB16> e{ctx};
       e.eo = eo;
       e.clover = clover;
-      return run_schedule(ctx, e, pb, res, 12, delta > 0 ? delta : 0.1);
+      return run_schedule(ctx, e, pb, res, 12, delta > 0 ? delta : 0.03);
     }
   }
   hp_set_error("unknown precision %d", prec);

@@ -36,13 +36,14 @@ class HProbeError(RuntimeError):
 
 HP_OK, HP_EINVAL, HP_EUNSUPPORTED, HP_ENOMEM, HP_ECUDA, HP_ENOCONV, HP_ETIMEOUT = range(7)
 OP_LAPLACIAN, OP_WILSON = 0, 1
+PROBE_KINDS = {"hp": 0, "natural": 1, "z2": 2}
 PREC = {"fp64": 0, "fp32": 1, "fp16": 2, "bf16": 3}
 
 EXPORTED = ["hp_ctx_create", "hp_ctx_destroy", "hp_last_error", "hp_ctx_synchronize", "hp_basis_info",
             "hp_phase_values",
             "hp_permutation", "hp_probe_vectors", "hp_trace_inv", "hp_trace_inv_grad", "hp_trace_inv_batch",
             "hp_operator_apply", "hp_dslash_bench", "hp_profile_enable", "hp_profile_report",
-            "hp_launch_count", "hp_operator_apply_noalloc"]
+            "hp_launch_count", "hp_operator_apply_noalloc", "hp_probe_sequence"]
 
 
 class Lattice(C.Structure):
@@ -64,7 +65,8 @@ class SolverOpts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("rhs_block", C.c_int32), ("maxiter", C.c_int32),
                 ("dilution", C.c_int32), ("z0_seed", C.c_uint64), ("first", C.c_int64), ("delta", C.c_double),
                 ("check_every", C.c_int32), ("use_graph", C.c_int32), ("block_threads", C.c_int32),
-                ("rhs_per_thread", C.c_int32), ("even_odd", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("rhs_per_thread", C.c_int32), ("even_odd", C.c_int32), ("probe_kind", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class SolveStats(C.Structure):
@@ -91,6 +93,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hp_phase_values": (C.c_int, [I32, P]),
         "hp_permutation": (C.c_int, [P, C.POINTER(Lattice), P]),
         "hp_probe_vectors": (C.c_int, [P, C.POINTER(Lattice), I64, I64, C.c_uint64, P, C.POINTER(I32)]),
+        "hp_probe_sequence": (C.c_int, [P, C.POINTER(Lattice), I32, I64, I64, C.c_uint64, P, C.POINTER(I32)]),
         "hp_trace_inv": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I64, D, C.POINTER(SolverOpts),
                                    P, P, C.POINTER(SolveStats)]),
         "hp_trace_inv_grad": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I64, D,
@@ -205,11 +208,17 @@ class Context:
         _check(lib().hp_permutation(self._h, C.byref(make_lattice(dims)), _ptr(out)))
         return out
 
-    def probe_vectors(self, dims: Sequence[int], first: int, count: int, z0_seed: int, out) -> int:
-        """uint16 phases into ``out`` (device int16/uint16 tensor of count*V); returns the period."""
+    def probe_vectors(self, dims: Sequence[int], first: int, count: int, z0_seed: int, out, kind=0) -> int:
+        """uint16 phases into ``out`` (device int16/uint16 tensor of count*V); returns the period.
+        kind: the probing sequence (0 / "hp", 1 / "natural", 2 / "z2")."""
         per = C.c_int32()
-        _check(lib().hp_probe_vectors(self._h, C.byref(make_lattice(dims)), int(first), int(count),
-                                      C.c_uint64(z0_seed), _ptr(out), C.byref(per)))
+        k = PROBE_KINDS[kind] if isinstance(kind, str) else int(kind)
+        if k == 0:
+            _check(lib().hp_probe_vectors(self._h, C.byref(make_lattice(dims)), int(first), int(count),
+                                          C.c_uint64(z0_seed), _ptr(out), C.byref(per)))
+        else:
+            _check(lib().hp_probe_sequence(self._h, C.byref(make_lattice(dims)), k, int(first), int(count),
+                                           C.c_uint64(z0_seed), _ptr(out), C.byref(per)))
         return per.value
 
     # ---------------------------------------------------------------- operators
@@ -230,7 +239,10 @@ class Context:
 
     @staticmethod
     def make_opts(precision="fp64", rhs_block=0, maxiter=0, z0_seed=0, first=0, delta=0.0, check_every=0,
-                  use_graph=0, block_threads=0, dilution=0, rhs_per_thread=0, even_odd=0) -> SolverOpts:
+                  use_graph=0, block_threads=0, dilution=0, rhs_per_thread=0, even_odd=0,
+                  probe_kind=0) -> SolverOpts:
+        """probe_kind: 0 / "hp" hierarchical probing, 1 / "natural" Hadamard vectors in natural
+        order, 2 / "z2" Z_2 noise vectors (seeded by z0_seed)."""
         o = SolverOpts()
         o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
         o.rhs_block = rhs_block
@@ -244,6 +256,7 @@ class Context:
         o.block_threads = block_threads
         o.rhs_per_thread = rhs_per_thread
         o.even_odd = even_odd
+        o.probe_kind = PROBE_KINDS[probe_kind] if isinstance(probe_kind, str) else int(probe_kind)
         return o
 
     def operator_apply(self, op: Operator, dims, nrhs: int, precision, inp, out):

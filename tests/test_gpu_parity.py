@@ -608,3 +608,69 @@ def test_clover_gradient_vs_oracle(ctx, hp):
     g_ref = E.wilson_grad_mass_field(dims, U, 0.118, 3, 7, mass_field=mf, method="dense", csw=CSW).real
     assert st["max_true_residual"] <= 1e-12
     assert np.allclose(g, g_ref, rtol=1e-7, atol=1e-9)
+
+
+# ------------------------------------------------------------------ the comparison sequences (Section 5.2)
+@pytest.mark.parametrize("kind,dims,seed", [("natural", (8, 8, 8, 8), 0), ("natural", (2, 4, 8), 11),
+                                            ("natural", (1024,), 3), ("z2", (4, 4, 4, 4), 12345),
+                                            ("z2", (12, 12), 7), ("z2", (3, 5, 4, 6), 1)])
+def test_probe_sequence_bit_exact(ctx, hp, kind, dims, seed):
+    V = int(np.prod(dims))
+    for first, count in [(0, min(V, 40)), (V - 5, 5)]:
+        out = torch.empty(count * V, dtype=torch.int16, device="cuda:0")
+        per = ctx.probe_vectors(dims, first, count, seed, out, kind=kind)
+        ref = (Pr.probe_phases_natural(V, first, count, seed) if kind == "natural"
+               else Pr.probe_phases_z2(V, first, count, seed))
+        got = out.cpu().numpy().astype(np.int64).reshape(count, V) & 0xFFFF
+        assert np.array_equal(got, ref * (per // 2))
+
+
+def test_natural_order_rejects_non_power_of_two(ctx, hp):
+    out = torch.empty(12 * 12, dtype=torch.int16, device="cuda:0")
+    with pytest.raises(hp.HProbeError) as e:
+        ctx.probe_vectors((12, 12), 0, 1, 0, out, kind="natural")
+    assert e.value.status == hp.HP_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("kind", ["natural", "z2"])
+def test_laplacian_trace_comparison_sequences(ctx, hp, kind):
+    dims = (8, 8, 8, 8)
+    op = ctx.make_operator(hp.OP_LAPLACIAN, 0.05)
+    s = 24
+    T, _, st = ctx.trace_inv(op, dims, s, 1e-12, ctx.make_opts("fp64", z0_seed=21, probe_kind=kind))
+    T_ref = E.trace_prefix(E.laplacian_quadratures(dims, 0.05, 0, s, 21, method="dense", kind=kind))
+    assert np.all(rel(T, T_ref) <= TRACE_RTOL)
+    assert st["max_true_residual"] <= 1e-12
+
+
+def test_wilson_trace_z2_noise(ctx, hp):
+    dims = (4, 4, 2, 4)
+    U = synth.gauge_links(dims, 0.3, 31)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.12, links_dev(U), None)
+    T, _, st = ctx.trace_inv(op, dims, 3, 1e-10, ctx.make_opts("fp16", z0_seed=8, even_odd=1, probe_kind="z2"))
+    W = E.probe_vectors(dims, 0, 3, 8, kind="z2")
+    X = E.wilson_solutions(dims, U, 0.12, W, method="dense")
+    q = [sum(np.vdot(E._dilute(W[m], a), X[m, a]) for a in range(12)) for m in range(3)]
+    assert np.all(rel(T, E.trace_prefix(q)) <= TRACE_RTOL)
+
+
+def test_variance_of_hierarchical_probing_over_z0_matches_closed_form(ctx, hp):
+    """The GPU's T_s over many z_0 (4^4 Laplacian): its sample variance agrees with the exact
+    z_0-variance within the sampling error, and the hierarchical sequence has a smaller variance
+    than natural order at the completion point s = 32."""
+    from oracle import probing as Pr
+
+    dims = (4, 4, 4, 4)
+    V = 256
+    B = np.linalg.inv(O.laplacian_dense(dims, 0.5))
+    op = ctx.make_operator(hp.OP_LAPLACIAN, 0.5)
+    seeds = range(1, 201)
+    Ts = np.array([ctx.trace_inv(op, dims, 32, 1e-13, ctx.make_opts("fp64", z0_seed=z, rhs_block=64))[0][31].real
+                   for z in seeds])
+    ph, _ = Pr.probe_phases(dims, 0, 32, 0)
+    var = E.z0_variance(B, 1 - 2 * ph, 32)
+    n = len(Ts)
+    assert abs(Ts.mean() - np.trace(B)) <= 4 * np.sqrt(var / n)
+    assert abs(Ts.var(ddof=1) / var - 1) <= 4 * np.sqrt(2.0 / (n - 1)) + 0.1
+    var_nat = E.z0_variance(B, 1 - 2 * Pr.probe_phases_natural(V, 0, 32, 0), 32)
+    assert var < var_nat

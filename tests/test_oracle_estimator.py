@@ -138,3 +138,73 @@ def test_wilson_gradient_fd():
     tp = E.trace_prefix(E.wilson_quadratures(dims, U, 0.12, 0, s, 7, mass=h, mass_field=mf, method="dense"))[-1]
     tm = E.trace_prefix(E.wilson_quadratures(dims, U, 0.12, 0, s, 7, mass=-h, mass_field=mf, method="dense"))[-1]
     assert np.isclose(((tp - tm) / (2 * h)).real, np.sum(g).real, rtol=1e-7)
+
+
+# ------------------------------------------------------------------ the comparison sequences (NEXT-2)
+def test_natural_hadamard_is_sylvester_in_natural_order():
+    import scipy.linalg
+
+    from oracle import probing as Pr
+
+    V = 64
+    ph = Pr.probe_phases_natural(V, 0, V, 0)
+    H = scipy.linalg.hadamard(V)
+    assert np.array_equal(1 - 2 * ph, H.T)               # row m of ph is column m of H
+    z0 = Pr.z0_signs(99, V)
+    assert np.array_equal((1 - 2 * Pr.probe_phases_natural(V, 3, 5, 99)), (H[:, 3:8] * z0[:, None]).T)
+
+
+def test_z2_noise_is_splitmix64_counter_stream():
+    from oracle import probing as Pr
+
+    V = 10
+    ph = Pr.probe_phases_z2(V, 2, 3, 1234567)
+    for t in range(3):
+        for i in range(V):
+            assert ph[t, i] == Pr.splitmix64_output(1234567, (2 + t) * V + i) >> 63
+    big = Pr.probe_phases_z2(64, 0, 64, 5)
+    assert 0.4 < big.mean() < 0.6
+
+
+@pytest.mark.parametrize("kind", ["hp", "natural"])
+def test_z0_variance_formula_matches_enumeration_of_all_z0(kind):
+    """Brute force over all 2^16 vectors z_0 on the 2^4 torus: the mean of T_s is Tr A^-1 exactly
+    (bias removal, Section 4) and its variance is the closed form of z0_variance."""
+    from oracle import probing as Pr
+
+    dims = (2, 2, 2, 2)
+    V = 16
+    B = np.linalg.inv(O.laplacian_dense(dims, 0.3))
+    if kind == "hp":
+        ph, _ = Pr.probe_phases(dims, 0, V, 0)
+    else:
+        ph = Pr.probe_phases_natural(V, 0, V, 0)
+    Z = 1 - 2 * ph
+    bits = (np.arange(2 ** V)[:, None] >> np.arange(V)[None, :]) & 1
+    Z0 = 1 - 2 * bits                                    # all 65536 z_0
+    for s in (1, 2, 3, 4, 8, 16):
+        C = Z[:s].T @ Z[:s]
+        T = np.einsum("ki,ij,kj->k", Z0, B * C, Z0) / s  # T_s for every z_0
+        assert abs(T.mean() - np.trace(B)) <= 1e-12 * np.trace(B)
+        assert abs(T.var() - E.z0_variance(B, Z, s)) <= 1e-10 * max(T.var(), 1e-30) + 1e-24
+    assert E.z0_variance(B, Z, 16) <= 1e-28              # s = N: exact for every z_0
+
+
+def test_hierarchical_variance_at_completion_is_same_colour_sum():
+    """At a completion point s = 2^{k}, sum_m z_m z_m^T = s [same colour] (Proposition of Section 2),
+    so the variance reduces to 2 sum over same-colour pairs i != j of (A^-1)_ij^2: the elements the
+    colouring could not remove."""
+    from oracle import probing as Pr
+
+    dims = (4, 4, 4, 4)
+    V = 256
+    B = np.linalg.inv(O.laplacian_dense(dims, 0.5))
+    ph, _ = Pr.probe_phases(dims, 0, 32, 0)
+    Z = 1 - 2 * ph
+    for s in (2, 32):
+        C = Z[:s].T @ Z[:s]
+        same = (C == s)
+        assert np.all((C == s) | (C == 0))
+        direct = 2 * np.sum(np.where(same & ~np.eye(V, dtype=bool), B ** 2, 0.0))
+        assert abs(E.z0_variance(B, Z, s) - direct) <= 1e-12 * direct
+    assert E.z0_variance(B, Z, 32) < 0.2 * E.z0_variance(B, Z, 2)
