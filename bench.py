@@ -50,15 +50,19 @@ def hbm_peak():
 
 
 def source_hash():
+    """Hash of the sources of the solver kernels (the DRAM traffic below is valid for them only)."""
     h = hashlib.sha256()
-    for f in ("hp_fields.cuh", "hp_wilson.cu", "hp_internal.h"):
+    for f in ("hp_fields.cuh", "hp_wilson_impl.cuh", "hp_internal.h"):
         with open(os.path.join(ROOT, "paper_1302_4018_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
 
 
-# DRAM traffic per launch from one ncu capture, valid only for the source it was taken on
-NCU_TRAFFIC = {}
+# DRAM traffic of one launch with every slot active (24 on 32^3x64), from one ncu capture of the
+# same kernel on 32^3x16 with 12 slots (411.9 MB read + 146.7 MB written): the spinor part scaled
+# by the site-RHS ratio (8x), the links (read once per launch) by the site ratio (4x); valid only
+# for the kernel source it was taken on
+NCU_TRAFFIC = {("k_eo_even", "85ee1d9c94c8"): {"bytes_all_slots": 4.1668e9, "alg_bytes_all_slots": 1048576 * 104 * 24 + 4 * 2097152 * 36}}
 
 
 class Clocks:
@@ -327,7 +331,11 @@ def run_ours(args):
     top_name, top_rec = top
     top_bytes = kernel_bytes(top_name, prec, V, dict(counts, launches=top_rec["launches"]))
     achieved = top_bytes / (top_rec["ms"] / 1e3) / 1e9 if top_bytes else None
-    trace_ncu = NCU_TRAFFIC.get((top_name, source_hash()))
+    trace_ncu = None
+    nt = NCU_TRAFFIC.get((top_name, source_hash()))
+    if nt and top_bytes and DIMS == (32, 32, 32, 64) and args.rhs_block == 24 and not args.csw:
+        # the capture's traffic per byte of algorithmic work, applied to this run's average launch
+        trace_ncu = nt["bytes_all_slots"] / nt["alg_bytes_all_slots"] * top_bytes / top_rec["launches"]
     roofline = {"kernel": top_name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": (top_bytes / top_rec["launches"]) if top_bytes else None,
