@@ -49,12 +49,20 @@ def hbm_peak():
         return HBM_FALLBACK, "fallback"
 
 
-def source_hash():
-    """Hash of the sources of the solver kernels (the DRAM traffic below is valid for them only)."""
+def source_hash(kernel):
+    """Hash of the sources a kernel is built from: the shared field and geometry headers and the
+    kernel's own definition in the solver templates (its DRAM traffic below is valid for them only)."""
     h = hashlib.sha256()
-    for f in ("hp_fields.cuh", "hp_wilson_impl.cuh", "hp_internal.h"):
-        with open(os.path.join(ROOT, "paper_1302_4018_gb300", "csrc", f), "rb") as fh:
+    csrc = os.path.join(ROOT, "paper_1302_4018_gb300", "csrc")
+    for f in ("hp_fields.cuh", "hp_internal.h"):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    with open(os.path.join(csrc, "hp_wilson_impl.cuh")) as fh:
+        text = fh.read()
+    for name in (kernel, "eo_hop", "eo_site", "site_diag", "add_diag"):   # the kernel and its helpers
+        i = text.find(" %s(" % name)
+        if i >= 0:
+            h.update(text[text.rfind("\n\n", 0, i):text.find("\n}\n", i)].encode())
     return h.hexdigest()[:12]
 
 
@@ -62,7 +70,7 @@ def source_hash():
 # same kernel on 32^3x16 with 12 slots (411.9 MB read + 146.7 MB written): the spinor part scaled
 # by the site-RHS ratio (8x), the links (read once per launch) by the site ratio (4x); valid only
 # for the kernel source it was taken on
-NCU_TRAFFIC = {("k_eo_even", "85ee1d9c94c8"): {"bytes_all_slots": 4.1668e9, "alg_bytes_all_slots": 1048576 * 104 * 24 + 4 * 2097152 * 36}}
+NCU_TRAFFIC = {("k_eo_even", "5c1bb325740d"): {"bytes_all_slots": 4.1668e9, "alg_bytes_all_slots": 1048576 * 104 * 24 + 4 * 2097152 * 36}}
 
 
 class Clocks:
@@ -332,7 +340,7 @@ def run_ours(args):
     top_bytes = kernel_bytes(top_name, prec, V, dict(counts, launches=top_rec["launches"]))
     achieved = top_bytes / (top_rec["ms"] / 1e3) / 1e9 if top_bytes else None
     trace_ncu = None
-    nt = NCU_TRAFFIC.get((top_name, source_hash()))
+    nt = NCU_TRAFFIC.get((top_name, source_hash(top_name)))
     if nt and top_bytes and DIMS == (32, 32, 32, 64) and args.rhs_block == 24 and not args.csw:
         # the capture's traffic per byte of algorithmic work, applied to this run's average launch
         trace_ncu = nt["bytes_all_slots"] / nt["alg_bytes_all_slots"] * top_bytes / top_rec["launches"]

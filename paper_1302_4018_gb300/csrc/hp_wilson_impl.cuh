@@ -949,11 +949,12 @@ __global__ void __launch_bounds__(NT, MASK == MASK_RUN ? 6 : 4) k_eo_even(WArgs 
 //   EPI_G: group update r_g -= S e, r = r_g, (r^, r_g), ||r_g||^2   (in = e, mid FP32)
 enum { EPI_G = 3 };
 
-// at least five resident blocks of 128 threads (<= 102 registers): the odd-site kernels are
-// latency-bound, and the register count the compiler picks unconstrained halves the warps an SM holds
-#define EO_ODD_MINB 5
+// resident blocks of 128 threads: six (<= 85 registers) with 18-real links, five (<= 102) with the
+// reconstructing 12-real form; the odd-site kernels are latency-bound, and the register count the
+// compiler picks unconstrained halves the warps an SM holds
+#define EO_ODD_MINB(REC) ((REC) == 18 ? 6 : 5)
 template <int SIN, int SMID, int LPR, int REC, int NT, int EPI, bool CL>
-__global__ void __launch_bounds__(NT, EO_ODD_MINB) k_eo_odd(WArgs a, FieldPtr in, FieldPtr mid, FieldPtr out, int nslots) {
+__global__ void __launch_bounds__(NT, EO_ODD_MINB(REC)) k_eo_odd(WArgs a, FieldPtr in, FieldPtr mid, FieldPtr out, int nslots) {
   EO_PREAMBLE(EPI == EPI_G ? MASK_GROUP : MASK_RUN)
   typedef float R;
   constexpr int NQ = EPI == EPI_V ? 2 : 3;
