@@ -595,13 +595,27 @@ def run_variance(args):
         study[kind] = {"s": points,
                        "mean_rel_error": [float(abs(Ts[:, s - 1].mean() - exact) / exact) for s in points],
                        "std_over_seeds": [float(Ts[:, s - 1].std(ddof=1)) if len(Ts) > 1 else None for s in points]}
+    # the same hierarchical sequence with every quadrature bracketed to 1e-10 (Gauss / Gauss-Radau
+    # bounds from the CG coefficients) instead of a 1e-10 residual
+    opts = ctx.make_opts("fp64", z0_seed=1, rhs_block=128)
+    _, _, st_res = ctx.trace_inv(op, dims, S, 1e-10, opts)
+    ctx.trace_inv_bounds(op, dims, S, 1e-10, opts)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    Tb, lo, hi, st_b = ctx.trace_inv_bounds(op, dims, S, 1e-10, opts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bounds = {"solves_per_s": st_b["rhs_solved"] / (e0.elapsed_time(e1) / 1e3),
+              "iters_per_solve": st_b["iterations_total"] / max(1, st_b["rhs_solved"]),
+              "iters_per_solve_residual_stop": st_res["iterations_total"] / max(1, st_res["rhs_solved"]),
+              "T_S": float(Tb[-1].real), "T_S_lower": float(lo[-1]), "T_S_upper": float(hi[-1])}
     out = {"metric": "probing solves/s, Section 5.2 variance study (64^3 Laplacian, cond ~100, CG 1e-10)",
            "value": solves / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic (shifted periodic Laplacian, exact trace in closed form)",
            "config": {"workload": "64^3 Laplacian m = 12/99, %d vectors of hierarchical probing, natural-order "
                                   "Hadamard and Z_2 noise per z_0 seed, %d seeds" % (S, args.steps)},
-           "exact_trace": exact, "study": study}
+           "exact_trace": exact, "study": study, "quadrature_bounds": bounds}
     print(json.dumps(out), flush=True)
 
 

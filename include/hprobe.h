@@ -217,6 +217,25 @@ hp_status hp_trace_inv(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat
                        double tol, const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
                        hp_solve_stats* stats);
 
+/* hp_trace_inv for the Hermitian positive definite Laplacian with guaranteed
+ * bounds on every quadrature (Section 1.1.2: the Gauss quadrature of
+ * z^H A^-1 z computed by Lanczos comes with lower and upper bounds): with
+ * x_0 = 0, CG's step lengths gamma_k and residual ratios delta_{k+1} give the
+ * Gauss rule G_k = sum_{j<k} gamma_j ||r_j||^2 <= z^H A^-1 z and, for a node
+ * 0 < mu <= lambda_min(A), the Gauss-Radau rule G_k + gt_k ||r_k||^2 >= z^H A^-1 z,
+ * gt_0 = 1/mu, gt_{k+1} = (gt_k - gamma_k) / (mu (gt_k - gamma_k) + delta_{k+1}).
+ * Each solve stops when its bracket is at most quad_tol times G_k (no residual
+ * test: the bracket certifies the quadrature, whose error falls as the square
+ * of the residual).  lambda_min: the node mu; <= 0 selects mass + min mu(s)
+ * (the hopping part of A is positive semidefinite).
+ * trace_prefix (host): T_s from z^H x as in hp_trace_inv; T_lower, T_upper
+ * (host, double[s_max]): bounds on Re T_s, s = 1 .. s_max.  opts->first must be 0.
+ * Errors: HP_EINVAL for a Wilson operator, quad_tol <= 0, a node <= 0; as
+ * hp_trace_inv otherwise (HP_ENOCONV if a bracket does not close in maxiter). */
+hp_status hp_trace_inv_bounds(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t s_max,
+                              double quad_tol, double lambda_min, const hp_solver_opts* opts,
+                              double* trace_prefix, double* T_lower, double* T_upper, hp_solve_stats* stats);
+
 /* hp_trace_inv plus the derivative of Re T_{s_max} with respect to the
  * per-site mass mu(s) (real):
  *   dT/dmu(s) = -(1/s_max) sum_{m,a} sum_c conj(y_{m,a}(s,c)) x_{m,a}(s,c),  y = A^-H v.

@@ -48,6 +48,43 @@ def cg(apply: Apply, b: np.ndarray, tol: float = 1e-13, maxiter: int = 10000) ->
     raise RuntimeError("oracle CG did not converge")
 
 
+def cg_quadrature_bounds(apply: Apply, b: np.ndarray, mu: float, tol: float,
+                         maxiter: int = 10000) -> tuple[np.ndarray, list]:
+    """CG on a Hermitian positive definite A with bounds on the quadrature b^H A^-1 b (Section 1.1.2:
+    the Lanczos/Gauss quadrature of z^H A^-1 z comes with lower and upper bounds).
+
+    With x_0 = 0, step lengths gamma_k = ||r_k||^2 / (p_k, A p_k) and delta_{k+1} = ||r_{k+1}||^2 /
+    ||r_k||^2, the Gauss rule after k steps is G_k = sum_{j<k} gamma_j ||r_j||^2 = b^H x_k (a lower
+    bound), and for 0 < mu <= lambda_min(A) the Gauss-Radau rule with the node mu adds
+    gt_k ||r_k||^2 (an upper bound), gt_0 = 1/mu,
+        gt_{k+1} = (gt_k - gamma_k) / (mu (gt_k - gamma_k) + delta_{k+1})
+    (the CG form of the Gauss-Radau recurrence of Golub and Meurant).  Stops when the bracket
+    is at most tol times the lower bound; returns x and the list of (lower, upper) per step."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = np.vdot(r, r).real
+    G, gt = 0.0, 1.0 / mu
+    hist = [(G, G + gt * rr)]
+    if rr == 0.0:
+        return x, hist
+    for _ in range(maxiter):
+        Ap = apply(p)
+        gamma = rr / np.vdot(p, Ap).real
+        x = x + gamma * p
+        r = r - gamma * Ap
+        rr_new = np.vdot(r, r).real
+        delta = rr_new / rr
+        G += gamma * rr
+        gt = (gt - gamma) / (mu * (gt - gamma) + delta)
+        hist.append((G, G + gt * rr_new))
+        if gt * rr_new <= tol * G:
+            return x, hist
+        p = r + delta * p
+        rr = rr_new
+    raise RuntimeError("oracle CG did not reach the quadrature tolerance")
+
+
 def bicgstab(apply: Apply, b: np.ndarray, tol: float = 1e-13, maxiter: int = 10000) -> tuple[np.ndarray, int]:
     bn = _norm(b)
     x = np.zeros_like(b)

@@ -211,9 +211,15 @@ static hp_status finish_trace(hp_ctx* ctx, const SolveResult& res, int L, int do
   return HP_OK;
 }
 
+// quadrature-bracket stopping of the Laplacian CG (hp_trace_inv_bounds)
+struct BoundsReq {
+  double quad_tol, lambda_min;
+  double *T_lower, *T_upper;
+};
+
 static hp_status trace_common(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t s_max, double tol,
                               const hp_solver_opts* opts, double* q_inout, double* trace_prefix, double* dT_dmu,
-                              double* dT_dm, hp_solve_stats* stats) {
+                              double* dT_dm, hp_solve_stats* stats, const BoundsReq* bounds = nullptr) {
   HP_TRY(check_ctx(ctx));
   LatGeom g;
   LatticeSetup* ls = nullptr;
@@ -238,6 +244,26 @@ static hp_status trace_common(hp_ctx* ctx, const hp_operator* op, const hp_latti
     return HP_EINVAL;
   }
   HP_TRY(prepare_operator(ctx, op, &g, opts->precision, "op0"));
+  if (bounds) {   // Gauss-Radau node: the caller's bound, else m + min mu(x) (the Laplacian part is PSD)
+    double mu = bounds->lambda_min;
+    if (!(mu > 0.0)) {
+      mu = op->mass;
+      if (op->mass_field) {
+        std::vector<double> mf((size_t)g.V);
+        HP_CUDA(cudaMemcpyAsync(mf.data(), g.mass_field, sizeof(double) * mf.size(), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+        HP_CUDA(cudaStreamSynchronize(ctx->stream));
+        mu += *std::min_element(mf.begin(), mf.end());
+      }
+    }
+    if (!(mu > 0.0) || !std::isfinite(mu)) {
+      hp_set_error("the Gauss-Radau node must be positive (lambda_min = %g): the operator is not positive definite",
+                   mu);
+      return HP_EINVAL;
+    }
+    g.quad_mu = mu;
+    g.quad_tol = bounds->quad_tol;
+  }
   SolveProblem pb;
   pb.lats.push_back(g);
   pb.s_max.push_back(s_max);
@@ -255,6 +281,18 @@ static hp_status trace_common(hp_ctx* ctx, const hp_operator* op, const hp_latti
   HP_TRY(run_solve(ctx, pb, res));
   const int dof = op->kind == HP_OP_WILSON ? 12 : g.parts;
   HP_TRY(finish_trace(ctx, res, 0, dof, opts->first, s_max, q_inout, trace_prefix));
+  if (bounds) {   // T_s bounds: (1/s) sum over probes and parts of the per-solve brackets
+    double lo = 0.0, hi = 0.0;
+    for (int64_t m = 0; m < s_max; ++m) {
+      for (int a = 0; a < dof; ++a) {
+        const double2 b = res.qb[0][(size_t)m * dof + a];
+        lo += b.x;
+        hi += b.y;
+      }
+      bounds->T_lower[m] = lo / (double)(m + 1);
+      bounds->T_upper[m] = hi / (double)(m + 1);
+    }
+  }
   if (grad) {
     void* p = nullptr;
     double* out = dT_dmu;
@@ -288,6 +326,27 @@ extern "C" hp_status hp_trace_inv(hp_ctx* ctx, const hp_operator* op, const hp_l
                                   const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
                                   hp_solve_stats* stats) {
   return trace_common(ctx, op, lat, s_max, tol, opts, q_inout, trace_prefix, nullptr, nullptr, stats);
+}
+
+extern "C" hp_status hp_trace_inv_bounds(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t s_max,
+                                         double quad_tol, double lambda_min, const hp_solver_opts* opts,
+                                         double* trace_prefix, double* T_lower, double* T_upper,
+                                         hp_solve_stats* stats) {
+  if (!op || op->kind != HP_OP_LAPLACIAN) {
+    hp_set_error("hp_trace_inv_bounds: the quadrature bounds need a Hermitian positive definite operator "
+                 "(the Laplacian)");
+    return HP_EINVAL;
+  }
+  if (!T_lower || !T_upper || !(quad_tol > 0.0) || !std::isfinite(quad_tol)) {
+    hp_set_error("hp_trace_inv_bounds: T_lower, T_upper and a positive quad_tol are required");
+    return HP_EINVAL;
+  }
+  if (opts && opts->first != 0) {
+    hp_set_error("hp_trace_inv_bounds: first must be 0");
+    return HP_EINVAL;
+  }
+  const BoundsReq b{quad_tol, lambda_min, T_lower, T_upper};
+  return trace_common(ctx, op, lat, s_max, quad_tol, opts, nullptr, trace_prefix, nullptr, nullptr, stats, &b);
 }
 
 extern "C" hp_status hp_trace_inv_grad(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t s_max,

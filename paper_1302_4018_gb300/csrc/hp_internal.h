@@ -59,6 +59,8 @@ struct LatGeom {
   int qstride[8];         // strides of the q-torus (sizes p_j)
   unsigned long long z0_seed;
   int probe_kind;         // hp_probe_kind: hierarchical (0), natural-order Hadamard (1), Z_2 noise (2)
+  double quad_tol;        // Laplacian CG: > 0 stops on the quadrature bracket (Gauss / Gauss-Radau)
+  double quad_mu;         // the Gauss-Radau node, 0 < quad_mu <= lambda_min(A)
   const uint32_t* loc;    // [V] hierarchical position of each site
   const int32_t* wtab;    // [Q] position inside the odd block of each q point
   const double2* ptab;    // [P] (cos, sin) of 2 pi k / P
@@ -98,7 +100,9 @@ enum { SLOT_EMPTY = 0, SLOT_INIT = 1, SLOT_RUN = 2, SLOT_DONE = 3, SLOT_FAIL = 4
 struct SlotState {
   double2 alpha, beta, omega, rho;   // BiCGStab scalars (CG uses .x)
   double bnorm2, rnorm2, rmax2, true_res2;
-  double rexact2, pad_d;             // ||r||^2 at the last FP64 true residual
+  double rexact2;                    // ||r||^2 at the last FP64 true residual
+  double gauss, radau;               // CG quadrature bounds: Gauss sum G_k, Gauss-Radau coefficient
+  double pad_d;
   double2 q;                         // quadrature v^H x at harvest
   int status, need_update, restart, iters;   // need_update: 1 group (FP32) update, 2 FP64 true residual
   int updates, lat, a, m;            // lattice index, dilution index / part, probe index
@@ -201,6 +205,7 @@ struct SolveProblem {
 
 struct SolveResult {
   std::vector<std::vector<double2>> qj;   // per lattice, per right-hand side (m*dof+a)
+  std::vector<std::vector<double2>> qb;   // CG quadrature bounds (lower, upper) in the same order
   hp_solve_stats stats;
   bool unconverged = false;
 };

@@ -145,6 +145,8 @@ __global__ void __launch_bounds__(NT) k_cg_init(LArgs a) {
       S->need_update = 0;
       S->restart = 0;
       S->true_res2 = tot[0];
+      S->gauss = 0.0;
+      S->radau = g.quad_mu > 0.0 ? 1.0 / g.quad_mu : 0.0;
       S->status = tot[0] > 0.0 ? SLOT_RUN : SLOT_DONE;
       a.cnt[slot] = 0;
     }
@@ -169,6 +171,7 @@ __global__ void __launch_bounds__(NT) k_cg_ap(LArgs a) {
     block_sum_partials<1, NT>(part, a.gy, nparts, tot);
     if (threadIdx.x == 0) {
       S->alpha = make_double2(tot[0] != 0.0 ? S->rho.x / tot[0] : 0.0, 0.0);
+      S->gauss += S->alpha.x * S->rho.x;   // Gauss rule: G_{k+1} = G_k + gamma_k ||r_k||^2
       S->restart = 0;
       S->sloppy_mv += 1;
       a.cnt[slot] = 0;
@@ -196,13 +199,24 @@ __global__ void __launch_bounds__(NT) k_cg_xr(LArgs a) {
     block_sum_partials<1, NT>(part, a.gy, nparts, tot);
     if (threadIdx.x == 0) {
       const double rr = tot[0];
-      S->beta = make_double2(S->rho.x != 0.0 ? rr / S->rho.x : 0.0, 0.0);
+      const double delta = S->rho.x != 0.0 ? rr / S->rho.x : 0.0;
+      S->beta = make_double2(delta, 0.0);
       S->rho = make_double2(rr, 0.0);
       S->rnorm2 = rr;
       S->iters += 1;
+      if (g.quad_mu > 0.0) {   // Gauss-Radau: gt_{k+1} = (gt_k - gamma_k) / (mu (gt_k - gamma_k) + delta_{k+1})
+        const double d = S->radau - S->alpha.x;
+        const double den = g.quad_mu * d + delta;
+        S->radau = den > 0.0 ? fmax(d, 0.0) / den : 0.0;
+      }
       if (S->iters >= a.maxiter) {
         S->status = SLOT_FAIL;
         S->need_update = 1;
+      } else if (g.quad_tol > 0.0) {   // stop on the quadrature bracket: no residual test, no restart
+        if (S->radau * rr <= g.quad_tol * S->gauss || rr == 0.0 || !(rr == rr)) {
+          S->true_res2 = rr;
+          S->status = (rr == rr) ? SLOT_DONE : SLOT_FAIL;
+        }
       } else if (rr <= a.tol2 * S->bnorm2 || !(rr == rr)) {
         S->need_update = 1;
       }

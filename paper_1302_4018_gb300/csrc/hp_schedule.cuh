@@ -25,10 +25,12 @@ hp_status run_schedule(hp_ctx* ctx, Engine& eng, SolveProblem& pb, SolveResult& 
   };
   std::vector<Item> queue;
   res.qj.assign(nl, {});
+  res.qb.assign(nl, {});
   for (int L = 0; L < nl; ++L) {
     const int dof = pb.lats[L].op_kind == HP_OP_WILSON ? dof_wilson : pb.lats[L].parts;
     const int64_t n = (pb.s_max[L] - pb.first[L]) * dof;
     res.qj[L].assign((size_t)n, make_double2(0.0, 0.0));
+    res.qb[L].assign((size_t)n, make_double2(0.0, 0.0));
     for (int64_t m = pb.first[L]; m < pb.s_max[L]; ++m)
       for (int a = 0; a < dof; ++a) queue.push_back({L, (int)m, a});
   }
@@ -125,6 +127,7 @@ hp_status run_schedule(hp_ctx* ctx, Engine& eng, SolveProblem& pb, SolveResult& 
         const int L = S.lat;
         const int dof = pb.lats[L].op_kind == HP_OP_WILSON ? dof_wilson : pb.lats[L].parts;
         res.qj[L][(size_t)(S.m - pb.first[L]) * dof + S.a] = S.q;
+        res.qb[L][(size_t)(S.m - pb.first[L]) * dof + S.a] = make_double2(S.gauss, S.gauss + S.radau * S.rnorm2);
         res.stats.rhs_solved += 1;
         res.stats.iterations_total += S.iters;
         res.stats.iterations_max = std::max(res.stats.iterations_max, S.iters);

@@ -43,7 +43,7 @@ EXPORTED = ["hp_ctx_create", "hp_ctx_destroy", "hp_last_error", "hp_ctx_synchron
             "hp_phase_values",
             "hp_permutation", "hp_probe_vectors", "hp_trace_inv", "hp_trace_inv_grad", "hp_trace_inv_batch",
             "hp_operator_apply", "hp_dslash_bench", "hp_profile_enable", "hp_profile_report",
-            "hp_launch_count", "hp_operator_apply_noalloc", "hp_probe_sequence"]
+            "hp_launch_count", "hp_operator_apply_noalloc", "hp_probe_sequence", "hp_trace_inv_bounds"]
 
 
 class Lattice(C.Structure):
@@ -96,6 +96,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hp_probe_sequence": (C.c_int, [P, C.POINTER(Lattice), I32, I64, I64, C.c_uint64, P, C.POINTER(I32)]),
         "hp_trace_inv": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I64, D, C.POINTER(SolverOpts),
                                    P, P, C.POINTER(SolveStats)]),
+        "hp_trace_inv_bounds": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I64, D, D,
+                                          C.POINTER(SolverOpts), P, P, P, C.POINTER(SolveStats)]),
         "hp_trace_inv_grad": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I64, D,
                                         C.POINTER(SolverOpts), P, P, P, C.POINTER(SolveStats)]),
         "hp_trace_inv_batch": (C.c_int, [P, I32, P, P, P, D, C.POINTER(SolverOpts), P, C.POINTER(SolveStats)]),
@@ -275,6 +277,19 @@ class Context:
         _check(lib().hp_trace_inv(self._h, C.byref(op), C.byref(make_lattice(dims)), int(s_max), float(tol),
                                   C.byref(opts), _ptr(q_inout), _ptr(T), C.byref(st)))
         return T, q_inout, st.as_dict()
+
+    def trace_inv_bounds(self, op: Operator, dims, s_max: int, quad_tol: float, opts: SolverOpts,
+                         lambda_min: float = 0.0):
+        """Laplacian: (T [s_max] complex, T_lower [s_max], T_upper [s_max], stats dict) with every
+        quadrature bracketed by Gauss / Gauss-Radau rules to quad_tol (relative)."""
+        T = np.zeros(s_max, dtype=np.complex128)
+        lo = np.zeros(s_max)
+        hi = np.zeros(s_max)
+        st = SolveStats()
+        _check(lib().hp_trace_inv_bounds(self._h, C.byref(op), C.byref(make_lattice(dims)), int(s_max),
+                                         float(quad_tol), float(lambda_min), C.byref(opts), _ptr(T), _ptr(lo),
+                                         _ptr(hi), C.byref(st)))
+        return T, lo, hi, st.as_dict()
 
     def trace_inv_grad(self, op: Operator, dims, s_max: int, tol: float, opts: SolverOpts, grad_out):
         """Returns (T, dT/dm, stats); dT/dmu(x) is written into ``grad_out`` (host float64 array or

@@ -103,3 +103,4 @@ def test_noalloc_rejects_clover_without_gpu():
                                        None)
     assert st == hprobe.HP_EINVAL
     assert "csw" in lib.hp_last_error().decode()
+

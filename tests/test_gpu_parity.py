@@ -674,3 +674,45 @@ def test_variance_of_hierarchical_probing_over_z0_matches_closed_form(ctx, hp):
     assert abs(Ts.var(ddof=1) / var - 1) <= 4 * np.sqrt(2.0 / (n - 1)) + 0.1
     var_nat = E.z0_variance(B, 1 - 2 * Pr.probe_phases_natural(V, 0, 32, 0), 32)
     assert var < var_nat
+
+
+# ------------------------------------------------------------------ quadrature bounds (Section 1.1.2)
+@pytest.mark.parametrize("dims,mass,seed,mf", [((8, 8, 8, 8), 0.05, 1, False), ((6, 6, 2, 3), 0.2, 5, False),
+                                               ((4, 4, 4, 8), 0.1, 3, True)])
+def test_laplacian_quadrature_bounds_bracket_the_oracle(ctx, hp, dims, mass, seed, mf):
+    """Every prefix T_s lies between the Gauss and Gauss-Radau bounds, and the brackets closed to
+    the requested relative width; the last case uses a mass field (node m + min mu)."""
+    V = int(np.prod(dims))
+    field = synth.mass_field(dims, 0.02, 40) if mf else None
+    op = ctx.make_operator(hp.OP_LAPLACIAN, mass, 0.0, None, dev(field) if mf else None)
+    s = min(32, hp.basis_info(dims)["n_vectors"])
+    T, lo, hi, st = ctx.trace_inv_bounds(op, dims, s, 1e-10, ctx.make_opts("fp64", z0_seed=seed, rhs_block=64))
+    T_ref = E.trace_prefix(E.laplacian_quadratures(dims, mass, 0, s, seed, mass_field=field, method="dense")).real
+    assert np.all(lo <= T_ref * (1 + 1e-12)) and np.all(hi >= T_ref * (1 - 1e-12))
+    assert np.all((hi - lo) <= 1.1e-10 * np.abs(lo))
+    assert np.all(rel(T.real, T_ref) <= 1e-9)
+    assert st["rhs_solved"] == s * (2 if hp.basis_info(dims)["period"] > 2 else 1)
+
+
+def test_quadrature_bounds_stop_earlier_than_the_residual(ctx, hp):
+    """The quadrature error falls as the square of the residual: bracketing each quadrature to 1e-10
+    takes fewer CG iterations than a 1e-10 residual, for the same estimate."""
+    dims = (8, 8, 8, 8)
+    op = ctx.make_operator(hp.OP_LAPLACIAN, 0.05)
+    opts = ctx.make_opts("fp64", z0_seed=2, rhs_block=64)
+    T, lo, hi, sb = ctx.trace_inv_bounds(op, dims, 64, 1e-10, opts)
+    T2, _, sr = ctx.trace_inv(op, dims, 64, 1e-10, opts)
+    assert sb["iterations_total"] < 0.8 * sr["iterations_total"]
+    assert np.all(rel(T, T2) <= 1e-9)
+
+
+def test_quadrature_bounds_reject_wilson_and_bad_node(ctx, hp):
+    U = synth.gauge_links((4, 4, 2, 4), 0.3, 1)
+    opw = ctx.make_operator(hp.OP_WILSON, 0.0, 0.12, links_dev(U), None)
+    with pytest.raises(hp.HProbeError) as e:
+        ctx.trace_inv_bounds(opw, (4, 4, 2, 4), 2, 1e-10, ctx.make_opts("fp64"))
+    assert e.value.status == hp.HP_EINVAL
+    opl = ctx.make_operator(hp.OP_LAPLACIAN, -0.5)
+    with pytest.raises(hp.HProbeError) as e:
+        ctx.trace_inv_bounds(opl, (4, 4), 2, 1e-10, ctx.make_opts("fp64"))
+    assert e.value.status == hp.HP_EINVAL

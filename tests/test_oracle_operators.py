@@ -178,3 +178,41 @@ def test_clover_vanishes_on_pure_gauge_links():
     D = O.wilson_dense(Ug, dims, 0.12, 0.0, clover=O.clover_term(Ug, dims, 0.12, 1.7))
     exact = free_wilson_trace_inverse(dims, 0.12)
     assert abs(np.trace(np.linalg.inv(D)).real - exact) <= 1e-10 * exact
+
+
+# ------------------------------------------------------------------ quadrature bounds (Section 1.1.2)
+@pytest.mark.parametrize("case", ["laplacian", "random_spd"])
+def test_cg_quadrature_bounds_bracket_the_exact_quadrature(case):
+    """Gauss (lower) and Gauss-Radau (upper) bounds from the CG coefficients: every step brackets
+    b^T A^-1 b, the lower bound is b^T x_k, and the bracket closes to the tolerance."""
+    rng = np.random.default_rng(3)
+    if case == "laplacian":
+        dims = (4, 4, 2, 4)
+        A = O.laplacian_dense(dims, 0.2)
+        mu = 0.2                                        # lambda_min of the shifted Laplacian
+    else:
+        n = 80
+        Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        lam = np.sort(rng.uniform(0.1, 5.0, n))
+        A = (Q * lam) @ Q.T
+        mu = 0.9 * lam[0]
+    b = rng.standard_normal(A.shape[0])
+    exact = b @ np.linalg.solve(A, b)
+    x, hist = S.cg_quadrature_bounds(lambda v: A @ v, b, mu, 1e-12)
+    for lo, hi in hist:
+        assert lo <= exact * (1 + 1e-12) and hi >= exact * (1 - 1e-12)
+    assert abs(hist[-1][0] - b @ x) <= 1e-12 * exact
+    assert hist[-1][1] - hist[-1][0] <= 1e-12 * hist[-1][0]
+    widths = [hi - lo for lo, hi in hist]
+    assert widths[-1] < 1e-9 * widths[0]
+
+
+def test_cg_quadrature_bounds_needs_mu_below_spectrum():
+    """A node above lambda_min loses the guarantee: the 'upper bound' falls below the exact value
+    at some step (the property the bound rests on is real)."""
+    dims = (4, 4, 2, 4)
+    A = O.laplacian_dense(dims, 0.2)
+    b = np.random.default_rng(4).standard_normal(A.shape[0])
+    exact = b @ np.linalg.solve(A, b)
+    _, hist = S.cg_quadrature_bounds(lambda v: A @ v, b, 3.0, 1e-12)
+    assert any(hi < exact * (1 - 1e-9) for _, hi in hist)
