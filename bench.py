@@ -67,10 +67,10 @@ def source_hash(kernel):
 
 
 # DRAM traffic of one launch with every slot active (24 on 32^3x64), from one ncu capture of the
-# same kernel on 32^3x16 with 12 slots (411.9 MB read + 146.7 MB written): the spinor part scaled
+# same kernel on 32^3x16 with 12 slots (411.8 MB read + 146.2 MB written): the spinor part scaled
 # by the site-RHS ratio (8x), the links (read once per launch) by the site ratio (4x); valid only
 # for the kernel source it was taken on
-NCU_TRAFFIC = {("k_eo_even", "5c1bb325740d"): {"bytes_all_slots": 4.1668e9, "alg_bytes_all_slots": 1048576 * 104 * 24 + 4 * 2097152 * 36}}
+NCU_TRAFFIC = {("k_eo_even", "8a6ecae2d29e"): {"bytes_all_slots": 4.162e9, "alg_bytes_all_slots": 1048576 * 104 * 24 + 4 * 2097152 * 36}}
 
 
 class Clocks:
