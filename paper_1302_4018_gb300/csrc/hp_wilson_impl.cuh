@@ -10,11 +10,6 @@
 
 #include "hp_fields.cuh"
 
-template <int SPR>
-static size_t spinor_bytes_of() {
-  return SPR == PR64 ? 192 : (SPR == PR32 ? 96 : 48);
-}
-
 static size_t field_bytes(int spr, int nslots, int Vmax, size_t* norm_bytes) {
   size_t per = spr == PR64 ? 192 : (spr == PR32 ? 96 : 48);
   *norm_bytes = (spr == PR16 || spr == PRB16) ? sizeof(float) * (size_t)nslots * Vmax : 0;
