@@ -619,6 +619,160 @@ def run_variance(args):
     print(json.dumps(out), flush=True)
 
 
+SPARSE_DIMS = (64, 64, 64)
+SPARSE_SEED = 4242
+
+
+def sparse_kernel_bytes(name, n, nnz, c):
+    """Algorithmic DRAM bytes of a sparse-CG kernel over the run: the CSR matrix (12 B per entry,
+    4 B per row pointer) once per launch, every vector of a right-hand-side iteration read or
+    written once (8 B per row).  c: rhs_iters, exact (true residuals), launches."""
+    mat = 12 * nnz + 4 * (n + 1)
+    if name == "k_cg_ap":        # q = A p, (p, q)
+        return mat * c["launches"] + 16 * n * c["rhs_iters"]
+    if name == "k_cg_xr":        # x += a p, r -= a q, (r, r)
+        return 48 * n * c["rhs_iters"]
+    if name == "k_cg_p":         # p = r + b p
+        return 24 * n * c["rhs_iters"]
+    if name == "k_cg_true":      # r = b - A x
+        return mat * c["launches"] + 16 * n * c["exact"]
+    return None
+
+
+def run_sparse(args):
+    """Algorithm 1 and the probing trace on a general sparse matrix: the weighted graph Laplacian
+    plus 0.1 I of the periodic 64^3 grid (edge weights U[0.5, 1.5]) with its rows renumbered by a
+    seeded permutation, so that the row order carries no lattice structure (n = 262144, 7 entries
+    per row).  One step = the hierarchical colouring of the matrix plus FP64 CG to 1e-10 on the
+    first S probing vectors (complex vectors: two real solves each)."""
+    import torch
+
+    from oracle import solvers as OS
+    from oracle import sparse_probing as OSP
+    from paper_1302_4018_gb300 import hprobe, synth
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = hprobe.Context(0, stream=stream.cuda_stream)
+    rp, ci, val = synth.grid_matrix(SPARSE_DIMS, SPARSE_SEED, shift=0.1)
+    n, nnz = len(rp) - 1, len(ci)
+    dev = lambda a: torch.from_numpy(a).to("cuda:0")
+    rp_d, ci_d, val_d = dev(rp), dev(ci), dev(val)
+    paths_d = torch.zeros((32, n), dtype=torch.int32, device="cuda:0")
+    S = args.sparse_vectors
+
+    def step(rp_, ci_, val_, paths_out, seed, ev=None):
+        if ev:
+            ev[0].record(stream)
+        paths, rad = ctx.sparse_coloring(rp_, ci_, 32, paths_out=paths_out)
+        if ev:
+            ev[1].record(stream)
+        T, _, st = ctx.trace_inv_sparse(rp_, ci_, val_, paths, rad, S, TOL,
+                                        ctx.make_opts("fp64", z0_seed=seed, rhs_block=args.sparse_rhs_block))
+        return T, st, rad
+
+    for w in range(args.warmup):
+        step(rp_d, ci_d, val_d, paths_d, 500 + w)
+    ctx.profile_enable(True)
+    ctx.profile_report()
+    clocks = Clocks(0)
+    n0 = ctx.launch_count()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    e0.record(stream)
+    runs = [step(rp_d, ci_d, val_d, paths_d, 1 + i, evs[i]) for i in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    colour_ms = sum(ev[0].elapsed_time(ev[1]) for ev in evs) / args.steps
+    launches = ctx.launch_count() - n0
+    prof = ctx.profile_report()
+    prof.pop("_autotune", None)
+    ctx.profile_enable(False)
+    stats = [r[1] for r in runs]
+    rad = runs[-1][2]
+    solves = sum(s["rhs_solved"] for s in stats)
+    iters = sum(s["iterations_total"] for s in stats)
+    exact = sum(s["reliable_updates"] for s in stats)
+    value = solves / (ms / 1e3)
+
+    # end to end: host CSR arrays through the C ABI, paths back to the host and in again
+    e2e = None
+    if not args.no_e2e:
+        step(rp, ci, val, None, 900)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_solves = sum(step(rp, ci, val, None, 901 + i)[1]["rhs_solved"] for i in range(max(1, min(2, args.steps))))
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        k = max(1, min(2, args.steps))
+        nlev = len(rad)
+        e2e = {"value": e2e_solves / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(2 * rp.nbytes + 2 * ci.nbytes + val.nbytes + 4 * nlev * n),
+               "d2h_bytes_per_step": int(4 * 32 * n + 32 * S), "steps": k}
+
+    peak, peak_kind = hbm_peak()
+    counts = {"rhs_iters": iters, "exact": exact}
+    kernels = {}
+    for name, rec in prof.items():
+        b = sparse_kernel_bytes(name, n, nnz, dict(counts, launches=rec["launches"]))
+        kernels[name] = {"launches": rec["launches"], "ms": rec["ms"],
+                         "GBps": (b / (rec["ms"] / 1e3) / 1e9) if b and rec["ms"] > 0 else None}
+    tot_ms = sum(r["ms"] for r in prof.values()) or 1.0
+    for k_ in kernels.values():
+        k_["share"] = k_["ms"] / tot_ms
+    top_name, top_rec = max(kernels.items(), key=lambda kv: kv[1]["ms"])
+    top_bytes = sparse_kernel_bytes(top_name, n, nnz, dict(counts, launches=top_rec["launches"]))
+    achieved = top_bytes / (top_rec["ms"] / 1e3) / 1e9 if top_bytes else None
+    roofline = {"kernel": top_name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": (top_bytes / top_rec["launches"]) if top_bytes else None,
+                "mean_launch_ms": top_rec["ms"] / top_rec["launches"], "traffic": None}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle as it stands: Algorithm 1 on the whole matrix, then its CG (scipy SpMV as the
+        # matrix-vector product) on the first probing vector's two real parts
+        import scipy.sparse as ssp
+
+        A = ssp.csr_matrix((val, ci, rp), shape=(n, n))
+        t0 = time.perf_counter()
+        _, _, opaths = OSP.hierarchical_coloring(A)
+        t_col = time.perf_counter() - t0
+        ph, Pp = OSP.path_phases(opaths, 0, 1, 1)
+        from oracle import probing as OP
+
+        w = OP.probe_values(ph, Pp)[0]
+        t0 = time.perf_counter()
+        for part in (w.real.copy(), w.imag.copy()):
+            if np.any(part):
+                OS.cg(lambda x: A @ x, part, tol=TOL)
+        t_solve = (time.perf_counter() - t0) / 2
+        per_step = solves / args.steps
+        cpu = {"value": per_step / (t_col + t_solve * per_step), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "Algorithm 1 on the whole matrix (%.1f s) and oracle CG on the two real parts of "
+                         "probing vector 0 (%.2f s per solve); value = solves per step / (colouring + "
+                         "solves per step x time per solve)" % (t_col, t_solve)}
+
+    out = {"metric": "probing solves/s, Algorithm 1 + CG trace on a general sparse matrix (n = 262144, CG 1e-10)",
+           "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic (weighted graph Laplacian + 0.1 I of a renumbered periodic grid)",
+           "config": {"workload": "renumbered 64^3 periodic grid Laplacian + 0.1 I, %d entries, hierarchical "
+                                  "colouring + %d probing vectors, FP64 CG 1e-10" % (nnz, S),
+                      "n": n, "nnz": nnz, "vectors": S, "rhs_block": args.sparse_rhs_block,
+                      "radices": rad, "l2": "vectors of all slots together exceed L2 (128 x 2 MB per vector)"},
+           "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
+           "colouring_ms": colour_ms,
+           "solver": {"rhs": solves, "iters_per_solve": iters / max(1, solves),
+                      "max_true_residual": max(s["max_true_residual"] for s in stats)},
+           "estimate": {"T_S": float(runs[-1][0][-1].real)}, "kernels": kernels}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -631,7 +785,9 @@ def main():
     ap.add_argument("--fp64-probes", type=int, default=1)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="headline", choices=["headline", "batch", "grad", "variance"])
+    ap.add_argument("--workload", default="headline", choices=["headline", "batch", "grad", "variance", "sparse"])
+    ap.add_argument("--sparse-vectors", type=int, default=128)
+    ap.add_argument("--sparse-rhs-block", type=int, default=128)
     ap.add_argument("--variance-vectors", type=int, default=512)
     ap.add_argument("--even-odd", type=int, default=1, help="1: iterate on the odd-site Schur complement")
     ap.add_argument("--grad-probes", type=int, default=128)
@@ -655,6 +811,8 @@ def main():
         run_grad(args)
     elif args.workload == "variance":
         run_variance(args)
+    elif args.workload == "sparse":
+        run_sparse(args)
     else:
         run_ours(args)
 

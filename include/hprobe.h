@@ -257,6 +257,60 @@ hp_status hp_trace_inv_batch(hp_ctx* ctx, int32_t nlat, const hp_operator* ops, 
                              const int64_t* s_max, double tol, const hp_solver_opts* opts,
                              double* const* trace_prefix, hp_solve_stats* stats);
 
+/* Hierarchical colouring of a general sparse matrix (Section 2.1, Algorithm 1).
+ * Level 1 colours the graph of A greedily, rows in increasing index, each row
+ * taking the smallest colour none of the already coloured rows of its CSR row
+ * has (entries i -> i are ignored).  The rows of each colour form a block of the
+ * next level, whose graph is the pattern of A_b(rows, :) A_b(:, rows) for the
+ * block's graph A_b; a block recurses unless it got one colour or as many
+ * colours as rows (a diagonal or dense block), and no level beyond max_levels
+ * is coloured.  Within every block rows keep their index order, so the result
+ * is the sequential algorithm's, bit for bit (computed as Jones-Plassmann
+ * rounds with the row index as priority, all blocks of a level at once).
+ * n: rows (>= 1); row_ptr int32[n+1] (row_ptr[0] = 0, non-decreasing),
+ * col_idx int32[row_ptr[n]] in [0, n): the pattern of A, host or device, read only.
+ * paths: int32[max_levels][n], host or device, written: paths[l][i] = colour of
+ * row i at level l + 1, 0 at the levels below the one where its block stopped.
+ * radices (host, int32[max_levels]): c(l + 1) = the largest colour count of a
+ * block of level l + 1 (0 past *n_levels); *n_levels (host): levels coloured.
+ * Working memory: the next level's graph, deduplicated through hash tables of
+ * up to four times its two-hop candidate count (HP_ENOMEM if that fails).
+ * Errors: HP_EINVAL for n < 1, max_levels outside [1, 32], NULL outputs, a
+ * decreasing row_ptr or a column index outside [0, n). */
+hp_status hp_sparse_coloring(hp_ctx* ctx, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                             int32_t max_levels, int32_t* paths, int32_t* radices, int32_t* n_levels);
+
+/* The probing vectors of a colour hierarchy (Section 2.2, Eq. Hperm-general-
+ * recursive, with the Fourier factor F_c(l) at every level): vector m has the
+ * mixed-radix digits d_l(m) (radix c(l), level 1 least significant) and
+ *   v_m(i) = z_0(i) prod_l exp(2 pi i d_l(m) paths[l][i] / c(l)),
+ * z_0 as in hp_probe_vectors (none for z0_seed = 0).  Where blocks of one level
+ * have different colour counts, c(l) is the largest (every row's colour is below
+ * it), so the first c(1)...c(k) vectors are exactly orthogonal on each
+ * colour class of level k.  The levels used are the smallest k with
+ * c(1)...c(k) >= first + count; the phases (uint16[count][n], device) are
+ * over the period P = lcm(2, c(1), ..., c(k)) returned in *period_out (host).
+ * paths / radices / n_levels as hp_sparse_coloring returns them (paths host or
+ * device; radices host).  Errors: HP_EINVAL for a range outside [0, n], a colour
+ * outside [0, c(l)), a host phase_dev; HP_EUNSUPPORTED when the hierarchy
+ * resolves fewer than first + count vectors or P exceeds 65535. */
+hp_status hp_sparse_probe_vectors(hp_ctx* ctx, int32_t n, const int32_t* paths, const int32_t* radices,
+                                  int32_t n_levels, int64_t first, int64_t count, uint64_t z0_seed,
+                                  uint16_t* phase_dev, int32_t* period_out);
+
+/* hp_trace_inv for a real symmetric positive definite sparse matrix A in CSR
+ * (row_ptr, col_idx as hp_sparse_coloring; values double[row_ptr[n]]; host or
+ * device): the probes are hp_sparse_probe_vectors' (opts->probe_kind 0) or the
+ * natural-order Hadamard / Z_2 sequences (1, 2; paths unused), each solved by
+ * FP64 CG to a true relative residual tol (complex probes as two real solves).
+ * q_inout, trace_prefix, stats as hp_trace_inv.  Errors: as hp_trace_inv and
+ * hp_sparse_probe_vectors, plus HP_EUNSUPPORTED for a precision other than FP64.
+ * A matrix that is not symmetric positive definite ends in HP_ENOCONV. */
+hp_status hp_trace_inv_sparse(hp_ctx* ctx, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                              const double* values, const int32_t* paths, const int32_t* radices, int32_t n_levels,
+                              int64_t s_max, double tol, const hp_solver_opts* opts, double* q_inout,
+                              double* trace_prefix, hp_solve_stats* stats);
+
 /* y = A x for nrhs fields in the canonical layout: Wilson complex128
  * [nrhs][V][4][3], Laplacian double [nrhs][V]; host or device.  precision
  * selects the stencil kernel used (the input is rounded to that storage,

@@ -128,12 +128,17 @@ def path_phases(paths: np.ndarray, first: int, count: int, z0_seed: int = 0) -> 
     return out, P
 
 
-def sparse_quadratures(A: sp.csr_matrix, paths: np.ndarray, first: int, count: int, z0_seed: int) -> np.ndarray:
-    """q_m = v_m^H A^-1 v_m for the path probing vectors (dense solve: small matrices)."""
+def quadratures_of_phases(A: sp.csr_matrix, phases: np.ndarray, P: int) -> np.ndarray:
+    """q_m = v_m^H A^-1 v_m (Section 1.1.2) for v_m(i) = exp(2 pi i phases[m, i] / P), by a dense
+    solve (small matrices)."""
     from .probing import probe_values
 
+    W = probe_values(phases, P)
+    X = np.linalg.solve(A.toarray(), W.T)
+    return np.array([np.vdot(W[m], X[:, m]) for m in range(W.shape[0])])
+
+
+def sparse_quadratures(A: sp.csr_matrix, paths: np.ndarray, first: int, count: int, z0_seed: int) -> np.ndarray:
+    """q_m for the path probing vectors m = first .. first+count-1."""
     ph, P = path_phases(paths, first, count, z0_seed)
-    W = probe_values(ph, P)
-    Ad = A.toarray()
-    X = np.linalg.solve(Ad, W.T)
-    return np.array([np.vdot(W[m], X[:, m]) for m in range(count)])
+    return quadratures_of_phases(A, ph, P)

@@ -328,6 +328,48 @@ extern "C" hp_status hp_trace_inv(hp_ctx* ctx, const hp_operator* op, const hp_l
   return trace_common(ctx, op, lat, s_max, tol, opts, q_inout, trace_prefix, nullptr, nullptr, stats);
 }
 
+extern "C" hp_status hp_trace_inv_sparse(hp_ctx* ctx, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                                         const double* values, const int32_t* paths, const int32_t* radices,
+                                         int32_t n_levels, int64_t s_max, double tol, const hp_solver_opts* opts,
+                                         double* q_inout, double* trace_prefix, hp_solve_stats* stats) {
+  HP_TRY(check_ctx(ctx));
+  if (!values) {
+    hp_set_error("sparse matrix: values are NULL");
+    return HP_EINVAL;
+  }
+  HP_TRY(check_solver_args(s_max, tol, opts, n, n));
+  if (opts->precision != HP_PREC_FP64) {
+    hp_set_error("the sparse CG runs in FP64 only (precision %d)", opts->precision);
+    return HP_EUNSUPPORTED;
+  }
+  if (opts->dilution != 0 && opts->dilution != 1) {
+    hp_set_error("dilution %d not supported for a sparse matrix (1)", opts->dilution);
+    return HP_EINVAL;
+  }
+  if (!trace_prefix || (opts->first > 0 && !q_inout)) {
+    hp_set_error("trace_prefix is NULL, or first > 0 without the earlier quadratures in q_inout");
+    return HP_EINVAL;
+  }
+  LatGeom g;
+  HP_TRY(hp_sparse_geom(ctx, n, row_ptr, col_idx, values, paths, radices, n_levels, s_max, opts->probe_kind, &g));
+  g.z0_seed = opts->z0_seed;
+  SolveProblem pb;
+  pb.lats.push_back(g);
+  pb.s_max.push_back(s_max);
+  pb.first.push_back(opts->first);
+  pb.tol = tol;
+  pb.opts = *opts;
+  SolveResult res;
+  HP_TRY(hp_solve_laplace(ctx, pb, res));
+  HP_TRY(finish_trace(ctx, res, 0, g.parts, opts->first, s_max, q_inout, trace_prefix));
+  if (stats) *stats = res.stats;
+  if (res.unconverged) {
+    hp_set_error("%d right-hand sides missed tol within maxiter", res.stats.n_unconverged);
+    return HP_ENOCONV;
+  }
+  return HP_OK;
+}
+
 extern "C" hp_status hp_trace_inv_bounds(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t s_max,
                                          double quad_tol, double lambda_min, const hp_solver_opts* opts,
                                          double* trace_prefix, double* T_lower, double* T_upper,

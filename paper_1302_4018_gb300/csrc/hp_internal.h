@@ -49,6 +49,8 @@ enum { PR64 = 0, PR32 = 1, PR16 = 2, PRB16 = 3, PRFF = 4 };
 // Everything a kernel needs about one lattice: geometry, probing basis and
 // operator.  Plain data, copied to device memory as an array (one entry per
 // lattice of a batch).
+#define HP_MAX_LEVELS 32   // levels of a colour hierarchy of a general sparse matrix
+
 struct LatGeom {
   int nd;                 // number of dimensions (operators: padded to 4)
   int L[8];
@@ -59,6 +61,14 @@ struct LatGeom {
   int qstride[8];         // strides of the q-torus (sizes p_j)
   unsigned long long z0_seed;
   int probe_kind;         // hp_probe_kind: hierarchical (0), natural-order Hadamard (1), Z_2 noise (2)
+  // a general sparse matrix (Algorithm 1 path): CSR rows of A, and the colour hierarchy that
+  // defines the probing vectors (paths[l * V + i] = colour of row i at level l + 1)
+  const int* csr_rp;
+  const int* csr_ci;
+  const double* csr_val;
+  const int* paths;
+  int nlev;
+  int radix[HP_MAX_LEVELS];
   double quad_tol;        // Laplacian CG: > 0 stops on the quadrature bracket (Gauss / Gauss-Radau)
   double quad_mu;         // the Gauss-Radau node, 0 < quad_mu <= lambda_min(A)
   const uint32_t* loc;    // [V] hierarchical position of each site
@@ -176,6 +186,12 @@ static inline int blocks_for(hp_ctx* ctx, long long n, int threads) {
   return (int)std::max(1LL, std::min(b, cap));
 }
 
+// general sparse matrix (hp_sparse.cu): geometry of the CSR operator and its probing sequence
+// for vectors m < s_end (row_ptr may be NULL for the probing vectors alone)
+hp_status hp_sparse_geom(hp_ctx* ctx, int32_t n, const int32_t* row_ptr, const int32_t* col_idx, const double* values,
+                         const int32_t* paths, const int32_t* radices, int32_t n_levels, int64_t s_end,
+                         int32_t probe_kind, LatGeom* g);
+
 // lattice setup (hp_core.cu)
 hp_status hp_validate_lattice(const hp_lattice* lat, int max_nd, std::vector<int64_t>* dims);
 hp_status hp_get_lattice(hp_ctx* ctx, const std::vector<int64_t>& dims, LatticeSetup** out);
@@ -225,6 +241,18 @@ __device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long s
 }
 
 __device__ __forceinline__ int probe_phase(const LatGeom& g, uint32_t site, uint32_t m) {
+  if (g.paths) {   // general sparse matrix: mixed-radix digits of m against the colour path of the row
+    int ph = 0;
+    uint32_t rest = m;
+    for (int l = 0; l < g.nlev; ++l) {
+      const uint32_t r = (uint32_t)g.radix[l];
+      const uint32_t d = rest % r;
+      rest /= r;
+      ph += (g.P / (int)r) * (int)((d * (uint32_t)g.paths[(size_t)l * g.V + site]) % r);
+    }
+    if (g.z0_seed && (splitmix64_at(g.z0_seed, site) >> 63)) ph += g.P >> 1;
+    return ph % g.P;
+  }
   if (g.probe_kind == HP_PROBE_Z2)   // independent Z_2 noise: top bit of output m V + site
     return (splitmix64_at(g.z0_seed, (unsigned long long)m * (unsigned long long)g.V + site) >> 63) ? (g.P >> 1) : 0;
   if (g.probe_kind == HP_PROBE_NATURAL) {   // Sylvester Hadamard H(site, m), natural order (V = 2^K)

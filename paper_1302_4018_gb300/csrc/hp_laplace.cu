@@ -17,6 +17,11 @@ static int lblocks(hp_ctx* ctx, long long n, int threads) {
 }
 
 __device__ __forceinline__ double lap_site(const LatGeom& g, const double* __restrict__ x, int site) {
+  if (g.csr_rp) {   // a general sparse matrix: row `site` of A times x
+    double acc = 0.0;
+    for (int e = g.csr_rp[site]; e < g.csr_rp[site + 1]; ++e) acc += g.csr_val[e] * __ldg(x + g.csr_ci[e]);
+    return acc;
+  }
   int r = site, st = 1;
   double acc = 0.0;
 #pragma unroll
@@ -75,16 +80,19 @@ struct LArgs {
   double *x, *r, *p, *q;   // [slot][Vmax]
   double tol2;
   int maxiter;
+  int by_slot;   // 1: grid (tiles, slots), 0: grid (slots, tiles)
 };
 
 #define LSLOT(COND)                                                \
-  const int slot = blockIdx.x;                                     \
+  const int slot = a.by_slot ? blockIdx.y : blockIdx.x;            \
+  const int bx = a.by_slot ? blockIdx.x : blockIdx.y;              \
+  const int gx = a.by_slot ? gridDim.x : gridDim.y;                \
   SlotState* S = a.st + slot;                                      \
   if (!(COND)) return;                                             \
   const LatGeom g = a.lats[S->lat];                                \
   const int ntiles = (g.V + NT - 1) / NT;                          \
-  if ((int)blockIdx.y >= ntiles) return;                           \
-  const int nparts = min((int)gridDim.y, ntiles);                  \
+  if (bx >= ntiles) return;                                        \
+  const int nparts = min(gx, ntiles);                              \
   double* part = a.part + (size_t)slot * 4 * a.gy;                 \
   const size_t off = (size_t)slot * a.Vmax;                        \
   (void)nparts;                                                    \
@@ -96,7 +104,7 @@ __device__ __forceinline__ double lap_source(const LatGeom& g, int site, int m, 
 }
 
 template <int NQ, int NT>
-__device__ __forceinline__ void lreduce(double (&v)[NQ], double* part, int gy) {
+__device__ __forceinline__ void lreduce(double (&v)[NQ], double* part, int gy, int bx) {
   __shared__ double sh[NQ][NT / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -112,7 +120,7 @@ __device__ __forceinline__ void lreduce(double (&v)[NQ], double* part, int gy) {
     for (int qq = 0; qq < NQ; ++qq) {
       double t = 0.0;
       for (int w = 0; w < NT / 32; ++w) t += sh[qq][w];
-      part[(size_t)qq * gy + blockIdx.y] = t;
+      part[(size_t)qq * gy + bx] = t;
     }
   }
 }
@@ -122,7 +130,7 @@ __global__ void __launch_bounds__(NT) k_cg_init(LArgs a) {
   LSLOT(S->status == SLOT_INIT)
   double acc[1] = {0.0};
   const int m = S->m, pa = S->a;
-  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+  for (int tile = bx; tile < ntiles; tile += gx) {
     const int site = tile * NT + threadIdx.x;
     if (site >= g.V) continue;
     double b = lap_source(g, site, m, pa);
@@ -131,7 +139,7 @@ __global__ void __launch_bounds__(NT) k_cg_init(LArgs a) {
     a.p[off + site] = b;
     acc[0] += b * b;
   }
-  lreduce<1, NT>(acc, part, a.gy);
+  lreduce<1, NT>(acc, part, a.gy, bx);
   if (last_block(a.cnt + slot, nparts)) {
     double tot[1];
     block_sum_partials<1, NT>(part, a.gy, nparts, tot);
@@ -158,14 +166,14 @@ template <int NT>
 __global__ void __launch_bounds__(NT) k_cg_ap(LArgs a) {
   LSLOT(S->status == SLOT_RUN)
   double acc[1] = {0.0};
-  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+  for (int tile = bx; tile < ntiles; tile += gx) {
     const int site = tile * NT + threadIdx.x;
     if (site >= g.V) continue;
     double qv = lap_site(g, a.p + off, site);
     a.q[off + site] = qv;
     acc[0] += a.p[off + site] * qv;
   }
-  lreduce<1, NT>(acc, part, a.gy);
+  lreduce<1, NT>(acc, part, a.gy, bx);
   if (last_block(a.cnt + slot, nparts)) {
     double tot[1];
     block_sum_partials<1, NT>(part, a.gy, nparts, tot);
@@ -185,7 +193,7 @@ __global__ void __launch_bounds__(NT) k_cg_xr(LArgs a) {
   LSLOT(S->status == SLOT_RUN)
   const double al = S->alpha.x;
   double acc[1] = {0.0};
-  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+  for (int tile = bx; tile < ntiles; tile += gx) {
     const int site = tile * NT + threadIdx.x;
     if (site >= g.V) continue;
     a.x[off + site] += al * a.p[off + site];
@@ -193,7 +201,7 @@ __global__ void __launch_bounds__(NT) k_cg_xr(LArgs a) {
     a.r[off + site] = rv;
     acc[0] += rv * rv;
   }
-  lreduce<1, NT>(acc, part, a.gy);
+  lreduce<1, NT>(acc, part, a.gy, bx);
   if (last_block(a.cnt + slot, nparts)) {
     double tot[1];
     block_sum_partials<1, NT>(part, a.gy, nparts, tot);
@@ -231,14 +239,14 @@ __global__ void __launch_bounds__(NT) k_cg_true(LArgs a) {
   LSLOT(S->need_update)
   double acc[1] = {0.0};
   const int m = S->m, pa = S->a;
-  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+  for (int tile = bx; tile < ntiles; tile += gx) {
     const int site = tile * NT + threadIdx.x;
     if (site >= g.V) continue;
     double rv = lap_source(g, site, m, pa) - lap_site(g, a.x + off, site);
     a.r[off + site] = rv;
     acc[0] += rv * rv;
   }
-  lreduce<1, NT>(acc, part, a.gy);
+  lreduce<1, NT>(acc, part, a.gy, bx);
   if (last_block(a.cnt + slot, nparts)) {
     double tot[1];
     block_sum_partials<1, NT>(part, a.gy, nparts, tot);
@@ -266,7 +274,7 @@ template <int NT>
 __global__ void __launch_bounds__(NT) k_cg_p(LArgs a) {
   LSLOT(S->status == SLOT_RUN)
   const double be = S->restart ? 0.0 : S->beta.x;
-  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+  for (int tile = bx; tile < ntiles; tile += gx) {
     const int site = tile * NT + threadIdx.x;
     if (site >= g.V) continue;
     a.p[off + site] = a.r[off + site] + be * a.p[off + site];
@@ -278,12 +286,12 @@ __global__ void __launch_bounds__(NT) k_lquad(LArgs a) {
   LSLOT(S->status == SLOT_DONE || S->status == SLOT_FAIL)
   double acc[1] = {0.0};
   const int m = S->m, pa = S->a;
-  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+  for (int tile = bx; tile < ntiles; tile += gx) {
     const int site = tile * NT + threadIdx.x;
     if (site >= g.V) continue;
     acc[0] += lap_source(g, site, m, pa) * a.x[off + site];
   }
-  lreduce<1, NT>(acc, part, a.gy);
+  lreduce<1, NT>(acc, part, a.gy, bx);
   if (last_block(a.cnt + slot, nparts)) {
     double tot[1];
     block_sum_partials<1, NT>(part, a.gy, nparts, tot);
@@ -315,10 +323,15 @@ struct LaplaceEngine {
   hp_ctx* ctx;
   LArgs a;
   int nslots, gy;
-  dim3 grid() const { return dim3(nslots, gy); }
+  // A sparse matrix runs with slots along y: the blocks of one slot are scheduled together,
+  // so the vector its rows gather from stays in L2 while the slot runs (slots along x would
+  // interleave all of them, and every gather of a renumbered matrix would be a DRAM sector).
+  // The lattice stencil reads neighbours that are near in memory; there slots along x measured
+  // faster (all slots stream at once).
+  dim3 grid() const { return a.by_slot ? dim3(gy, nslots) : dim3(nslots, gy); }
   int group() const { return 1; }
   hp_status setup(int ns, int Vmax, const LatGeom* lats_dev, SlotState* st, const hp_solver_opts& o, double tol,
-                  double, const LatGeom&) {
+                  double, const LatGeom& big) {
     nslots = ns;
     memset(&a, 0, sizeof(a));
     a.lats = lats_dev;
@@ -344,6 +357,7 @@ struct LaplaceEngine {
     a.q = (double*)p;
     a.tol2 = tol * tol;
     a.maxiter = o.maxiter > 0 ? o.maxiter : 10000;
+    a.by_slot = big.csr_rp != nullptr;
     return HP_OK;
   }
   hp_status init() {

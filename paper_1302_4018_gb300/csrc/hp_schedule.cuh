@@ -40,6 +40,7 @@ hp_status run_schedule(hp_ctx* ctx, Engine& eng, SolveProblem& pb, SolveResult& 
     nslots = (int)std::max(12LL, std::min(want, 256LL));
   }
   nslots = (int)std::min<long long>(nslots, std::max<size_t>(1, queue.size()));
+  nslots = std::min(nslots, 65535);   // one grid dimension of the solver kernels
   nslots = (nslots + Engine::GROUP_MAX - 1) / Engine::GROUP_MAX * Engine::GROUP_MAX;
   int big = 0;
   for (int L = 1; L < nl; ++L)

@@ -43,7 +43,8 @@ EXPORTED = ["hp_ctx_create", "hp_ctx_destroy", "hp_last_error", "hp_ctx_synchron
             "hp_phase_values",
             "hp_permutation", "hp_probe_vectors", "hp_trace_inv", "hp_trace_inv_grad", "hp_trace_inv_batch",
             "hp_operator_apply", "hp_dslash_bench", "hp_profile_enable", "hp_profile_report",
-            "hp_launch_count", "hp_operator_apply_noalloc", "hp_probe_sequence", "hp_trace_inv_bounds"]
+            "hp_launch_count", "hp_operator_apply_noalloc", "hp_probe_sequence", "hp_trace_inv_bounds",
+            "hp_sparse_coloring", "hp_sparse_probe_vectors", "hp_trace_inv_sparse"]
 
 
 class Lattice(C.Structure):
@@ -108,6 +109,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hp_launch_count": (C.c_int, [P, C.POINTER(I64)]),
         "hp_operator_apply_noalloc": (C.c_int, [C.POINTER(Operator), C.POINTER(Lattice), I64, P, P, P]),
         "hp_profile_report": (C.c_int, [P, C.c_char_p, I64]),
+        "hp_sparse_coloring": (C.c_int, [P, I32, P, P, I32, P, P, C.POINTER(I32)]),
+        "hp_sparse_probe_vectors": (C.c_int, [P, I32, P, P, I32, I64, I64, C.c_uint64, P, C.POINTER(I32)]),
+        "hp_trace_inv_sparse": (C.c_int, [P, I32, P, P, P, P, P, I32, I64, D, C.POINTER(SolverOpts), P, P,
+                                          C.POINTER(SolveStats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -290,6 +295,54 @@ class Context:
                                          float(quad_tol), float(lambda_min), C.byref(opts), _ptr(T), _ptr(lo),
                                          _ptr(hi), C.byref(st)))
         return T, lo, hi, st.as_dict()
+
+    # ---------------------------------------------------------------- general sparse matrices
+    @staticmethod
+    def _csr(row_ptr, col_idx, values=None):
+        """int32 row_ptr / col_idx (and float64 values): numpy arrays or torch tensors, either side."""
+        for a, dt in ((row_ptr, "int32"), (col_idx, "int32"), (values, "float64")):
+            if a is not None:
+                assert str(a.dtype).endswith(dt), "CSR arrays must be %s" % dt
+        return _ptr(row_ptr), _ptr(col_idx), _ptr(values)
+
+    def sparse_coloring(self, row_ptr, col_idx, max_levels: int = 32, paths_out=None):
+        """Hierarchical colouring of the pattern of an n x n CSR matrix (Algorithm 1).  Returns
+        (paths [n_levels, n] int32, radices list): paths[l, i] = colour of row i at level l + 1.
+        ``paths_out`` (optional, int32 [max_levels, n], host or device) receives all levels."""
+        n = int(row_ptr.shape[0]) - 1
+        if paths_out is None:
+            paths_out = np.zeros((max_levels, max(n, 0)), dtype=np.int32)
+        rad = np.zeros(max_levels, dtype=np.int32)
+        nl = C.c_int32()
+        rp, ci, _ = self._csr(row_ptr, col_idx)
+        _check(lib().hp_sparse_coloring(self._h, n, rp, ci, int(max_levels), _ptr(paths_out), _ptr(rad),
+                                        C.byref(nl)))
+        return paths_out[:nl.value], [int(r) for r in rad[:nl.value]]
+
+    def sparse_probe_vectors(self, paths, radices: Sequence[int], first: int, count: int, z0_seed: int, out) -> int:
+        """uint16 phases of the path probing vectors into ``out`` (device tensor of count*n);
+        returns the period."""
+        n = int(paths.shape[1])
+        rad = np.ascontiguousarray(np.asarray(radices, dtype=np.int32))
+        per = C.c_int32()
+        _check(lib().hp_sparse_probe_vectors(self._h, n, _ptr(paths), _ptr(rad), len(rad), int(first), int(count),
+                                             C.c_uint64(z0_seed), _ptr(out), C.byref(per)))
+        return per.value
+
+    def trace_inv_sparse(self, row_ptr, col_idx, values, paths, radices: Sequence[int], s_max: int, tol: float,
+                         opts: SolverOpts, q_inout=None):
+        """Tr(A^-1) estimates of a real symmetric positive definite CSR matrix with the path probing
+        vectors (or opts.probe_kind's sequence): (T [s_max] complex, q, stats)."""
+        n = int(row_ptr.shape[0]) - 1
+        rad = np.ascontiguousarray(np.asarray(radices, dtype=np.int32))
+        T = np.zeros(s_max, dtype=np.complex128)
+        st = SolveStats()
+        if q_inout is not None:
+            assert q_inout.dtype == np.complex128 and q_inout.shape == (s_max,)
+        rp, ci, va = self._csr(row_ptr, col_idx, values)
+        _check(lib().hp_trace_inv_sparse(self._h, n, rp, ci, va, _ptr(paths), _ptr(rad), len(rad), int(s_max),
+                                         float(tol), C.byref(opts), _ptr(q_inout), _ptr(T), C.byref(st)))
+        return T, q_inout, st.as_dict()
 
     def trace_inv_grad(self, op: Operator, dims, s_max: int, tol: float, opts: SolverOpts, grad_out):
         """Returns (T, dT/dm, stats); dT/dmu(x) is written into ``grad_out`` (host float64 array or

@@ -136,3 +136,90 @@ def batch_config(seed: int = 3000, lattices=BATCH_LATTICES) -> list[dict]:
         s = int(rng.choice([64, 128, 256, 512]))
         out.append({"dims": tuple(dims), "kappa": kappa, "eps": eps, "s": s, "link_seed": 1100 + i})
     return out
+
+
+# ------------------------------------------------------------ general sparse matrices
+# Stand-ins for the general sparse matrices of Section 2.1 (the paper fixes none): a
+# periodic grid whose rows are renumbered by a seeded permutation (so the natural order
+# carries no lattice structure), and random graphs.  CSR arrays: row_ptr int32[n+1],
+# col_idx int32[nnz] (sorted within each row, duplicates merged), values float64[nnz].
+
+def csr_from_entries(n: int, rows, cols, vals=None):
+    """CSR of the entries (rows, cols, vals); repeated (row, col) pairs are merged (values summed)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    key = rows * n + cols
+    uniq, inv = np.unique(key, return_inverse=True)
+    r = (uniq // n).astype(np.int64)
+    c = (uniq % n).astype(np.int32)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(row_ptr, r + 1, 1)
+    row_ptr = np.cumsum(row_ptr).astype(np.int32)
+    if vals is None:
+        return row_ptr, c
+    v = np.zeros(len(uniq), dtype=np.float64)
+    np.add.at(v, inv, np.asarray(vals, dtype=np.float64))
+    return row_ptr, c, v
+
+
+def _weighted_laplacian(n: int, ei, ej, w, shift: float):
+    """A = D - W + shift I for the undirected weighted edges (ei, ej, w): symmetric positive definite."""
+    rows = np.concatenate([ei, ej, np.arange(n), ei, ej])
+    cols = np.concatenate([ej, ei, np.arange(n), ei, ej])
+    vals = np.concatenate([-w, -w, np.full(n, shift), w, w])
+    return csr_from_entries(n, rows, cols, vals)
+
+
+def grid_matrix(dims: Sequence[int], seed: int, shift: float = 0.1, renumber: bool = True):
+    """Weighted graph Laplacian plus shift of the periodic grid dims (nearest neighbours), edge
+    weights U[0.5, 1.5] and the row renumbering permutation from PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = volume(dims)
+    idx = np.arange(n)
+    coords = []
+    r = idx.copy()
+    for L in dims:
+        coords.append(r % L)
+        r //= L
+    ei, ej = [], []
+    stride = 1
+    for j, L in enumerate(dims):
+        if L > 1:
+            fw = idx + np.where(coords[j] == L - 1, -(L - 1) * stride, stride)
+            ei.append(idx)
+            ej.append(fw)
+        stride *= L
+    ei = np.concatenate(ei)
+    ej = np.concatenate(ej)
+    keep = ei != ej
+    ei, ej = ei[keep], ej[keep]
+    w = rng.uniform(0.5, 1.5, len(ei))
+    if renumber:
+        perm = rng.permutation(n)
+        ei, ej = perm[ei], perm[ej]
+    return _weighted_laplacian(n, ei, ej, w, shift)
+
+
+def random_graph_matrix(n: int, degree: int, seed: int, shift: float = 0.1):
+    """Weighted graph Laplacian plus shift of a random graph: every row draws `degree` partners
+    uniformly (self pairs dropped), weights U[0.5, 1.5], all from PCG64(seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ei = np.repeat(np.arange(n), degree)
+    ej = rng.integers(0, n, n * degree)
+    keep = ei != ej
+    ei, ej = ei[keep], ej[keep]
+    w = rng.uniform(0.5, 1.5, len(ei))
+    return _weighted_laplacian(n, ei, ej, w, shift)
+
+
+def random_pattern(n: int, degree: int, seed: int, symmetric: bool = True, diagonal: bool = True):
+    """A sparsity pattern only: `degree` uniform partners per row from PCG64(seed), mirrored when
+    symmetric, the diagonal stored when asked."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ei = np.repeat(np.arange(n), degree)
+    ej = rng.integers(0, n, n * degree)
+    if symmetric:
+        ei, ej = np.concatenate([ei, ej]), np.concatenate([ej, ei])
+    if diagonal:
+        ei, ej = np.concatenate([ei, np.arange(n)]), np.concatenate([ej, np.arange(n)])
+    return csr_from_entries(n, ei, ej)
