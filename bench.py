@@ -36,6 +36,7 @@ METRIC = "probing solves/s (32^3x64 Wilson, mixed precision, true residual 1e-10
 UNIT = "solves/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 HBM_FALLBACK = 6800.0
+FP64_TFLOPS = 1.25   # nominal dense FP64 rate of a GB300
 # mean iterations per solve of this workload with the oracle's algorithm (unpreconditioned BiCGStab
 # in FP64), measured with the library's FP64 solver on a GB300 (12 right-hand sides, 44.75)
 FP64_ITERS_PER_SOLVE = 44.75
@@ -624,18 +625,28 @@ SPARSE_SEED = 4242
 
 
 def sparse_kernel_bytes(name, n, nnz, c):
-    """Algorithmic DRAM bytes of a sparse-CG kernel over the run: the CSR matrix (12 B per entry,
-    4 B per row pointer) once per launch, every vector of a right-hand-side iteration read or
-    written once (8 B per row).  c: rhs_iters, exact (true residuals), launches."""
+    """Algorithmic DRAM bytes of a sparse-CG kernel over the run: the CSR matrix (12 B per entry
+    in FP64, 8 B in FP32, 4 B per row pointer) once per launch, every vector of a
+    right-hand-side iteration read or written once (8 B per row in FP64, 4 B in FP32).
+    c: rhs_iters, exact (true residuals), launches."""
+    if name.startswith("k_bcm_"):             # FP32 iteration, FP64 reliable updates
+        mat32 = 8 * nnz + 4 * (n + 1)
+        return {"k_bcm_ap": mat32 * c["launches"] + 8 * n * c["rhs_iters"],
+                "k_bcm_xr": 24 * n * c["rhs_iters"],
+                "k_bcm_p": 12 * n * c["rhs_iters"],
+                "k_bcm_fold": 24 * n * c["exact"]}.get(name)
     mat = 12 * nnz + 4 * (n + 1)
+    if name == "k_btrue_slot":               # r = b - A x, one pass over the matrix per slot
+        return (mat + 16 * n) * c["exact"]
+    name = name.replace("k_bcg_", "k_cg_")   # the blocked engine's kernels do the same work
     if name == "k_cg_ap":        # q = A p, (p, q)
         return mat * c["launches"] + 16 * n * c["rhs_iters"]
     if name == "k_cg_xr":        # x += a p, r -= a q, (r, r)
         return 48 * n * c["rhs_iters"]
     if name == "k_cg_p":         # p = r + b p
         return 24 * n * c["rhs_iters"]
-    if name == "k_cg_true":      # r = b - A x
-        return mat * c["launches"] + 16 * n * c["exact"]
+    if name == "k_cg_true":      # r = b - A x (launches without a slot to update leave at once)
+        return (mat + 16 * n) * c["exact"]
     return None
 
 
@@ -668,7 +679,8 @@ def run_sparse(args):
         if ev:
             ev[1].record(stream)
         T, _, st = ctx.trace_inv_sparse(rp_, ci_, val_, paths, rad, S, TOL,
-                                        ctx.make_opts("fp64", z0_seed=seed, rhs_block=args.sparse_rhs_block))
+                                        ctx.make_opts(args.sparse_precision, z0_seed=seed,
+                                                      rhs_block=args.sparse_rhs_block))
         return T, st, rad
 
     for w in range(args.warmup):
@@ -726,11 +738,22 @@ def run_sparse(args):
         k_["share"] = k_["ms"] / tot_ms
     top_name, top_rec = max(kernels.items(), key=lambda kv: kv[1]["ms"])
     top_bytes = sparse_kernel_bytes(top_name, n, nnz, dict(counts, launches=top_rec["launches"]))
-    achieved = top_bytes / (top_rec["ms"] / 1e3) / 1e9 if top_bytes else None
-    roofline = {"kernel": top_name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": (top_bytes / top_rec["launches"]) if top_bytes else None,
-                "mean_launch_ms": top_rec["ms"] / top_rec["launches"], "traffic": None}
+    if top_name == "k_bcg_ap":
+        # FP64 multiply-adds bound this kernel on GB300 (2 flops per entry and right-hand side
+        # against the nominal 1.25 TFLOP/s FP64 rate; ncu: FP64 pipe 75% busy, DRAM 16%)
+        flops = 2.0 * nnz * iters
+        achieved = flops / (top_rec["ms"] / 1e3) / 1e12
+        roofline = {"kernel": top_name, "bound": "alu", "achieved": achieved, "peak": FP64_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_TFLOPS, "peak_source": "nominal FP64 rate",
+                    "flops_per_launch": flops / top_rec["launches"],
+                    "hbm_frac_of_%s" % peak_kind: top_bytes / (top_rec["ms"] / 1e3) / 1e9 / peak,
+                    "mean_launch_ms": top_rec["ms"] / top_rec["launches"], "traffic": None}
+    else:
+        achieved = top_bytes / (top_rec["ms"] / 1e3) / 1e9 if top_bytes else None
+        roofline = {"kernel": top_name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": (achieved / peak) if achieved else None, "peak_source": peak_kind,
+                    "algorithmic_bytes_per_launch": (top_bytes / top_rec["launches"]) if top_bytes else None,
+                    "mean_launch_ms": top_rec["ms"] / top_rec["launches"], "traffic": None}
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -760,14 +783,18 @@ def run_sparse(args):
     out = {"metric": "probing solves/s, Algorithm 1 + CG trace on a general sparse matrix (n = 262144, CG 1e-10)",
            "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64", "data": "synthetic (weighted graph Laplacian + 0.1 I of a renumbered periodic grid)",
+           "dtype": "f64" if args.sparse_precision == "fp64" else "f32 iteration + f64 reliable updates",
+           "data": "synthetic (weighted graph Laplacian + 0.1 I of a renumbered periodic grid)",
            "config": {"workload": "renumbered 64^3 periodic grid Laplacian + 0.1 I, %d entries, hierarchical "
-                                  "colouring + %d probing vectors, FP64 CG 1e-10" % (nnz, S),
+                                  "colouring + %d probing vectors, CG (%s iteration) to a true residual "
+                                  "of 1e-10" % (nnz, S, args.sparse_precision),
                       "n": n, "nnz": nnz, "vectors": S, "rhs_block": args.sparse_rhs_block,
-                      "radices": rad, "l2": "vectors of all slots together exceed L2 (128 x 2 MB per vector)"},
+                      "precision": args.sparse_precision,
+                      "radices": rad, "l2": "the iteration vectors of one block exceed L2 (4 x %d MB)" % (n * args.sparse_rhs_block * 4 >> 20)},
            "clocks": clk, "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
            "colouring_ms": colour_ms,
            "solver": {"rhs": solves, "iters_per_solve": iters / max(1, solves),
+                      "reliable_updates_per_solve": exact / max(1, solves),
                       "max_true_residual": max(s["max_true_residual"] for s in stats)},
            "estimate": {"T_S": float(runs[-1][0][-1].real)}, "kernels": kernels}
     print(json.dumps(out), flush=True)
@@ -787,7 +814,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="headline", choices=["headline", "batch", "grad", "variance", "sparse"])
     ap.add_argument("--sparse-vectors", type=int, default=128)
-    ap.add_argument("--sparse-rhs-block", type=int, default=128)
+    ap.add_argument("--sparse-rhs-block", type=int, default=64)
+    ap.add_argument("--sparse-precision", default="fp32", choices=["fp64", "fp32"])
     ap.add_argument("--variance-vectors", type=int, default=512)
     ap.add_argument("--even-odd", type=int, default=1, help="1: iterate on the odd-site Schur complement")
     ap.add_argument("--grad-probes", type=int, default=128)

@@ -302,10 +302,15 @@ hp_status hp_sparse_probe_vectors(hp_ctx* ctx, int32_t n, const int32_t* paths, 
  * (row_ptr, col_idx as hp_sparse_coloring; values double[row_ptr[n]]; host or
  * device): the probes are hp_sparse_probe_vectors' (opts->probe_kind 0) or the
  * natural-order Hadamard / Z_2 sequences (1, 2; paths unused), each solved by
- * FP64 CG to a true relative residual tol (complex probes as two real solves).
- * q_inout, trace_prefix, stats as hp_trace_inv.  Errors: as hp_trace_inv and
- * hp_sparse_probe_vectors, plus HP_EUNSUPPORTED for a precision other than FP64.
- * A matrix that is not symmetric positive definite ends in HP_ENOCONV. */
+ * CG to a true relative residual tol computed in FP64 (complex probes as two
+ * real solves).  The right-hand sides run in blocks of B = 32, 64 or 128
+ * (opts->rhs_block rounded up; 0: 64) with the vectors stored [row][B].
+ * opts->precision: HP_PREC_FP64, or HP_PREC_MIXED_FP32 = FP32 iteration with
+ * FP64 reliable updates (a true residual whenever ||r|| fell by opts->delta,
+ * default 1e-3, since the last one).  q_inout, trace_prefix, stats as
+ * hp_trace_inv.  Errors: as hp_trace_inv and hp_sparse_probe_vectors, plus
+ * HP_EUNSUPPORTED for FP16 / BF16.  A matrix that is not symmetric positive
+ * definite ends in HP_ENOCONV. */
 hp_status hp_trace_inv_sparse(hp_ctx* ctx, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
                               const double* values, const int32_t* paths, const int32_t* radices, int32_t n_levels,
                               int64_t s_max, double tol, const hp_solver_opts* opts, double* q_inout,

@@ -338,8 +338,8 @@ extern "C" hp_status hp_trace_inv_sparse(hp_ctx* ctx, int32_t n, const int32_t* 
     return HP_EINVAL;
   }
   HP_TRY(check_solver_args(s_max, tol, opts, n, n));
-  if (opts->precision != HP_PREC_FP64) {
-    hp_set_error("the sparse CG runs in FP64 only (precision %d)", opts->precision);
+  if (opts->precision != HP_PREC_FP64 && opts->precision != HP_PREC_MIXED_FP32) {
+    hp_set_error("the sparse CG iterates in FP64 or FP32 (precision %d)", opts->precision);
     return HP_EUNSUPPORTED;
   }
   if (opts->dilution != 0 && opts->dilution != 1) {

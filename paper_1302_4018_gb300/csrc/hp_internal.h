@@ -68,7 +68,8 @@ struct LatGeom {
   const double* csr_val;
   const int* paths;
   int nlev;
-  int radix[HP_MAX_LEVELS];
+  const int* radix;       // [nlev] colour counts c(l) in device memory (an array here would be
+                          // indexed dynamically and move the whole struct to local memory)
   double quad_tol;        // Laplacian CG: > 0 stops on the quadrature bracket (Gauss / Gauss-Radau)
   double quad_mu;         // the Gauss-Radau node, 0 < quad_mu <= lambda_min(A)
   const uint32_t* loc;    // [V] hierarchical position of each site

@@ -660,8 +660,10 @@ hp_status hp_sparse_geom(hp_ctx* ctx, int32_t n, const int32_t* row_ptr, const i
       }
     }
     g->nlev = k;
-    for (int l = 0; l < k; ++l) g->radix[l] = radices[l];
     const void* p = nullptr;
+    HP_TRY(hp_ws(ctx, "sp.radix", sizeof(int) * HP_MAX_LEVELS, (void**)&p));
+    if (k) HP_CUDA(cudaMemcpyAsync((void*)p, radices, sizeof(int) * k, cudaMemcpyHostToDevice, ctx->stream));
+    g->radix = (const int*)p;
     if (k) {
       HP_TRY(hp_device_view(ctx, paths, sizeof(int32_t) * (size_t)n * k, "sp.in.paths", &p));
     } else {   // one vector (z_0 itself): the digit loop reads no path, but the pointer marks the kind

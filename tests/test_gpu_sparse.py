@@ -167,6 +167,25 @@ def test_sparse_trace_parity(ctx, hp, name, s_max, z0):
     assert st["rhs_solved"] >= s_max
 
 
+@pytest.mark.parametrize("prec,rhs_block", [("fp64", 64), ("fp64", 128), ("fp32", 0), ("fp32", 64), ("fp32", 128)])
+def test_sparse_trace_blocks_and_mixed_precision(ctx, prec, rhs_block):
+    """Every block size of the blocked CG, in FP64 and with FP32 iteration + FP64 reliable
+    updates: the certified true residual gives the same quadratures."""
+    rp, ci, val = _spd("random400")
+    n = len(rp) - 1
+    paths, rad = ctx.sparse_coloring(rp, ci, 32)
+    s_max = 96
+    q = np.zeros(s_max, dtype=np.complex128)
+    T, q, st = ctx.trace_inv_sparse(rp, ci, val, np.ascontiguousarray(paths), rad, s_max, 1e-12,
+                                    ctx.make_opts(prec, z0_seed=5, rhs_block=rhs_block), q_inout=q)
+    A = sp.csr_matrix((val, ci, rp), shape=(n, n))
+    qo = S.sparse_quadratures(A, np.ascontiguousarray(paths.T), 0, s_max, 5)
+    assert np.abs(q - qo).max() <= 1e-9 * np.abs(qo).max()
+    assert st["max_true_residual"] <= 1e-12
+    if prec == "fp32":
+        assert st["reliable_updates"] >= st["rhs_solved"]   # at least the final FP64 check per solve
+
+
 def test_sparse_trace_device_inputs_and_restart(ctx):
     """Device CSR and paths; first > 0 continues from earlier quadratures."""
     rp, ci, val = _spd("random400")
