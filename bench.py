@@ -71,7 +71,7 @@ def source_hash(kernel):
 # same kernel on 32^3x16 with 12 slots (411.8 MB read + 146.2 MB written): the spinor part scaled
 # by the site-RHS ratio (8x), the links (read once per launch) by the site ratio (4x); valid only
 # for the kernel source it was taken on
-NCU_TRAFFIC = {("k_eo_even", "8a6ecae2d29e"): {"bytes_all_slots": 4.162e9, "alg_bytes_all_slots": 1048576 * 104 * 24 + 4 * 2097152 * 36}}
+NCU_TRAFFIC = {("k_eo_even", "22bb82742bef"): {"bytes_all_slots": 4.162e9, "alg_bytes_all_slots": 1048576 * 104 * 24 + 4 * 2097152 * 36}}
 
 
 class Clocks:

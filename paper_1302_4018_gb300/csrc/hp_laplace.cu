@@ -516,6 +516,11 @@ __device__ __forceinline__ void bk_finish(const BArgs& a, const LatGeom& g, int 
 }
 
 #define BK_ROWS(i) for (int i = blockIdx.x * (BT / 32) + (threadIdx.x >> 5); i < g.V; i += gridDim.x * (BT / 32))
+// rows i0 + u tw, u < BR, per warp and step: a streaming kernel issues all their loads first
+constexpr int BR = 4;
+#define BK_ROW_BATCHES(i0, tw)                            \
+  const int tw = gridDim.x * (BT / 32);                   \
+  for (int i0 = blockIdx.x * (BT / 32) + (threadIdx.x >> 5); i0 < g.V; i0 += BR * tw)
 
 // x = 0, r = p = b for the slots being filled; ||b||^2
 template <int SPL>
@@ -555,11 +560,11 @@ __global__ void __launch_bounds__(BT) k_bcg_init(BArgs a) {
 // the next 32 are requested before the current ones are used), broadcasts each entry, and
 // issues U gathers of B contiguous values before it adds them.  Each warp walks a long chain of
 // dependent loads, so every load that can be issued early is.
-template <int SPL, typename T, class Flush>
+template <int SPL, typename T, int U = 8, class Flush>
 __device__ __forceinline__ void bk_spmv_rows(const LatGeom& g, const T* __restrict__ val, const T* __restrict__ v,
                                              const T* __restrict__ own_src, int r0, int r1, int lane,
                                              const bool (&on)[SPL], Flush&& flush) {
-  constexpr int B = 32 * SPL, U = 8;
+  constexpr int B = 32 * SPL;
   constexpr unsigned FULL = 0xffffffffu;
   if (r0 >= r1) return;
   int i = r0, rbase = r0;
@@ -669,17 +674,32 @@ __global__ void __launch_bounds__(BT) k_bcg_xr(BArgs a) {
   double* __restrict__ r = a.r;
   const double* __restrict__ p = a.p;
   const double* __restrict__ q = a.q;
-#pragma unroll 4
-  BK_ROWS(i) {
+  BK_ROW_BATCHES(i0, tw) {   // loads of BR rows first, then the updates: BR x 4 SPL loads in flight
+    double xv[BR][SPL], pv[BR][SPL], qv[BR][SPL], rv[BR][SPL];
 #pragma unroll
-    for (int k = 0; k < SPL; ++k) {
-      if (!on[k]) continue;
-      const size_t o = (size_t)i * B + lane + 32 * k;
-      x[o] += al[k] * p[o];
-      const double rv = r[o] - al[k] * q[o];
-      r[o] = rv;
-      acc[k] += rv * rv;
-    }
+    for (int u = 0; u < BR; ++u)
+#pragma unroll
+      for (int k = 0; k < SPL; ++k) {
+        const int i = i0 + u * tw;
+        if (i >= g.V || !on[k]) continue;
+        const size_t o = (size_t)i * B + lane + 32 * k;
+        xv[u][k] = x[o];
+        pv[u][k] = p[o];
+        qv[u][k] = q[o];
+        rv[u][k] = r[o];
+      }
+#pragma unroll
+    for (int u = 0; u < BR; ++u)
+#pragma unroll
+      for (int k = 0; k < SPL; ++k) {
+        const int i = i0 + u * tw;
+        if (i >= g.V || !on[k]) continue;
+        const size_t o = (size_t)i * B + lane + 32 * k;
+        x[o] = xv[u][k] + al[k] * pv[u][k];
+        const double rn = rv[u][k] - al[k] * qv[u][k];
+        r[o] = rn;
+        acc[k] += rn * rn;
+      }
   }
   bk_finish<SPL>(a, g, BK_XR, acc);
 }
@@ -700,14 +720,26 @@ __global__ void __launch_bounds__(BT) k_bcg_p(BArgs a) {
   }
   double* __restrict__ p = a.p;
   const double* __restrict__ r = a.r;
-#pragma unroll 4
-  BK_ROWS(i) {
+  BK_ROW_BATCHES(i0, tw) {
+    double pv[BR][SPL], rv[BR][SPL];
 #pragma unroll
-    for (int k = 0; k < SPL; ++k) {
-      if (!on[k]) continue;
-      const size_t o = (size_t)i * B + lane + 32 * k;
-      p[o] = r[o] + be[k] * p[o];
-    }
+    for (int u = 0; u < BR; ++u)
+#pragma unroll
+      for (int k = 0; k < SPL; ++k) {
+        const int i = i0 + u * tw;
+        if (i >= g.V || !on[k]) continue;
+        const size_t o = (size_t)i * B + lane + 32 * k;
+        pv[u][k] = p[o];
+        rv[u][k] = r[o];
+      }
+#pragma unroll
+    for (int u = 0; u < BR; ++u)
+#pragma unroll
+      for (int k = 0; k < SPL; ++k) {
+        const int i = i0 + u * tw;
+        if (i >= g.V || !on[k]) continue;
+        p[(size_t)i * B + lane + 32 * k] = rv[u][k] + be[k] * pv[u][k];
+      }
   }
 }
 
@@ -776,7 +808,7 @@ __global__ void __launch_bounds__(BT) k_bcm_init(BArgs a) {
 
 // q = A p, (p, q) in FP32
 template <int SPL>
-__global__ void __launch_bounds__(BT, SPL == 1 ? 4 : (SPL == 2 ? 3 : 2)) k_bcm_ap(BArgs a) {
+__global__ void __launch_bounds__(BT, SPL <= 2 ? 4 : 2) k_bcm_ap(BArgs a) {
   constexpr int B = 32 * SPL;
   const LatGeom g = *a.lat;
   const int lane = threadIdx.x & 31;
@@ -789,7 +821,7 @@ __global__ void __launch_bounds__(BT, SPL == 1 ? 4 : (SPL == 2 ? 3 : 2)) k_bcm_a
   }
   int r0, r1;
   bk_warp_rows(g.V, r0, r1);
-  bk_spmv_rows<SPL, float>(g, a.val32, a.pf, a.pf, r0, r1, lane, on,
+  bk_spmv_rows<SPL, float, 16>(g, a.val32, a.pf, a.pf, r0, r1, lane, on,
                            [&](int i, const float (&qv)[SPL], const float (&pv)[SPL]) {
 #pragma unroll
                              for (int k = 0; k < SPL; ++k) {
@@ -823,17 +855,32 @@ __global__ void __launch_bounds__(BT) k_bcm_xr(BArgs a) {
   float* __restrict__ rf = a.rf;
   const float* __restrict__ pf = a.pf;
   const float* __restrict__ qf = a.qf;
-#pragma unroll 4
-  BK_ROWS(i) {
+  BK_ROW_BATCHES(i0, tw) {
+    float xv[BR][SPL], pv[BR][SPL], qv[BR][SPL], rv[BR][SPL];
 #pragma unroll
-    for (int k = 0; k < SPL; ++k) {
-      if (!on[k]) continue;
-      const size_t o = (size_t)i * B + lane + 32 * k;
-      xl[o] = fmaf(al[k], pf[o], xl[o]);
-      const float rv = fmaf(-al[k], qf[o], rf[o]);
-      rf[o] = rv;
-      accf[k] = fmaf(rv, rv, accf[k]);
-    }
+    for (int u = 0; u < BR; ++u)
+#pragma unroll
+      for (int k = 0; k < SPL; ++k) {
+        const int i = i0 + u * tw;
+        if (i >= g.V || !on[k]) continue;
+        const size_t o = (size_t)i * B + lane + 32 * k;
+        xv[u][k] = xl[o];
+        pv[u][k] = pf[o];
+        qv[u][k] = qf[o];
+        rv[u][k] = rf[o];
+      }
+#pragma unroll
+    for (int u = 0; u < BR; ++u)
+#pragma unroll
+      for (int k = 0; k < SPL; ++k) {
+        const int i = i0 + u * tw;
+        if (i >= g.V || !on[k]) continue;
+        const size_t o = (size_t)i * B + lane + 32 * k;
+        xl[o] = fmaf(al[k], pv[u][k], xv[u][k]);
+        const float rn = fmaf(-al[k], qv[u][k], rv[u][k]);
+        rf[o] = rn;
+        accf[k] = fmaf(rn, rn, accf[k]);
+      }
   }
   double acc[SPL];
 #pragma unroll
@@ -882,14 +929,26 @@ __global__ void __launch_bounds__(BT) k_bcm_p(BArgs a) {
   }
   float* __restrict__ pf = a.pf;
   const float* __restrict__ rf = a.rf;
-#pragma unroll 4
-  BK_ROWS(i) {
+  BK_ROW_BATCHES(i0, tw) {
+    float pv[BR][SPL], rv[BR][SPL];
 #pragma unroll
-    for (int k = 0; k < SPL; ++k) {
-      if (!on[k]) continue;
-      const size_t o = (size_t)i * B + lane + 32 * k;
-      pf[o] = fmaf(be[k], pf[o], rf[o]);
-    }
+    for (int u = 0; u < BR; ++u)
+#pragma unroll
+      for (int k = 0; k < SPL; ++k) {
+        const int i = i0 + u * tw;
+        if (i >= g.V || !on[k]) continue;
+        const size_t o = (size_t)i * B + lane + 32 * k;
+        pv[u][k] = pf[o];
+        rv[u][k] = rf[o];
+      }
+#pragma unroll
+    for (int u = 0; u < BR; ++u)
+#pragma unroll
+      for (int k = 0; k < SPL; ++k) {
+        const int i = i0 + u * tw;
+        if (i >= g.V || !on[k]) continue;
+        pf[(size_t)i * B + lane + 32 * k] = fmaf(be[k], pv[u][k], rv[u][k]);
+      }
   }
 }
 
