@@ -213,11 +213,13 @@ def random_graph_matrix(n: int, degree: int, seed: int, shift: float = 0.1):
 
 
 def random_pattern(n: int, degree: int, seed: int, symmetric: bool = True, diagonal: bool = True):
-    """A sparsity pattern only: `degree` uniform partners per row from PCG64(seed), mirrored when
-    symmetric, the diagonal stored when asked."""
+    """A sparsity pattern only: `degree` uniform partners per row from PCG64(seed) (self pairs
+    dropped), mirrored when symmetric, the diagonal stored when asked."""
     rng = np.random.Generator(np.random.PCG64(seed))
     ei = np.repeat(np.arange(n), degree)
     ej = rng.integers(0, n, n * degree)
+    keep = ei != ej
+    ei, ej = ei[keep], ej[keep]
     if symmetric:
         ei, ej = np.concatenate([ei, ej]), np.concatenate([ej, ei])
     if diagonal:

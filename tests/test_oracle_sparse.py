@@ -105,3 +105,50 @@ def test_full_basis_is_exact_when_paths_are_unique():
     s = int(np.prod(SP.radices(paths)))
     q = SP.sparse_quadratures(A, paths, 0, s, z0_seed=7)
     assert abs(q.sum().real / s - np.trace(np.linalg.inv(A.toarray()))) <= 1e-12 * np.trace(np.linalg.inv(A.toarray()))
+
+
+# ------------------------------------------------------------ the seeded sparse inputs
+def test_csr_from_entries_merges_and_sorts():
+    from paper_1302_4018_gb300 import synth
+
+    rp, ci, v = synth.csr_from_entries(4, [2, 0, 2, 0, 3], [1, 3, 1, 0, 3], [1.0, 2.0, 3.0, 4.0, 5.0])
+    A = sp.csr_matrix((v, ci, rp), shape=(4, 4)).toarray()
+    expect = np.zeros((4, 4))
+    expect[2, 1], expect[0, 3], expect[0, 0], expect[3, 3] = 4.0, 2.0, 4.0, 5.0
+    assert np.array_equal(A, expect)
+    assert rp.dtype == np.int32 and ci.dtype == np.int32
+    for i in range(4):   # column indices sorted within each row
+        assert np.all(np.diff(ci[rp[i]:rp[i + 1]]) > 0)
+
+
+@pytest.mark.parametrize("dims", [(7,), (4, 6), (3, 4, 5), (2, 3)])
+def test_grid_matrix_is_a_renumbered_weighted_laplacian(dims):
+    """Symmetric, row sums = shift, off-diagonal weights in [0.5, 1.5] (per distinct neighbour),
+    and the renumbered matrix is a symmetric permutation of the unrenumbered one's pattern."""
+    from paper_1302_4018_gb300 import synth
+
+    n = int(np.prod(dims))
+    rp, ci, v = synth.grid_matrix(dims, 11, shift=0.25)
+    A = sp.csr_matrix((v, ci, rp), shape=(n, n)).toarray()
+    assert np.allclose(A, A.T, atol=0)
+    assert np.allclose(A.sum(axis=1), 0.25)
+    off = -(A - np.diag(np.diag(A)))
+    assert np.all(off[off != 0] >= 0.5 - 1e-12)
+    assert np.linalg.eigvalsh(A).min() > 0.25 - 1e-9   # Laplacian (PSD) + 0.25 I
+    rp0, ci0, v0 = synth.grid_matrix(dims, 11, shift=0.25, renumber=False)
+    deg = np.sort(np.diff(rp))
+    assert np.array_equal(deg, np.sort(np.diff(rp0)))
+
+
+def test_random_graph_matrix_is_spd_and_random_pattern_shapes():
+    from paper_1302_4018_gb300 import synth
+
+    rp, ci, v = synth.random_graph_matrix(120, 3, 5, shift=0.1)
+    A = sp.csr_matrix((v, ci, rp), shape=(120, 120)).toarray()
+    assert np.allclose(A, A.T) and np.linalg.eigvalsh(A).min() > 0.1 - 1e-9
+    rp, ci = synth.random_pattern(50, 2, 6, symmetric=False, diagonal=False)
+    P = sp.csr_matrix((np.ones(len(ci)), ci, rp), shape=(50, 50)).toarray()
+    assert not np.any(np.diag(P)) and not np.allclose(P, P.T)
+    rp, ci = synth.random_pattern(50, 2, 6, symmetric=True, diagonal=True)
+    P = sp.csr_matrix((np.ones(len(ci)), ci, rp), shape=(50, 50)).toarray()
+    assert np.all(np.diag(P)) and np.allclose(P, P.T)
