@@ -104,3 +104,27 @@ def test_noalloc_rejects_clover_without_gpu():
     assert st == hprobe.HP_EINVAL
     assert "csw" in lib.hp_last_error().decode()
 
+
+
+def test_sparse_entry_points_reject_a_missing_context_without_gpu():
+    """The general-sparse calls validate their context and arguments before any device work."""
+    from paper_1302_4018_gb300 import hprobe
+
+    lib = hprobe.lib()
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    ci = np.array([0, 1], dtype=np.int32)
+    paths = np.zeros(4, dtype=np.int32)
+    rad = np.array([1], dtype=np.int32)
+    nl = ctypes.c_int32()
+    assert lib.hp_sparse_coloring(None, 2, rp.ctypes.data, ci.ctypes.data, 2, paths.ctypes.data, rad.ctypes.data,
+                                  ctypes.byref(nl)) == hprobe.HP_EINVAL
+    per = ctypes.c_int32()
+    assert lib.hp_sparse_probe_vectors(None, 2, paths.ctypes.data, rad.ctypes.data, 1, 0, 1, 0, None,
+                                       ctypes.byref(per)) == hprobe.HP_EINVAL
+    opts = hprobe.Context.make_opts("fp64")
+    T = np.zeros(2, dtype=np.complex128)
+    vals = np.ones(2)
+    assert lib.hp_trace_inv_sparse(None, 2, rp.ctypes.data, ci.ctypes.data, vals.ctypes.data, paths.ctypes.data,
+                                   rad.ctypes.data, 1, 1, 1e-10, ctypes.byref(opts), None, T.ctypes.data,
+                                   None) == hprobe.HP_EINVAL
+    assert "context" in lib.hp_last_error().decode().lower()
