@@ -694,7 +694,7 @@ def run_sparse(args):
             ev[1].record(stream)
         T, _, st = ctx.trace_inv_sparse(rp_, ci_, val_, paths, rad, S, TOL,
                                         ctx.make_opts(args.sparse_precision, z0_seed=seed,
-                                                      rhs_block=args.sparse_rhs_block))
+                                                      rhs_block=args.sparse_rhs_block, delta=args.sparse_delta))
         return T, st, rad
 
     for w in range(args.warmup):
@@ -830,6 +830,8 @@ def main():
     ap.add_argument("--sparse-vectors", type=int, default=128)
     ap.add_argument("--sparse-rhs-block", type=int, default=64)
     ap.add_argument("--sparse-precision", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--sparse-delta", type=float, default=0.0,
+                    help="reliable-update threshold of the FP32 iteration (0: the library default 1e-3)")
     ap.add_argument("--variance-vectors", type=int, default=512)
     ap.add_argument("--even-odd", type=int, default=1, help="1: iterate on the odd-site Schur complement")
     ap.add_argument("--grad-probes", type=int, default=128)

@@ -307,7 +307,7 @@ hp_status hp_sparse_probe_vectors(hp_ctx* ctx, int32_t n, const int32_t* paths, 
  * (opts->rhs_block rounded up; 0: 64) with the vectors stored [row][B].
  * opts->precision: HP_PREC_FP64, or HP_PREC_MIXED_FP32 = FP32 iteration with
  * FP64 reliable updates (a true residual whenever ||r|| fell by opts->delta,
- * default 1e-3, since the last one).  q_inout, trace_prefix, stats as
+ * default 1e-5, since the last one).  q_inout, trace_prefix, stats as
  * hp_trace_inv.  Errors: as hp_trace_inv and hp_sparse_probe_vectors, plus
  * HP_EUNSUPPORTED for FP16 / BF16.  A matrix that is not symmetric positive
  * definite ends in HP_ENOCONV. */

@@ -1069,7 +1069,10 @@ struct BlockedSparseEngine {
         k_to_f32<<<blocks_for(ctx, nnz, 256), 256, 0, ctx->stream>>>(g.csr_val, nnz, (float*)p);
       }
       HP_LAUNCH_CHECK();
-      const double d = o.delta > 0.0 ? o.delta : 1e-3;
+      // default threshold: a true residual after every 10^5 reduction (measured on the renumbered
+      // 64^3 grid: 1e-3 -> 4.0 updates per solve, 1e-4 -> 3.0, 1e-5 -> 2.1 with the FP64 iteration
+      // count, 1e-6 -> 2.0 but 1.7% more iterations)
+      const double d = o.delta > 0.0 ? o.delta : 1e-5;
       a.delta2 = d * d;
     }
     a.tol2 = tol * tol;
