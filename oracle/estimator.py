@@ -107,6 +107,27 @@ def laplacian_quadratures(dims, mass, first, count, z0_seed, tol=1e-13, mass_fie
     return np.array([np.vdot(W[m], X[m]) for m in range(count)])
 
 
+def laplacian_deflated_quadratures(dims, mass, evecs, first, count, z0_seed, mass_field=None):
+    """Deflated probing (the variance reduction the conclusions pair with probing): with k
+    orthonormal real eigenvectors V (columns of evecs, n x k) of the real symmetric A and
+    P = I - V V^T, A^-1 = V diag(1/lambda) V^T + A^-1 P, so
+        Tr A^-1 = sum_j 1/lambda_j + Tr(A^-1 P),
+    and the probed part uses the projected vectors:  q_m = (P v_m)^H A^-1 (P v_m)  (dense solve)."""
+    W = probe_vectors(dims, first, count, z0_seed)
+    if np.all(W.imag == 0):
+        W = W.real
+    V = np.asarray(evecs, dtype=float)
+    Wp = W - (W @ V) @ V.T
+    A = ops.laplacian_dense(dims, mass, mass_field)
+    X = solvers.dense_solve(A, Wp.T).T
+    return np.array([np.vdot(Wp[m], X[m]) for m in range(count)])
+
+
+def deflated_trace_prefix(evals, q) -> np.ndarray:
+    """T_s = sum_j 1/lambda_j + (1/s) sum_{m<s} q_m."""
+    return float(np.sum(1.0 / np.asarray(evals, dtype=float))) + trace_prefix(q)
+
+
 def laplacian_grad_mass_field(dims, mass, s, z0_seed, tol=1e-13, mass_field=None, method="cg"):
     """dT_s/dmu(x); A is real symmetric (its stencil is symmetric), so A^-H v = A^-1 v = x."""
     W = probe_vectors(dims, 0, s, z0_seed)

@@ -208,3 +208,58 @@ def test_hierarchical_variance_at_completion_is_same_colour_sum():
         direct = 2 * np.sum(np.where(same & ~np.eye(V, dtype=bool), B ** 2, 0.0))
         assert abs(E.z0_variance(B, Z, s) - direct) <= 1e-12 * direct
     assert E.z0_variance(B, Z, 32) < 0.2 * E.z0_variance(B, Z, 2)
+
+
+# ------------------------------------------------------------------ deflated probing
+def _lowest_eigvecs(dims, mass, k):
+    A = O.laplacian_dense(dims, mass)
+    lam, V = np.linalg.eigh(A)
+    return lam[:k], V[:, :k]
+
+
+@pytest.mark.parametrize("k", [1, 5, 17])
+def test_deflated_full_sequence_is_exact(k):
+    """At s = N the nested vectors form an orthogonal basis (W^H W = N I), so the probed part is
+    Tr(P A^-1 P) = Tr(A^-1 P) and T_N = sum 1/lambda_j + Tr(A^-1 P) = Tr A^-1, the Fourier closed
+    form of the periodic Laplacian, for any number k of deflated eigenvectors."""
+    dims, mass = (4, 4, 2, 2), 0.3
+    N = 64
+    lam, V = _lowest_eigvecs(dims, mass, k)
+    q = E.laplacian_deflated_quadratures(dims, mass, V, 0, N, z0_seed=5)
+    T = E.deflated_trace_prefix(lam, q)
+    exact = laplacian_trace_inverse(dims, mass)
+    assert abs(T[-1] - exact) <= 1e-12 * exact
+    assert abs(T[-1].imag) <= 1e-12 * exact
+
+
+def test_deflating_every_eigenvector_leaves_nothing_to_probe():
+    """k = N: P = 0, every quadrature vanishes and T_s = Tr A^-1 for every s."""
+    dims, mass = (2, 2, 2, 4), 0.7
+    lam, V = _lowest_eigvecs(dims, mass, 32)
+    q = E.laplacian_deflated_quadratures(dims, mass, V, 0, 8, z0_seed=3)
+    assert np.abs(q).max() <= 1e-12
+    T = E.deflated_trace_prefix(lam, q)
+    assert np.allclose(T, laplacian_trace_inverse(dims, mass), rtol=1e-12, atol=0)
+
+
+def test_deflation_with_no_vectors_is_plain_probing():
+    dims, mass = (4, 4, 4, 2), 0.2
+    q0 = E.laplacian_quadratures(dims, mass, 0, 12, 9, method="dense")
+    q = E.laplacian_deflated_quadratures(dims, mass, np.zeros((128, 0)), 0, 12, z0_seed=9)
+    assert np.allclose(q, q0, rtol=1e-12, atol=0)
+
+
+def test_deflating_the_lowest_modes_reduces_the_z0_variance():
+    """The exact z_0-variance (1/s^2) sum_{i<j} |B_ij + B_ji|^2 C_ij^2 of the probed part falls
+    when B = A^-1 is replaced by A^-1 P with the 7 lowest modes removed (cond ~ 100 Laplacian)."""
+    from oracle import probing as Pr
+
+    dims, mass = (8, 8, 8), 12.0 / 99.0
+    A = O.laplacian_dense(dims, mass)
+    lam, V = np.linalg.eigh(A)
+    B = np.linalg.inv(A)
+    Bd = B - (V[:, :7] / lam[:7]) @ V[:, :7].T
+    ph, _ = Pr.probe_phases(dims, 0, 64, 0)
+    Z = 1 - 2 * ph
+    for s in (8, 16, 64):
+        assert E.z0_variance(Bd, Z, s) < 0.5 * E.z0_variance(B, Z, s)
