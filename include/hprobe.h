@@ -236,6 +236,26 @@ hp_status hp_trace_inv_bounds(hp_ctx* ctx, const hp_operator* op, const hp_latti
                               double quad_tol, double lambda_min, const hp_solver_opts* opts,
                               double* trace_prefix, double* T_lower, double* T_upper, hp_solve_stats* stats);
 
+/* Deflated hierarchical probing of the (real symmetric positive definite)
+ * Laplacian: the variance reduction that the paper's conclusions name as the
+ * next step after probing.  With k orthonormal real eigenvectors V of A
+ * (evecs: double[k][V] in the canonical site order, host or device) and their
+ * eigenvalues (evals: host double[k], all > 0), P = I - V V^T and
+ *   Tr A^-1 = sum_j 1/lambda_j + Tr(A^-1 P),
+ * the second term is estimated by probing with the projected vectors
+ * P v_m (v_m as in hp_trace_inv):
+ *   q_m = (P v_m)^H A^-1 (P v_m),  T_s = sum_j 1/lambda_j + (1/s) sum_{m<s} q_m.
+ * The identity needs V to span an invariant subspace (eigenvectors): other
+ * vectors give a biased estimate.  Removing the lowest modes removes the long-
+ * range part of A^-1 that the colouring cannot, so T_s converges faster.
+ * q_inout, trace_prefix, stats as hp_trace_inv; opts->first must be 0.
+ * Errors: HP_EINVAL for a Wilson operator, k outside [1, V], NULL arrays or an
+ * eigenvalue <= 0; as hp_trace_inv otherwise. */
+hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k,
+                                const double* evecs, const double* evals, int64_t s_max, double tol,
+                                const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
+                                hp_solve_stats* stats);
+
 /* hp_trace_inv plus the derivative of Re T_{s_max} with respect to the
  * per-site mass mu(s) (real):
  *   dT/dmu(s) = -(1/s_max) sum_{m,a} sum_c conj(y_{m,a}(s,c)) x_{m,a}(s,c),  y = A^-H v.

@@ -16,10 +16,14 @@ hp_status hp_bench_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int pre
                           double* bytes, double* flops);
 
 // q_m = sum_{a < dof} qj[m dof + a] (fixed order), then T_s = (1/s) sum_{m<s} q_m
-// sequentially in FP64; probes m < first take q from q_prev.
+// sequentially in FP64; probes m < first take q from q_prev.  Deflation adds the exact part
+// sum_j 1/lambda_j (nlam eigenvalues lam) to every T_s.
 __global__ void k_trace_prefix(const double2* __restrict__ qj, int dof, const double2* __restrict__ q_prev,
-                               int first, int s_max, double2* __restrict__ q_out, double2* __restrict__ T) {
+                               int first, int s_max, double2* __restrict__ q_out, double2* __restrict__ T,
+                               const double* __restrict__ lam, int nlam) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  double exact = 0.0;
+  for (int j = 0; j < nlam; ++j) exact += 1.0 / lam[j];
   double2 acc = make_double2(0.0, 0.0);
   for (int m = 0; m < s_max; ++m) {
     double2 q;
@@ -36,7 +40,7 @@ __global__ void k_trace_prefix(const double2* __restrict__ qj, int dof, const do
     q_out[m] = q;
     acc.x += q.x;
     acc.y += q.y;
-    T[m] = make_double2(acc.x / (m + 1), acc.y / (m + 1));
+    T[m] = make_double2(exact + acc.x / (m + 1), acc.y / (m + 1));
   }
 }
 
@@ -184,7 +188,8 @@ static hp_status run_solve(hp_ctx* ctx, SolveProblem& pb, SolveResult& res) {
 
 // q and prefix of one lattice on the device, copied to the caller's host arrays
 static hp_status finish_trace(hp_ctx* ctx, const SolveResult& res, int L, int dof, int64_t first, int64_t s_max,
-                              double* q_inout, double* trace_prefix) {
+                              double* q_inout, double* trace_prefix, const double* lam_dev = nullptr,
+                              int nlam = 0) {
   void* p = nullptr;
   const size_t nq = res.qj[L].size();
   HP_TRY(hp_ws(ctx, "trace.qj", sizeof(double2) * std::max<size_t>(nq, 1), &p));
@@ -200,7 +205,7 @@ static hp_status finish_trace(hp_ctx* ctx, const SolveResult& res, int L, int do
     HP_CUDA(cudaMemcpyAsync(qprev, q_inout, sizeof(double2) * (size_t)first, cudaMemcpyHostToDevice, ctx->stream));
   {
     ProfScope ps(ctx, "k_trace_prefix");
-    k_trace_prefix<<<1, 32, 0, ctx->stream>>>(qj, dof, qprev, (int)first, (int)s_max, qout, T);
+    k_trace_prefix<<<1, 32, 0, ctx->stream>>>(qj, dof, qprev, (int)first, (int)s_max, qout, T, lam_dev, nlam);
   }
   HP_LAUNCH_CHECK();
   if (q_inout)
@@ -217,9 +222,17 @@ struct BoundsReq {
   double *T_lower, *T_upper;
 };
 
+// deflated probing of the Laplacian (hp_trace_inv_deflated)
+struct DeflReq {
+  int32_t k;
+  const double* evecs;   // [k][V], host or device
+  const double* evals;   // [k], host
+};
+
 static hp_status trace_common(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t s_max, double tol,
                               const hp_solver_opts* opts, double* q_inout, double* trace_prefix, double* dT_dmu,
-                              double* dT_dm, hp_solve_stats* stats, const BoundsReq* bounds = nullptr) {
+                              double* dT_dm, hp_solve_stats* stats, const BoundsReq* bounds = nullptr,
+                              const DeflReq* defl = nullptr) {
   HP_TRY(check_ctx(ctx));
   LatGeom g;
   LatticeSetup* ls = nullptr;
@@ -244,6 +257,17 @@ static hp_status trace_common(hp_ctx* ctx, const hp_operator* op, const hp_latti
     return HP_EINVAL;
   }
   HP_TRY(prepare_operator(ctx, op, &g, opts->precision, "op0"));
+  const double* lam_dev = nullptr;
+  if (defl) {
+    const void* p = nullptr;
+    HP_TRY(hp_device_view(ctx, defl->evecs, sizeof(double) * (size_t)defl->k * g.V, "defl.V", &p));
+    g.defl_V = (const double*)p;
+    g.defl_k = defl->k;
+    void* l = nullptr;
+    HP_TRY(hp_ws(ctx, "defl.lam", sizeof(double) * (size_t)defl->k, &l));
+    HP_CUDA(cudaMemcpyAsync(l, defl->evals, sizeof(double) * (size_t)defl->k, cudaMemcpyHostToDevice, ctx->stream));
+    lam_dev = (const double*)l;
+  }
   if (bounds) {   // Gauss-Radau node: the caller's bound, else m + min mu(x) (the Laplacian part is PSD)
     double mu = bounds->lambda_min;
     if (!(mu > 0.0)) {
@@ -280,7 +304,8 @@ static hp_status trace_common(hp_ctx* ctx, const hp_operator* op, const hp_latti
   SolveResult res;
   HP_TRY(run_solve(ctx, pb, res));
   const int dof = op->kind == HP_OP_WILSON ? 12 : g.parts;
-  HP_TRY(finish_trace(ctx, res, 0, dof, opts->first, s_max, q_inout, trace_prefix));
+  HP_TRY(finish_trace(ctx, res, 0, dof, opts->first, s_max, q_inout, trace_prefix, lam_dev,
+                      defl ? defl->k : 0));
   if (bounds) {   // T_s bounds: (1/s) sum over probes and parts of the per-solve brackets
     double lo = 0.0, hi = 0.0;
     for (int64_t m = 0; m < s_max; ++m) {
@@ -326,6 +351,35 @@ extern "C" hp_status hp_trace_inv(hp_ctx* ctx, const hp_operator* op, const hp_l
                                   const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
                                   hp_solve_stats* stats) {
   return trace_common(ctx, op, lat, s_max, tol, opts, q_inout, trace_prefix, nullptr, nullptr, stats);
+}
+
+extern "C" hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k,
+                                           const double* evecs, const double* evals, int64_t s_max, double tol,
+                                           const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
+                                           hp_solve_stats* stats) {
+  if (!op || op->kind != HP_OP_LAPLACIAN) {
+    hp_set_error("deflated probing serves the (real symmetric) Laplacian");
+    return HP_EINVAL;
+  }
+  std::vector<int64_t> dims;
+  HP_TRY(hp_validate_lattice(lat, 4, &dims));
+  int64_t V = 1;
+  for (int64_t d : dims) V *= d;
+  if (k < 1 || k > V || !evecs || !evals) {
+    hp_set_error("deflation: 1 <= k <= V and non-NULL eigenvectors and eigenvalues required (k = %d)", k);
+    return HP_EINVAL;
+  }
+  for (int j = 0; j < k; ++j)
+    if (!(evals[j] > 0.0) || !std::isfinite(evals[j])) {
+      hp_set_error("deflation: eigenvalue %d is %g (the Laplacian is positive definite)", j, evals[j]);
+      return HP_EINVAL;
+    }
+  if (opts && opts->first != 0) {
+    hp_set_error("deflated probing needs first == 0");
+    return HP_EINVAL;
+  }
+  const DeflReq d{k, evecs, evals};
+  return trace_common(ctx, op, lat, s_max, tol, opts, q_inout, trace_prefix, nullptr, nullptr, stats, nullptr, &d);
 }
 
 extern "C" hp_status hp_trace_inv_sparse(hp_ctx* ctx, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,

@@ -70,6 +70,10 @@ struct LatGeom {
   int nlev;
   const int* radix;       // [nlev] colour counts c(l) in device memory (an array here would be
                           // indexed dynamically and move the whole struct to local memory)
+  // deflation (Laplacian): k orthonormal eigenvectors [k][V] in device memory; sources are
+  // projected, b -> b - V (V^T b)
+  const double* defl_V;
+  int defl_k;
   double quad_tol;        // Laplacian CG: > 0 stops on the quadrature bracket (Gauss / Gauss-Radau)
   double quad_mu;         // the Gauss-Radau node, 0 < quad_mu <= lambda_min(A)
   const uint32_t* loc;    // [V] hierarchical position of each site

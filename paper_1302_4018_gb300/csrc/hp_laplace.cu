@@ -81,6 +81,7 @@ struct LArgs {
   double tol2;
   int maxiter;
   int by_slot;   // 1: grid (tiles, slots), 0: grid (slots, tiles)
+  double* dc;    // deflation: V^T b of each slot's source, [slot][defl_k]
 };
 
 #define LSLOT(COND)                                                \
@@ -101,6 +102,40 @@ struct LArgs {
 __device__ __forceinline__ double lap_source(const LatGeom& g, int site, int m, int part) {
   double2 v = g.ptab[probe_phase(g, (uint32_t)site, (uint32_t)m)];
   return part == 0 ? v.x : v.y;
+}
+
+// the solved source: the probe, projected off the deflated eigenvectors when there are any
+__device__ __forceinline__ double lap_src(const LatGeom& g, const LArgs& a, int slot, int site, int m, int part) {
+  double b = lap_source(g, site, m, part);
+  if (g.defl_k) {
+    const double* c = a.dc + (size_t)slot * g.defl_k;
+    for (int j = 0; j < g.defl_k; ++j) b -= c[j] * g.defl_V[(size_t)j * g.V + site];
+  }
+  return b;
+}
+
+// deflation coefficients c_j = V_j^T b of the slots being filled: block (j, slot), one sum over
+// the lattice in a fixed order
+template <int NT>
+__global__ void __launch_bounds__(NT) k_cg_defl(LArgs a) {
+  const int j = blockIdx.x, slot = blockIdx.y;
+  const SlotState* S = a.st + slot;
+  if (S->status != SLOT_INIT) return;
+  const LatGeom g = a.lats[S->lat];
+  if (j >= g.defl_k) return;
+  double acc[1] = {0.0};
+  const double* vj = g.defl_V + (size_t)j * g.V;
+  for (int site = threadIdx.x; site < g.V; site += NT) acc[0] += vj[site] * lap_source(g, site, S->m, S->a);
+  __shared__ double sh[NT / 32];
+  double t = acc[0];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < NT / 32; ++w) tot += sh[w];
+    a.dc[(size_t)slot * g.defl_k + j] = tot;
+  }
 }
 
 template <int NQ, int NT>
@@ -206,7 +241,7 @@ __global__ void __launch_bounds__(NT) k_cg_init(LArgs a) {
   for (int tile = bx; tile < ntiles; tile += gx) {
     const int site = tile * NT + threadIdx.x;
     if (site >= g.V) continue;
-    double b = lap_source(g, site, m, pa);
+    double b = lap_src(g, a, slot, site, m, pa);
     a.x[off + site] = 0.0;
     a.r[off + site] = b;
     a.p[off + site] = b;
@@ -280,7 +315,7 @@ __global__ void __launch_bounds__(NT) k_cg_true(LArgs a) {
   for (int tile = bx; tile < ntiles; tile += gx) {
     const int site = tile * NT + threadIdx.x;
     if (site >= g.V) continue;
-    double rv = lap_source(g, site, m, pa) - lap_site(g, a.x + off, site);
+    double rv = lap_src(g, a, slot, site, m, pa) - lap_site(g, a.x + off, site);
     a.r[off + site] = rv;
     acc[0] += rv * rv;
   }
@@ -314,7 +349,7 @@ __global__ void __launch_bounds__(NT) k_lquad(LArgs a) {
   for (int tile = bx; tile < ntiles; tile += gx) {
     const int site = tile * NT + threadIdx.x;
     if (site >= g.V) continue;
-    acc[0] += lap_source(g, site, m, pa) * a.x[off + site];
+    acc[0] += lap_src(g, a, slot, site, m, pa) * a.x[off + site];
   }
   lreduce<1, NT>(acc, part, a.gy, bx);
   if (last_block(a.cnt + slot, nparts)) {
@@ -348,6 +383,7 @@ struct LaplaceEngine {
   hp_ctx* ctx;
   LArgs a;
   int nslots, gy;
+  int defl_k = 0;
   // A sparse matrix runs with slots along y: the blocks of one slot are scheduled together,
   // so the vector its rows gather from stays in L2 while the slot runs (slots along x would
   // interleave all of them, and every gather of a renumbered matrix would be a DRAM sector).
@@ -383,9 +419,18 @@ struct LaplaceEngine {
     a.tol2 = tol * tol;
     a.maxiter = o.maxiter > 0 ? o.maxiter : 10000;
     a.by_slot = big.csr_rp != nullptr;
+    defl_k = big.defl_k;
+    if (defl_k) {
+      HP_TRY(hp_ws(ctx, "solve.defl_c", sizeof(double) * (size_t)ns * defl_k, &p));
+      a.dc = (double*)p;
+    }
     return HP_OK;
   }
   hp_status init() {
+    if (defl_k) {
+      ProfScope ps(ctx, "k_cg_defl");
+      k_cg_defl<NT><<<dim3(defl_k, nslots), NT, 0, ctx->stream>>>(a);
+    }
     {
       ProfScope ps(ctx, "k_cg_init");
       k_cg_init<NT><<<grid(), NT, 0, ctx->stream>>>(a);

@@ -44,7 +44,7 @@ EXPORTED = ["hp_ctx_create", "hp_ctx_destroy", "hp_last_error", "hp_ctx_synchron
             "hp_permutation", "hp_probe_vectors", "hp_trace_inv", "hp_trace_inv_grad", "hp_trace_inv_batch",
             "hp_operator_apply", "hp_dslash_bench", "hp_profile_enable", "hp_profile_report",
             "hp_launch_count", "hp_operator_apply_noalloc", "hp_probe_sequence", "hp_trace_inv_bounds",
-            "hp_sparse_coloring", "hp_sparse_probe_vectors", "hp_trace_inv_sparse"]
+            "hp_sparse_coloring", "hp_sparse_probe_vectors", "hp_trace_inv_sparse", "hp_trace_inv_deflated"]
 
 
 class Lattice(C.Structure):
@@ -113,6 +113,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hp_sparse_probe_vectors": (C.c_int, [P, I32, P, P, I32, I64, I64, C.c_uint64, P, C.POINTER(I32)]),
         "hp_trace_inv_sparse": (C.c_int, [P, I32, P, P, P, P, P, I32, I64, D, C.POINTER(SolverOpts), P, P,
                                           C.POINTER(SolveStats)]),
+        "hp_trace_inv_deflated": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I32, P, P, I64, D,
+                                            C.POINTER(SolverOpts), P, P, C.POINTER(SolveStats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -342,6 +344,21 @@ class Context:
         rp, ci, va = self._csr(row_ptr, col_idx, values)
         _check(lib().hp_trace_inv_sparse(self._h, n, rp, ci, va, _ptr(paths), _ptr(rad), len(rad), int(s_max),
                                          float(tol), C.byref(opts), _ptr(q_inout), _ptr(T), C.byref(st)))
+        return T, q_inout, st.as_dict()
+
+    def trace_inv_deflated(self, op: Operator, dims, evecs, evals, s_max: int, tol: float, opts: SolverOpts,
+                           q_inout=None):
+        """Laplacian with k eigenvectors deflated: evecs float64 [k, V] (host array or device
+        tensor), evals float64 [k] (host).  Returns (T [s_max] complex, q, stats)."""
+        ev = np.ascontiguousarray(np.asarray(evals, dtype=np.float64))
+        k = int(ev.shape[0])
+        T = np.zeros(s_max, dtype=np.complex128)
+        st = SolveStats()
+        if q_inout is not None:
+            assert q_inout.dtype == np.complex128 and q_inout.shape == (s_max,)
+        _check(lib().hp_trace_inv_deflated(self._h, C.byref(op), C.byref(make_lattice(dims)), k, _ptr(evecs),
+                                           _ptr(ev), int(s_max), float(tol), C.byref(opts), _ptr(q_inout), _ptr(T),
+                                           C.byref(st)))
         return T, q_inout, st.as_dict()
 
     def trace_inv_grad(self, op: Operator, dims, s_max: int, tol: float, opts: SolverOpts, grad_out):
