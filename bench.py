@@ -71,7 +71,7 @@ def source_hash(kernel):
 # same kernel on 32^3x16 with 12 slots (411.8 MB read + 146.2 MB written): the spinor part scaled
 # by the site-RHS ratio (8x), the links (read once per launch) by the site ratio (4x); valid only
 # for the kernel source it was taken on
-NCU_TRAFFIC = {("k_eo_even", "22bb82742bef"): {"bytes_all_slots": 4.162e9, "alg_bytes_all_slots": 1048576 * 104 * 24 + 4 * 2097152 * 36}}
+NCU_TRAFFIC = {("k_eo_even", "0f9f8db23114"): {"bytes_all_slots": 4.162e9, "alg_bytes_all_slots": 1048576 * 104 * 24 + 4 * 2097152 * 36}}
 
 
 class Clocks:
@@ -294,8 +294,8 @@ def run_ours(args):
     if e2e_steps:
         e2e = {"value": ws * e2e_rhs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d / e2e_steps),
                "d2h_bytes_per_step": int(d2h / e2e_steps), "steps": e2e_steps}
-        # the copy rate of the links from pinned host memory (what separates e2e from value): the
-        # first copy after a solve, as in every e2e step, and the same copy repeated at once
+        # the copy rate of the links from pinned host memory: the first copy after the e2e steps
+        # and the same copy repeated at once
         scratch = torch.empty_like(links_dev)
         torch.cuda.synchronize()
         rates = []
