@@ -2,7 +2,7 @@
 
 Oracle (test infrastructure only).
 
-* Shifted periodic Laplacian (Section 5 control problem; BASELINE form for
+* Shifted periodic Laplacian (Section 5 control problem, written for
   d = 4):  A = (2d + m) I - sum_mu (S_mu + S_mu^T), plus an optional
   per-site mass field mu(x) on the diagonal.
 * Wilson-Dirac matrix (Section 1.1.1: a sparse matrix on a periodic 4-D

@@ -6,7 +6,7 @@ table built by the counters of Algorithms 2 and 3, and the per-level bit
 tables of Algorithms 4 and 5.  None of it uses the closed form of Lemma 4;
 the CUDA library does, and the tests check one against the other.
 
-Conventions (readings of the paper, listed in the design doc):
+Conventions (readings of the paper where it leaves the choice open):
   * site index i = x_1 + L_1 (x_2 + L_2 (x_3 + ...)), x_1 varies fastest;
     dimension j = 1 supplies the most significant bit of each bit section;
   * the section of level 1 (least significant coordinate bits) forms the most
