@@ -219,7 +219,7 @@ def run_ours(args):
     links_dev = torch.from_numpy(U.view(np.float64).reshape(-1)).to(device)
     links_host = torch.from_numpy(U.view(np.float64).reshape(-1)).pin_memory()
     del U
-    from paper_1302_4018_gb300.sharding import probe_block
+    from paper_1302_4018_gb300.sharding import gather_quadratures, probe_block
 
     prec = args.precision
     P = args.probes_per_step
@@ -228,8 +228,8 @@ def run_ours(args):
     round_no = [0]
 
     def next_first():
-        # rank r solves block r of every round (disjoint probes; its prefix below is left at q = 0 here,
-        # the ranks' quadrature blocks concatenate into the nested sequence)
+        # rank r solves block r of every round (disjoint probes: the other ranks' entries of q stay 0
+        # here until the all-gather at the end of the timed steps)
         first, _ = probe_block(rank, ws, P, round_no[0])
         round_no[0] += 1
         return first
@@ -258,6 +258,11 @@ def run_ours(args):
     stats = []
     for _ in range(args.steps):
         stats.append(step(next_first(), links_dev))
+    # the nested estimate over every probe solved so far: at N > 1 one all-gather of the ranks' FP64
+    # quadratures, then the prefix sums by the library's kernel (a one-rank run's T_s, bit for bit)
+    s_done = round_no[0] * ws * P
+    q_all = gather_quadratures(q, rank, ws, P, round_no[0], device) if ws > 1 else q[:s_done]
+    T_all = ctx.trace_prefix(q_all)
     ev1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -393,6 +398,8 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "solver": {"rhs": rhs, "iters_per_solve": iters / max(1, rhs), "reliable_updates_per_solve": updates / max(1, rhs),
                    "max_true_residual": max_res},
+        "trace": {"s": int(s_done), "T_s": [float(T_all[-1].real), float(T_all[-1].imag)],
+                  "gathered_over_ranks": ws > 1},
         "fp64_solver": fp64,
         "mixed_over_fp64": (value / ws / fp64["solves_per_s"] * ws) if fp64 else None,
         "dslash": dslash,

@@ -217,6 +217,29 @@ hp_status hp_trace_inv(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat
                        double tol, const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
                        hp_solve_stats* stats);
 
+/* hp_trace_inv that also returns the solutions x_{m,a} of the first n_keep
+ * right-hand sides it solves (Wilson only): right-hand side j = 12 (m - first) + a
+ * of x_out (device, complex128 [n_keep][V][4][3] in the canonical layout of
+ * hp_operator_apply) receives the converged A^-1 v_{m,a} as the solver holds it
+ * (FP64, or the float-float solution of the mixed modes rounded to FP64).
+ * With them a caller checks ||v_{m,a} - A x_{m,a}|| / ||v_{m,a}|| and
+ * q_m = sum_a v_{m,a}^H x_{m,a} independently of the library (Section 1.1.2:
+ * each quadrature is a linear solve).  n_keep = 0 is hp_trace_inv.
+ * Errors: as hp_trace_inv, plus HP_EINVAL for a Laplacian, n_keep outside
+ * [0, 12 (s_max - first)] or x_out not device memory. */
+hp_status hp_trace_inv_solutions(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t s_max,
+                                 double tol, const hp_solver_opts* opts, int64_t n_keep, double* x_out,
+                                 double* q_inout, double* trace_prefix, hp_solve_stats* stats);
+
+/* The prefix estimates of a quadrature sequence computed elsewhere (Section 1:
+ * T_s = (1/s) sum_{m<s} q_m; Section 2.2: nested prefixes): q (host or device,
+ * complex (re, im) pairs [s_max]) -> trace_prefix (host or device, the same
+ * layout), summed in the order and FP64 arithmetic hp_trace_inv uses.  Ranks
+ * that solved disjoint probe blocks gather their q into one sequence and call
+ * this, so that their T_s equals a one-rank run's bit for bit.
+ * Errors: HP_EINVAL for s_max outside [1, 2^31) or a NULL array. */
+hp_status hp_trace_prefix(hp_ctx* ctx, int64_t s_max, const double* q, double* trace_prefix);
+
 /* hp_trace_inv for the Hermitian positive definite Laplacian with guaranteed
  * bounds on every quadrature (Section 1.1.2: the Gauss quadrature of
  * z^H A^-1 z computed by Lanczos comes with lower and upper bounds): with
@@ -343,6 +366,21 @@ hp_status hp_trace_inv_sparse(hp_ctx* ctx, int32_t n, const int32_t* row_ptr, co
 hp_status hp_operator_apply(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t nrhs,
                             int32_t precision, const double* in, double* out);
 
+/* The operator the even-odd iteration solves (opts->even_odd = 1): with the
+ * sites split by parity (x_1 + x_2 + x_3 + x_4 even / odd) the Wilson matrix is
+ * [[A_e, -kappa H_eo], [-kappa H_oe, A_o]] (A = 1 + mass + mu(s) + C(s), the
+ * site-diagonal part; H the hopping term of Section 1.1.1), and its odd-site
+ * Schur complement is
+ *     S = A_o - kappa^2 H_oe A_e^-1 H_eo.
+ * out = S in on the odd sites (zero on the even sites) for nrhs fields in the
+ * canonical layout of hp_operator_apply (host or device; the even sites of in
+ * are ignored), computed by the kernels and the precision the iteration uses
+ * (precision as hp_operator_apply: the input is rounded to that storage, the
+ * result returned in FP64).  Errors: HP_EINVAL for a Laplacian, L_1 odd (the
+ * half-lattice numbering needs L_1 even), kappa = 0, nrhs outside [1, 65532]. */
+hp_status hp_schur_apply(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t nrhs,
+                         int32_t precision, const double* in, double* out);
+
 /* y = D x for the Wilson operator in FP64, allocating nothing (the paper has
  * no counterpart: this serves callers that cannot let a library allocate GPU
  * memory, e.g. an application whose device memory is reserved up front by
@@ -350,17 +388,22 @@ hp_status hp_operator_apply(hp_ctx* ctx, const hp_operator* op, const hp_lattice
  * cudaMalloc / cudaFree calls off a latency-critical stream).
  * Same operator, layouts and FP64 arithmetic as hp_operator_apply with
  * HP_PREC_FP64; op->links, op->mass_field (nullable), in_dev and out_dev
- * must all be device memory of the current device, and the work is queued
- * on cuda_stream (NULL: the legacy default stream); no context is used.
+ * must all be device memory of the current device, and out_dev must not
+ * overlap in_dev, the links or the mass field (threads write a site's output
+ * while others still read its neighbours' input, so an in-place call would
+ * return a wrong D x).  The work is queued on cuda_stream (NULL: the legacy
+ * default stream); no context is used.
  * Working memory is one fixed file-scope device array (11.9 MB, held by
  * every GPU that loads the library until the process exits) that stores the
  * rearranged links; each call rewrites the part it reads, so nothing needs
- * clearing, but calls that overlap on the GPU share it and race.  The first
- * call on each device resolves the array's device address
- * (cudaGetSymbolAddress), so make it before any stream capture.
+ * clearing, but calls that overlap on the GPU share it and race.  Every call
+ * looks up the array's device address on the current device
+ * (cudaGetSymbolAddress); the first call on a device also loads the library's
+ * device code there, so make it before any stream capture.
  * Errors: HP_EINVAL for a lattice above 20736 sites (12^4), ndim outside
- * [1, 4], nrhs < 1, host pointers, a non-Wilson operator or csw != 0 (the
- * clover blocks would need workspace). */
+ * [1, 4], nrhs < 1 or nrhs * V >= 2^31, host pointers or memory of another
+ * device, an output that overlaps an input, a non-Wilson operator or
+ * csw != 0 (the clover blocks would need workspace). */
 hp_status hp_operator_apply_noalloc(const hp_operator* op, const hp_lattice* lat, int64_t nrhs,
                                     const double* in_dev, double* out_dev, void* cuda_stream);
 

@@ -205,6 +205,41 @@ def wilson_apply(psi: np.ndarray, U: np.ndarray, dims: Sequence[int], kappa: flo
     return out - kappa * hop
 
 
+def site_parity(dims: Sequence[int]) -> np.ndarray:
+    """(x_1 + ... + x_d) mod 2 for every lexicographic site (the red-black split of the lattice)."""
+    V = int(np.prod(dims))
+    strides = [int(np.prod(dims[:j])) for j in range(len(dims))]
+    i = np.arange(V)
+    return sum((i // strides[j]) % dims[j] for j in range(len(dims))) % 2
+
+
+def wilson_schur_apply(x: np.ndarray, U: np.ndarray, dims: Sequence[int], kappa: float,
+                       mass: float = 0.0, mass_field: np.ndarray | None = None,
+                       clover: np.ndarray | None = None) -> np.ndarray:
+    """The odd-site Schur complement of D (even-odd preconditioning of the Section 1.1.1 matrix,
+    the operator a red-black ordered solve iterates on):  ordering the sites even then odd,
+        D = [[A_e, -kappa H_eo], [-kappa H_oe, A_o]],   A = 1 + m + mu(x) + C(x) (site-diagonal),
+        S = A_o - kappa^2 H_oe A_e^-1 H_eo.
+    Returns S x_o on the odd sites and 0 on the even ones (x [V, 4, 3]; its even sites are
+    ignored), from two applications of D and the diagonal blocks A_e solved site by site:
+    y = D x_o has y_o = A_o x_o and y_e = -kappa H_eo x_o; w = A_e^-1 y_e on the even sites;
+    z = D w has z_o = -kappa H_oe w = kappa^2 H_oe A_e^-1 H_eo x_o; so S x_o = y_o - z_o."""
+    par = site_parity(dims)
+    odd = (par == 1)[:, None, None]
+    y = wilson_apply(np.where(odd, x, 0), U, dims, kappa, mass, mass_field, clover=clover)
+    ye = np.where(odd, 0, y)
+    d = 1.0 + mass + (np.zeros(y.shape[0]) if mass_field is None else mass_field)
+    if clover is None:
+        w = ye / d[:, None, None]
+    else:
+        ev = np.nonzero(par == 0)[0]
+        A = clover[ev] + d[ev, None, None] * np.eye(12)[None]
+        w = np.zeros_like(ye)
+        w[ev] = np.linalg.solve(A, ye[ev].reshape(-1, 12, 1)).reshape(-1, 4, 3)
+    z = wilson_apply(w, U, dims, kappa, mass, mass_field, clover=clover)
+    return np.where(odd, y - z, 0)
+
+
 def wilson_dense(U: np.ndarray, dims: Sequence[int], kappa: float, mass: float = 0.0,
                  mass_field: np.ndarray | None = None, clover: np.ndarray | None = None) -> np.ndarray:
     """D as a dense 12V x 12V matrix, block by block from its definition."""

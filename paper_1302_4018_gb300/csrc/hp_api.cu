@@ -12,6 +12,8 @@
 hp_status hp_apply_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrhs, int prec, const double* in,
                           double* out);
 hp_status hp_apply_laplace(hp_ctx* ctx, LatGeom g, int nrhs, const double* in, double* out);
+hp_status hp_schur_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrhs, int prec, const double* in,
+                          double* out);
 hp_status hp_bench_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int prec, int nrhs, int iters, double* ms,
                           double* bytes, double* flops);
 
@@ -222,6 +224,12 @@ struct BoundsReq {
   double *T_lower, *T_upper;
 };
 
+// solutions kept for the caller (hp_trace_inv_solutions)
+struct KeepReq {
+  int64_t n_keep;
+  double* x_out;   // device, complex [n_keep][V][12]
+};
+
 // deflated probing of the Laplacian (hp_trace_inv_deflated)
 struct DeflReq {
   int32_t k;
@@ -232,7 +240,7 @@ struct DeflReq {
 static hp_status trace_common(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t s_max, double tol,
                               const hp_solver_opts* opts, double* q_inout, double* trace_prefix, double* dT_dmu,
                               double* dT_dm, hp_solve_stats* stats, const BoundsReq* bounds = nullptr,
-                              const DeflReq* defl = nullptr) {
+                              const DeflReq* defl = nullptr, const KeepReq* keep = nullptr) {
   HP_TRY(check_ctx(ctx));
   LatGeom g;
   LatticeSetup* ls = nullptr;
@@ -295,6 +303,24 @@ static hp_status trace_common(hp_ctx* ctx, const hp_operator* op, const hp_latti
   pb.tol = tol;
   pb.opts = *opts;
   pb.want_grad = grad;
+  if (keep) {
+    if (op->kind != HP_OP_WILSON) {
+      hp_set_error("solutions are kept for the Wilson operator only");
+      return HP_EINVAL;
+    }
+    if (keep->n_keep < 0 || keep->n_keep > (s_max - opts->first) * 12) {
+      hp_set_error("n_keep = %lld outside [0, 12 (s_max - first)]", (long long)keep->n_keep);
+      return HP_EINVAL;
+    }
+    if (keep->n_keep > 0) {
+      if (!keep->x_out || !hp_is_device_ptr(keep->x_out)) {
+        hp_set_error("x_out must be device memory");
+        return HP_EINVAL;
+      }
+      pb.x_keep = (double2*)keep->x_out;
+      pb.n_keep = keep->n_keep;
+    }
+  }
   if (grad) {
     void* p = nullptr;
     HP_TRY(hp_ws(ctx, "grad.acc", sizeof(double) * (size_t)g.V, &p));
@@ -351,6 +377,39 @@ extern "C" hp_status hp_trace_inv(hp_ctx* ctx, const hp_operator* op, const hp_l
                                   const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
                                   hp_solve_stats* stats) {
   return trace_common(ctx, op, lat, s_max, tol, opts, q_inout, trace_prefix, nullptr, nullptr, stats);
+}
+
+extern "C" hp_status hp_trace_inv_solutions(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t s_max,
+                                            double tol, const hp_solver_opts* opts, int64_t n_keep, double* x_out,
+                                            double* q_inout, double* trace_prefix, hp_solve_stats* stats) {
+  const KeepReq keep{n_keep, x_out};
+  return trace_common(ctx, op, lat, s_max, tol, opts, q_inout, trace_prefix, nullptr, nullptr, stats, nullptr, nullptr,
+                      &keep);
+}
+
+extern "C" hp_status hp_trace_prefix(hp_ctx* ctx, int64_t s_max, const double* q, double* trace_prefix) {
+  HP_TRY(check_ctx(ctx));
+  if (s_max < 1 || s_max >= (1LL << 31) || !q || !trace_prefix) {
+    hp_set_error("hp_trace_prefix: s_max = %lld outside [1, 2^31) or a NULL array", (long long)s_max);
+    return HP_EINVAL;
+  }
+  // every q_m is an input (first = s_max): the kernel and summation order of hp_trace_inv
+  void* p = nullptr;
+  HP_TRY(hp_ws(ctx, "trace.qprev", sizeof(double2) * (size_t)s_max, &p));
+  double2* qprev = (double2*)p;
+  HP_TRY(hp_ws(ctx, "trace.qout", sizeof(double2) * (size_t)s_max, &p));
+  double2* qout = (double2*)p;
+  HP_TRY(hp_ws(ctx, "trace.T", sizeof(double2) * (size_t)s_max, &p));
+  double2* T = (double2*)p;
+  HP_CUDA(cudaMemcpyAsync(qprev, q, sizeof(double2) * (size_t)s_max, cudaMemcpyDefault, ctx->stream));
+  {
+    ProfScope ps(ctx, "k_trace_prefix");
+    k_trace_prefix<<<1, 32, 0, ctx->stream>>>(nullptr, 0, qprev, (int)s_max, (int)s_max, qout, T, nullptr, 0);
+  }
+  HP_LAUNCH_CHECK();
+  HP_CUDA(cudaMemcpyAsync(trace_prefix, T, sizeof(double2) * (size_t)s_max, cudaMemcpyDefault, ctx->stream));
+  HP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return HP_OK;
 }
 
 extern "C" hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k,
@@ -519,6 +578,26 @@ extern "C" hp_status hp_operator_apply(hp_ctx* ctx, const hp_operator* op, const
     return hp_apply_laplace(ctx, g, (int)nrhs, in, out);
   }
   return hp_apply_wilson(ctx, op, g, (int)nrhs, precision, in, out);
+}
+
+extern "C" hp_status hp_schur_apply(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t nrhs,
+                                    int32_t precision, const double* in, double* out) {
+  HP_TRY(check_ctx(ctx));
+  LatGeom g;
+  HP_TRY(operator_geom(ctx, op, lat, &g, nullptr));
+  if (op->kind != HP_OP_WILSON) {
+    hp_set_error("hp_schur_apply: the even-odd Schur complement belongs to the Wilson operator");
+    return HP_EINVAL;
+  }
+  if (nrhs < 1 || nrhs > 65532 || !in || !out) {
+    hp_set_error("hp_schur_apply: nrhs in [1, 65532] and non-NULL buffers required");
+    return HP_EINVAL;
+  }
+  if (precision < HP_PREC_FP64 || precision > HP_PREC_MIXED_BF16) {
+    hp_set_error("unknown precision %d", precision);
+    return HP_EINVAL;
+  }
+  return hp_schur_wilson(ctx, op, g, (int)nrhs, precision, in, out);
 }
 
 extern "C" hp_status hp_dslash_bench(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t precision,

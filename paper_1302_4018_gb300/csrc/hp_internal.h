@@ -222,6 +222,8 @@ struct SolveProblem {
   hp_solver_opts opts;
   bool want_grad = false;
   std::vector<double*> grad_dev;   // per lattice, [V] accumulators (device)
+  double2* x_keep = nullptr;       // optional: solutions of the first n_keep right-hand sides of lattice 0
+  int64_t n_keep = 0;              // (device, complex [n_keep][V][12], right-hand side (m - first) dof + a)
 };
 
 struct SolveResult {

@@ -446,6 +446,10 @@ struct LaplaceEngine {
     HP_LAUNCH_CHECK();
     return HP_OK;
   }
+  hp_status keep(const std::vector<int>&, const std::vector<SlotState>&, const SolveProblem&) {
+    hp_set_error("solutions are kept for the Wilson operator only");
+    return HP_EUNSUPPORTED;
+  }
   hp_status harvest(const std::vector<int>& done_slots, const SolveProblem& pb, int* dev_slots) {
     {
       ProfScope ps(ctx, "k_lquad");
@@ -1157,6 +1161,10 @@ struct BlockedSparseEngine {
     { ProfScope ps(ctx, "k_bcg_p"); k_bcg_p<SPL><<<a.nstream, BT, 0, ctx->stream>>>(a); }
     HP_LAUNCH_CHECK();
     return HP_OK;
+  }
+  hp_status keep(const std::vector<int>&, const std::vector<SlotState>&, const SolveProblem&) {
+    hp_set_error("solutions are kept for the Wilson operator only");
+    return HP_EUNSUPPORTED;
   }
   hp_status harvest(const std::vector<int>&, const SolveProblem&, int*) {
     { ProfScope ps(ctx, "k_bcg_quad"); k_bcg_quad<SPL><<<a.nstream, BT, 0, ctx->stream>>>(a); }

@@ -16,7 +16,6 @@
 // and race.
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 
 #include "hp_fields.cuh"
 
@@ -24,27 +23,17 @@
 
 static __device__ __align__(256) double2 g_noalloc_links[36 * HP_NOALLOC_MAX_SITES];
 
-// Device address of g_noalloc_links, resolved once per device (host code must
-// not use the symbol itself: on the host it is only a stand-in).
-static std::mutex g_noalloc_mutex;
-static void* g_noalloc_ptr[64] = {nullptr};
-
-static hp_status noalloc_scratch(int dev, double2** out) {
-  if (dev < 0 || dev >= 64) {
-    hp_set_error("hp_operator_apply_noalloc: device %d outside [0, 64)", dev);
-    return HP_EINVAL;
+// Device address of g_noalloc_links on the current device.  Host code must not use the symbol
+// itself (on the host it is only a stand-in); the address is looked up on every call, so a
+// primary context that was torn down and re-created never leaves a stale pointer behind.
+static hp_status noalloc_scratch(double2** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_links);
+  if (e != cudaSuccess || !p) {
+    hp_set_error("hp_operator_apply_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    return HP_ECUDA;
   }
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_links);
-    if (e != cudaSuccess || !p) {
-      hp_set_error("hp_operator_apply_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-      return HP_ECUDA;
-    }
-    g_noalloc_ptr[dev] = p;
-  }
-  *out = (double2*)g_noalloc_ptr[dev];
+  *out = (double2*)p;
   return HP_OK;
 }
 
@@ -119,13 +108,19 @@ __global__ void k_noalloc_wilson(LatGeom g, const double2* __restrict__ in, doub
   }
 }
 
-static bool is_device(const void* p) {
+// device that owns p, or -1 when p is not device (or managed) memory
+static int owning_device(const void* p) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return -1;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) ? a.device : -1;
+}
+
+static bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const char *pa = (const char*)a, *pb = (const char*)b;
+  return pa < pb + nb && pb < pa + na;
 }
 
 extern "C" hp_status hp_operator_apply_noalloc(const hp_operator* op, const hp_lattice* lat, int64_t nrhs,
@@ -164,19 +159,37 @@ extern "C" hp_status hp_operator_apply_noalloc(const hp_operator* op, const hp_l
                  HP_NOALLOC_MAX_SITES);
     return HP_EINVAL;
   }
-  if (nrhs * V > (1LL << 31)) {
-    hp_set_error("hp_operator_apply_noalloc: nrhs * V exceeds 2^31");
+  if (nrhs > 0x7fffffffLL || nrhs * V >= (1LL << 31)) {
+    hp_set_error("hp_operator_apply_noalloc: nrhs * V must stay below 2^31");
     return HP_EINVAL;
   }
-  if (!is_device(op->links) || !is_device(in_dev) || !is_device(out_dev) ||
-      (op->mass_field && !is_device(op->mass_field))) {
-    hp_set_error("hp_operator_apply_noalloc: links, mass field, input and output must be device memory");
+  const void* ptrs[4] = {op->links, in_dev, out_dev, op->mass_field};
+  int owner[4] = {0, 0, 0, 0};
+  for (int i = 0; i < 4; ++i) {
+    if (!ptrs[i]) continue;
+    owner[i] = owning_device(ptrs[i]);
+    if (owner[i] < 0) {
+      hp_set_error("hp_operator_apply_noalloc: links, mass field, input and output must be device memory");
+      return HP_EINVAL;
+    }
+  }
+  const size_t field = (size_t)nrhs * V * 24 * sizeof(double);
+  if (ranges_overlap(out_dev, field, in_dev, field) ||
+      ranges_overlap(out_dev, field, op->links, (size_t)V * 72 * sizeof(double)) ||
+      (op->mass_field && ranges_overlap(out_dev, field, op->mass_field, (size_t)V * sizeof(double)))) {
+    hp_set_error("hp_operator_apply_noalloc: the output overlaps the input, the links or the mass field");
     return HP_EINVAL;
   }
   int dev = -1;
   HP_CUDA(cudaGetDevice(&dev));
+  for (int i = 0; i < 4; ++i) {
+    if (ptrs[i] && owner[i] != dev) {
+      hp_set_error("hp_operator_apply_noalloc: a buffer lives on device %d, the current device is %d", owner[i], dev);
+      return HP_EINVAL;
+    }
+  }
   double2* scratch = nullptr;
-  HP_TRY(noalloc_scratch(dev, &scratch));
+  HP_TRY(noalloc_scratch(&scratch));
   g.V = (int)V;
   g.mass = op->mass;
   g.kappa = op->kappa;

@@ -121,6 +121,7 @@ hp_status run_schedule(hp_ctx* ctx, Engine& eng, SolveProblem& pb, SolveResult& 
       if (host[sl].status == SLOT_DONE || host[sl].status == SLOT_FAIL) done.push_back(sl);
     if (!done.empty()) {
       HP_TRY(eng.harvest(done, pb, dev_slots));
+      if (pb.x_keep) HP_TRY(eng.keep(done, host, pb));
       HP_CUDA(cudaMemcpyAsync(host.data(), st_dev, sizeof(SlotState) * nslots, cudaMemcpyDeviceToHost, ctx->stream));
       HP_CUDA(cudaStreamSynchronize(ctx->stream));
       for (int sl : done) {

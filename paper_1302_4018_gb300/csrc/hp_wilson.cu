@@ -148,6 +148,7 @@ hp_status hp_prepare_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom* g, cons
 #define HP_WILSON_DECLARE(SUFFIX)                                                                             \
   hp_status hp_wilson_apply_##SUFFIX(hp_ctx* ctx, const LatGeom& g, int nrhs, const double* in, double* out); \
   hp_status hp_wilson_bench_##SUFFIX(hp_ctx* ctx, const LatGeom& g, int nrhs, int iters, double* ms);         \
+  hp_status hp_wilson_schur_##SUFFIX(hp_ctx* ctx, const LatGeom& g, int nrhs, const double* in, double* out); \
   hp_status hp_wilson_solve_##SUFFIX(hp_ctx* ctx, SolveProblem& pb, SolveResult& res, bool eo, bool clover,   \
                                      double delta);
 HP_WILSON_DECLARE(fp64)
@@ -164,6 +165,28 @@ hp_status hp_apply_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrh
     case HP_PREC_MIXED_FP32: return hp_wilson_apply_fp32(ctx, g, nrhs, in, out);
     case HP_PREC_MIXED_FP16: return hp_wilson_apply_fp16(ctx, g, nrhs, in, out);
     case HP_PREC_MIXED_BF16: return hp_wilson_apply_bf16(ctx, g, nrhs, in, out);
+  }
+  hp_set_error("unknown precision %d", prec);
+  return HP_EINVAL;
+}
+
+hp_status hp_schur_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrhs, int prec, const double* in,
+                          double* out) {
+  if (g.L[0] % 2) {
+    hp_set_error("the even-odd numbering (half-site index site >> 1) needs L_1 even (L_1 = %d)", g.L[0]);
+    return HP_EINVAL;
+  }
+  if (op->kappa == 0.0) {
+    hp_set_error("the Schur complement needs kappa != 0");
+    return HP_EINVAL;
+  }
+  HP_TRY(hp_prepare_mass(ctx, op, &g, "schur"));
+  HP_TRY(hp_prepare_wilson(ctx, op, &g, "schur", (1 << PR64) | (1 << PR32) | (1 << PR16)));
+  switch (prec) {
+    case HP_PREC_FP64: return hp_wilson_schur_fp64(ctx, g, nrhs, in, out);
+    case HP_PREC_MIXED_FP32: return hp_wilson_schur_fp32(ctx, g, nrhs, in, out);
+    case HP_PREC_MIXED_FP16: return hp_wilson_schur_fp16(ctx, g, nrhs, in, out);
+    case HP_PREC_MIXED_BF16: return hp_wilson_schur_bf16(ctx, g, nrhs, in, out);
   }
   hp_set_error("unknown precision %d", prec);
   return HP_EINVAL;

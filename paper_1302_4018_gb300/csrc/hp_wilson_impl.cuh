@@ -1400,6 +1400,23 @@ static __global__ void k_eo_grad(WArgs a, int lat, const int* __restrict__ slots
   }
 }
 
+// ---- the solutions of harvested slots in the canonical layout: slot slots[i] -> right-hand side idx[i]
+// of out (complex [n][V][12]; FP64, float-float hi + lo, or the two parities of the even-odd iteration)
+static __global__ void k_w_keep(WArgs a, const int* __restrict__ slots, const int* __restrict__ idx, int nsl,
+                                double2* __restrict__ out, LatGeom g) {
+  const long long total = (long long)nsl * g.V;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / g.V), site = (int)(t - (long long)i * g.V);
+    const int slot = slots[i];
+    double2* o = out + ((size_t)idx[i] * g.V + site) * 12;
+    const int par = a.eo ? site_parity(g, site) : 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+      o[k] = a.eo ? eo_solution_component(a, slot, site, par, k) : solution_component(a, slot, site, k);
+  }
+}
+
 // ================================================================ the engine
 template <int SPR>
 static hp_status tune_rpt(hp_ctx* ctx, const LatGeom& g, FieldPtr fi, FieldPtr fo, int nrhs, int Vmax, int* best);
@@ -1635,6 +1652,32 @@ struct WilsonEngine {
     HP_LAUNCH_CHECK();
     return HP_OK;
   }
+  // copy the solutions of the harvested slots that the caller keeps (lattice 0, first n_keep right-hand sides)
+  hp_status keep(const std::vector<int>& done_slots, const std::vector<SlotState>& host, const SolveProblem& pb) {
+    std::vector<int> list;
+    for (int sl : done_slots) {
+      const SlotState& S = host[sl];
+      const int64_t j = (int64_t)(S.m - pb.first[0]) * 12 + S.a;
+      if (S.lat == 0 && j < pb.n_keep) list.push_back(sl);
+    }
+    const int n = (int)list.size();
+    if (!n) return HP_OK;
+    for (int i = 0; i < n; ++i) {
+      const SlotState& S = host[list[i]];
+      list.push_back((int)((int64_t)(S.m - pb.first[0]) * 12 + S.a));
+    }
+    void* p = nullptr;
+    HP_TRY(hp_ws(ctx, "solve.keep", sizeof(int) * 2 * (size_t)nslots, &p));
+    int* d = (int*)p;
+    HP_CUDA(cudaMemcpyAsync(d, list.data(), sizeof(int) * 2 * n, cudaMemcpyHostToDevice, ctx->stream));
+    {
+      ProfScope ps(ctx, "k_w_keep");
+      k_w_keep<<<blocks_for(ctx, (long long)n * pb.lats[0].V, 256), 256, 0, ctx->stream>>>(a, d, d + n, n, pb.x_keep,
+                                                                                        pb.lats[0]);
+    }
+    HP_LAUNCH_CHECK();
+    return HP_OK;
+  }
   hp_status harvest(const std::vector<int>& done_slots, const SolveProblem& pb, int* dev_slots) {
     if (eo) {
       {
@@ -1775,6 +1818,98 @@ static hp_status apply_wilson_t(hp_ctx* ctx, const LatGeom& g, int nrhs, const d
   return HP_OK;
 }
 
+// ================================================================ Schur-complement apply
+// canonical complex [nrhs][V][12] -> half-lattice field of parity `par` (slot = right-hand side)
+template <int SPR>
+__global__ void k_eo_from_canonical(const double2* __restrict__ in, FieldPtr f, LatGeom g, int Vmax, int nrhs,
+                                    int par) {
+  const int Vh = g.V >> 1;
+  const long long total = (long long)nrhs * Vh;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int slot = (int)(t / Vh), h = (int)(t - (long long)slot * Vh);
+    int x[4], st[4];
+    const int site = eo_site(g, h, par, x, st);
+    typedef typename Real_of<SPR>::T R;
+    cplx<R> s[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const double2 v = in[((size_t)slot * g.V + site) * 12 + k];
+      s[k] = {(R)v.x, (R)v.y};
+    }
+    SpinorIO<SPR>::store(f, Vmax, slot, h, s);
+  }
+}
+
+// half-lattice field of parity `par` -> canonical complex [nrhs][V][12], zero on the other parity
+template <int SPR>
+__global__ void k_eo_to_canonical(FieldPtr f, LatGeom g, int Vmax, int nrhs, int par, double2* __restrict__ out) {
+  const long long total = (long long)nrhs * g.V;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int slot = (int)(t / g.V), site = (int)(t - (long long)slot * g.V);
+    double2* o = out + ((size_t)slot * g.V + site) * 12;
+    if (site_parity(g, site) != par) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) o[k] = make_double2(0.0, 0.0);
+      continue;
+    }
+    typedef typename Real_of<SPR>::T R;
+    cplx<R> s[12];
+    SpinorIO<SPR>::load(f, Vmax, slot, site >> 1, s);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = make_double2((double)s[k].x, (double)s[k].y);
+  }
+}
+
+// out = S in on the odd sites, S = A_o - kappa^2 H_oe A_e^-1 H_eo (the even-odd iteration's operator),
+// through the solver's own launches: a WilsonEngine set up for the right-hand sides as running slots
+// of one lattice, its V step v = S p, in the iteration precision SPR
+template <int SPR>
+static hp_status schur_apply_t(hp_ctx* ctx, const LatGeom& g, int nrhs, const double* in, double* out) {
+  WilsonEngine<SPR> e{ctx};
+  e.eo = true;
+  e.clover = g.clover != 0;
+  const int ns = (nrhs + WilsonEngine<SPR>::GROUP_MAX - 1) / WilsonEngine<SPR>::GROUP_MAX * WilsonEngine<SPR>::GROUP_MAX;
+  void* p = nullptr;
+  HP_TRY(hp_ws(ctx, "schur.lat", sizeof(LatGeom), &p));
+  LatGeom* lat_dev = (LatGeom*)p;
+  HP_CUDA(cudaMemcpyAsync(lat_dev, &g, sizeof(LatGeom), cudaMemcpyHostToDevice, ctx->stream));
+  HP_TRY(hp_ws(ctx, "schur.state", sizeof(SlotState) * ns, &p));
+  SlotState* st_dev = (SlotState*)p;
+  std::vector<SlotState> st(ns);
+  memset(st.data(), 0, sizeof(SlotState) * ns);
+  for (int i = 0; i < nrhs; ++i) st[i].status = SLOT_RUN;
+  HP_CUDA(cudaMemcpyAsync(st_dev, st.data(), sizeof(SlotState) * ns, cudaMemcpyHostToDevice, ctx->stream));
+  hp_solver_opts o;
+  memset(&o, 0, sizeof(o));
+  HP_TRY(e.setup(ns, g.V, lat_dev, st_dev, o, 1e-10, 0.0, g));
+  size_t nb = 0;
+  const size_t fb = field_bytes(SPR, ns, e.a.Vmax, &nb);
+  HP_CUDA(cudaMemsetAsync(e.a.rh.p, 0, fb, ctx->stream));   // the V step's epilogue reads r^
+  if (nb) HP_CUDA(cudaMemsetAsync(e.a.rh.nrm, 0, nb, ctx->stream));
+  const size_t cbytes = sizeof(double2) * 12 * (size_t)nrhs * g.V;
+  const void* din = nullptr;
+  HP_TRY(hp_device_view(ctx, in, cbytes, "schur.canon_in", &din));
+  double* dout = out;
+  const bool out_host = !hp_is_device_ptr(out);
+  if (out_host) {
+    HP_TRY(hp_ws(ctx, "schur.canon_out", cbytes, &p));
+    dout = (double*)p;
+  }
+  const long long nh = (long long)nrhs * (g.V >> 1);
+  k_eo_from_canonical<SPR><<<blocks_for(ctx, nh, 256), 256, 0, ctx->stream>>>((const double2*)din, e.a.p, g,
+                                                                               e.a.Vmax, nrhs, 1);
+  HP_LAUNCH_CHECK();
+  HP_TRY(e.eo_step(0));
+  k_eo_to_canonical<SPR><<<blocks_for(ctx, (long long)nrhs * g.V, 256), 256, 0, ctx->stream>>>(
+      e.a.v, g, e.a.Vmax, nrhs, 1, (double2*)dout);
+  HP_LAUNCH_CHECK();
+  if (out_host) HP_CUDA(cudaMemcpyAsync(out, dout, cbytes, cudaMemcpyDeviceToHost, ctx->stream));
+  HP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return HP_OK;
+}
+
 // fills a field with deterministic pseudo-random values (benchmark input)
 template <int SPR>
 __global__ void k_w_fill(FieldPtr f, int V, int nrhs, unsigned long long seed) {
@@ -1873,6 +2008,10 @@ hp_status wilson_apply_prec(hp_ctx* ctx, const LatGeom& g, int nrhs, const doubl
   return apply_wilson_t<SPR>(ctx, g, nrhs, in, out);
 }
 template <int SPR>
+hp_status wilson_schur_prec(hp_ctx* ctx, const LatGeom& g, int nrhs, const double* in, double* out) {
+  return schur_apply_t<SPR>(ctx, g, nrhs, in, out);
+}
+template <int SPR>
 hp_status wilson_bench_prec(hp_ctx* ctx, const LatGeom& g, int nrhs, int iters, double* ms) {
   return bench_wilson_t<SPR>(ctx, g, nrhs, iters, ms);
 }
@@ -1890,6 +2029,9 @@ hp_status wilson_solve_prec(hp_ctx* ctx, SolveProblem& pb, SolveResult& res, boo
   }                                                                                                           \
   hp_status hp_wilson_bench_##SUFFIX(hp_ctx* ctx, const LatGeom& g, int nrhs, int iters, double* ms) {        \
     return wilson_bench_prec<SPR>(ctx, g, nrhs, iters, ms);                                                   \
+  }                                                                                                           \
+  hp_status hp_wilson_schur_##SUFFIX(hp_ctx* ctx, const LatGeom& g, int nrhs, const double* in, double* out) { \
+    return wilson_schur_prec<SPR>(ctx, g, nrhs, in, out);                                                     \
   }                                                                                                           \
   hp_status hp_wilson_solve_##SUFFIX(hp_ctx* ctx, SolveProblem& pb, SolveResult& res, bool eo, bool clover,   \
                                      double delta) {                                                          \

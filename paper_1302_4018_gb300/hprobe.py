@@ -44,7 +44,8 @@ EXPORTED = ["hp_ctx_create", "hp_ctx_destroy", "hp_last_error", "hp_ctx_synchron
             "hp_permutation", "hp_probe_vectors", "hp_trace_inv", "hp_trace_inv_grad", "hp_trace_inv_batch",
             "hp_operator_apply", "hp_dslash_bench", "hp_profile_enable", "hp_profile_report",
             "hp_launch_count", "hp_operator_apply_noalloc", "hp_probe_sequence", "hp_trace_inv_bounds",
-            "hp_sparse_coloring", "hp_sparse_probe_vectors", "hp_trace_inv_sparse", "hp_trace_inv_deflated"]
+            "hp_sparse_coloring", "hp_sparse_probe_vectors", "hp_trace_inv_sparse", "hp_trace_inv_deflated",
+            "hp_trace_inv_solutions", "hp_trace_prefix", "hp_schur_apply"]
 
 
 class Lattice(C.Structure):
@@ -115,6 +116,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                           C.POINTER(SolveStats)]),
         "hp_trace_inv_deflated": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I32, P, P, I64, D,
                                             C.POINTER(SolverOpts), P, P, C.POINTER(SolveStats)]),
+        "hp_trace_inv_solutions": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I64, D,
+                                             C.POINTER(SolverOpts), I64, P, P, P, C.POINTER(SolveStats)]),
+        "hp_trace_prefix": (C.c_int, [P, I64, P, P]),
+        "hp_schur_apply": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I64, I32, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -274,6 +279,13 @@ class Context:
                                        _ptr(inp), _ptr(out)))
         return out
 
+    def schur_apply(self, op: Operator, dims, nrhs: int, precision, inp, out):
+        """out = S inp on the odd sites (the even-odd iteration's Schur complement), canonical layout."""
+        prec = PREC[precision] if isinstance(precision, str) else int(precision)
+        _check(lib().hp_schur_apply(self._h, C.byref(op), C.byref(make_lattice(dims)), int(nrhs), prec, _ptr(inp),
+                                    _ptr(out)))
+        return out
+
     def trace_inv(self, op: Operator, dims, s_max: int, tol: float, opts: SolverOpts, q_inout=None):
         """Returns (T [s_max] complex, q [s_max] complex or None, stats dict).  ``q_inout``: host
         complex128 array of s_max (entries < opts.first are inputs)."""
@@ -284,6 +296,29 @@ class Context:
         _check(lib().hp_trace_inv(self._h, C.byref(op), C.byref(make_lattice(dims)), int(s_max), float(tol),
                                   C.byref(opts), _ptr(q_inout), _ptr(T), C.byref(st)))
         return T, q_inout, st.as_dict()
+
+    def trace_inv_solutions(self, op: Operator, dims, s_max: int, tol: float, opts: SolverOpts, x_out,
+                            q_inout=None):
+        """hp_trace_inv that also writes the solutions of the first right-hand sides into x_out
+        (device float64 tensor of n_keep * V * 24 values, canonical layout).  Returns as trace_inv."""
+        V = int(np.prod(dims))
+        n_keep = x_out.numel() // (24 * V)
+        assert x_out.numel() == n_keep * 24 * V
+        T = np.zeros(s_max, dtype=np.complex128)
+        st = SolveStats()
+        if q_inout is not None:
+            assert q_inout.dtype == np.complex128 and q_inout.shape == (s_max,)
+        _check(lib().hp_trace_inv_solutions(self._h, C.byref(op), C.byref(make_lattice(dims)), int(s_max),
+                                            float(tol), C.byref(opts), n_keep, _ptr(x_out), _ptr(q_inout), _ptr(T),
+                                            C.byref(st)))
+        return T, q_inout, st.as_dict()
+
+    def trace_prefix(self, q):
+        """T_s = (1/s) sum_{m<s} q_m for a host complex128 sequence q, by the library's prefix kernel."""
+        q = np.ascontiguousarray(q, dtype=np.complex128)
+        T = np.zeros(q.shape[0], dtype=np.complex128)
+        _check(lib().hp_trace_prefix(self._h, int(q.shape[0]), _ptr(q), _ptr(T)))
+        return T
 
     def trace_inv_bounds(self, op: Operator, dims, s_max: int, quad_tol: float, opts: SolverOpts,
                          lambda_min: float = 0.0):

@@ -105,6 +105,24 @@ def test_noalloc_rejects_clover_without_gpu():
     assert "csw" in lib.hp_last_error().decode()
 
 
+def test_noalloc_rejects_host_buffers_without_gpu():
+    """Links, input and output of the allocation-free stencil must be device memory of the current
+    device: host arrays are an argument error, found before any launch."""
+    from paper_1302_4018_gb300 import hprobe
+
+    lib = hprobe.lib()
+    links = np.zeros(72 * 16)
+    op = hprobe.Context.make_operator(hprobe.OP_WILSON, 0.0, 0.12, links, None)
+    lat = hprobe.make_lattice((2, 2, 2, 2))
+    a, b = np.zeros(24 * 16), np.zeros(24 * 16)
+    st = lib.hp_operator_apply_noalloc(ctypes.byref(op), ctypes.byref(lat), 1, a.ctypes.data, b.ctypes.data, None)
+    assert st == hprobe.HP_EINVAL
+    assert "device memory" in lib.hp_last_error().decode()
+    st = lib.hp_operator_apply_noalloc(ctypes.byref(op), ctypes.byref(lat), 1 << 31, a.ctypes.data, b.ctypes.data,
+                                       None)
+    assert st == hprobe.HP_EINVAL
+    assert "2^31" in lib.hp_last_error().decode()
+
 
 def test_sparse_entry_points_reject_a_missing_context_without_gpu():
     """The general-sparse calls validate their context and arguments before any device work."""

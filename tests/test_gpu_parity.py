@@ -128,26 +128,10 @@ def test_wilson_apply_parity(ctx, hp, dims, prec, nrhs):
     out = torch.empty(psi.size * 2, dtype=torch.float64, device="cuda:0")
     ctx.operator_apply(op, dims, nrhs, prec, dev(psi.view(np.float64).reshape(-1)), out)
     got = out.cpu().numpy().view(np.complex128).reshape(psi.shape)
-    for r in range(nrhs):
+    for r in range(nrhs):   # per site: the largest component error of any site, relative to max |ref|
         ref = O.wilson_apply(psi[r], U, dims, 0.12, 0.03, mf)
-        err = np.linalg.norm(got[r] - ref) / np.linalg.norm(ref)
+        err = np.abs(got[r] - ref).max() / np.abs(ref).max()
         assert err <= WILSON_TOL[prec], err
-
-
-def test_wilson_apply_full_size_sampled(ctx, hp):
-    dims = (32, 32, 32, 64)
-    V = int(np.prod(dims))
-    U = synth.gauge_links(dims, 0.4, 1003, device="cuda:0")
-    psi = synth.random_spinors(dims, 1, 5)[0]
-    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.12, links_dev(U), None)
-    out = torch.empty(V * 24, dtype=torch.float64, device="cuda:0")
-    for prec in ("fp64", "fp32"):
-        ctx.operator_apply(op, dims, 1, prec, dev(psi.view(np.float64).reshape(-1)), out)
-        got = out.cpu().numpy().view(np.complex128).reshape(V, 4, 3)
-        ref = O.wilson_apply(psi, U, dims, 0.12)
-        sites = np.random.default_rng(0).integers(0, V, 2000)
-        err = np.linalg.norm(got[sites] - ref[sites]) / np.linalg.norm(ref[sites])
-        assert err <= WILSON_TOL[prec]
 
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (3, 5, 4, 6), (8, 8, 8, 8), (16, 1, 1, 1)])
@@ -560,7 +544,7 @@ def test_clover_apply_parity(ctx, hp, dims, prec, nrhs):
     C = O.clover_term(U, dims, 0.12, CSW)
     for r in range(nrhs):
         ref = O.wilson_apply(psi[r], U, dims, 0.12, 0.02, mf, clover=C)
-        err = np.linalg.norm(got[r] - ref) / np.linalg.norm(ref)
+        err = np.abs(got[r] - ref).max() / np.abs(ref).max()   # per site
         assert err <= WILSON_TOL[prec], err
     if prec in ("fp64", "fp32"):   # the clover term is far above the comparison tolerance
         plain = O.wilson_apply(psi[0], U, dims, 0.12, 0.02, mf)

@@ -10,7 +10,7 @@ import torch
 import torch.distributed as dist
 import torch.multiprocessing as mp
 
-from paper_1302_4018_gb300.sharding import assemble, probe_block
+from paper_1302_4018_gb300.sharding import assemble, gather_quadratures, probe_block
 
 
 def _free_port():
@@ -71,6 +71,52 @@ def test_two_ranks_tile_the_nested_sequence():
     assert np.allclose(seq, ref, rtol=1e-13)
     T = E.trace_prefix(seq)
     assert np.allclose(T, E.trace_prefix(ref), rtol=1e-13)
+
+
+def _worker_gather(rank, world, port, out_q):
+    """Each rank fills only its own probe blocks (the others stay zero, as in bench.py at N > 1),
+    then the all-gather helper gives every rank the whole nested sequence."""
+    from oracle import estimator as E
+
+    _init(rank, world, port)
+    dims, per_rank, rounds = (4, 4, 2, 2), 2, 3
+    q = np.zeros(rounds * world * per_rank + 5, dtype=np.complex128)
+    for rnd in range(rounds):
+        first, count = probe_block(rank, world, per_rank, rnd)
+        q[first:first + count] = E.laplacian_quadratures(dims, 0.3, first, count, 7, method="dense")
+    full = gather_quadratures(q, rank, world, per_rank, rounds)
+    out_q.put((rank, full.tobytes()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gathered_quadratures_equal_the_one_rank_sequence_bitwise():
+    from oracle import estimator as E
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_gather, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=240) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    # the one-rank run solves the same probes block by block in sequence order
+    one = np.concatenate([E.laplacian_quadratures((4, 4, 2, 2), 0.3, f, 2, 7, method="dense")
+                          for f in range(0, 12, 2)]).astype(np.complex128)
+    for r in range(2):
+        seq = np.frombuffer(got[r], dtype=np.complex128)
+        assert seq.tobytes() == one.tobytes(), r
+        assert E.trace_prefix(seq).tobytes() == E.trace_prefix(one).tobytes()
+
+
+def test_gather_on_one_rank_is_the_identity():
+    q = np.arange(8, dtype=np.float64).astype(np.complex128) * (1 + 0.5j)
+    assert np.array_equal(gather_quadratures(q, 0, 1, 4, 2), q)
+    with pytest.raises(ValueError):
+        gather_quadratures(q[:5], 0, 1, 4, 2)
 
 
 def _worker_leaves(rank, world, port, out_q):

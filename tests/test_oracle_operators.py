@@ -216,3 +216,31 @@ def test_cg_quadrature_bounds_needs_mu_below_spectrum():
     exact = b @ np.linalg.solve(A, b)
     _, hist = S.cg_quadrature_bounds(lambda v: A @ v, b, 3.0, 1e-12)
     assert any(hi < exact * (1 - 1e-9) for _, hi in hist)
+
+
+@pytest.mark.parametrize("dims,csw,with_mf", [((4, 2, 2, 2), 0.0, True), ((2, 4, 2, 4), 0.0, False),
+                                              ((4, 2, 2, 2), 1.3, True), ((2, 2, 4, 2), 0.7, False)])
+def test_schur_complement_matches_dense_partition(dims, csw, with_mf):
+    """wilson_schur_apply against the Schur complement of the dense matrix: rows and columns
+    of D split by site parity, S = D_oo - D_oe D_ee^-1 D_eo (numpy's inverse), applied to a
+    random odd-site vector; the even sites of the result are zero."""
+    from paper_1302_4018_gb300 import synth
+
+    U = synth.gauge_links(dims, 0.5, 21)
+    V = int(np.prod(dims))
+    mf = synth.mass_field(dims, 0.05, 22) if with_mf else None
+    C = O.clover_term(U, dims, 0.13, csw) if csw else None
+    D = O.wilson_dense(U, dims, 0.13, 0.02, mf, clover=C)
+    par = np.repeat(O.site_parity(dims), 12)
+    e, o = np.nonzero(par == 0)[0], np.nonzero(par == 1)[0]
+    S = D[np.ix_(o, o)] - D[np.ix_(o, e)] @ np.linalg.inv(D[np.ix_(e, e)]) @ D[np.ix_(e, o)]
+    x = synth.random_spinors(dims, 1, 23)[0]
+    got = O.wilson_schur_apply(x, U, dims, 0.13, 0.02, mf, clover=C).reshape(-1)
+    assert np.allclose(got[o], S @ x.reshape(-1)[o], rtol=0, atol=1e-12 * np.abs(S @ x.reshape(-1)[o]).max())
+    assert not np.any(got[e])
+    # and the parity split itself: every hop of D connects sites of opposite parity, so D_ee and
+    # D_oo are block diagonal over sites
+    site = np.repeat(np.arange(V), 12)
+    for idx in (e, o):
+        blk = D[np.ix_(idx, idx)]
+        assert not np.any(blk[site[idx][:, None] != site[idx][None, :]])

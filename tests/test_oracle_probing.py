@@ -170,6 +170,27 @@ def test_phase_values_correctly_rounded(Pp):
             assert abs(tab[kk, 0]) == 0.5 or abs(tab[kk, 1]) == 0.5
 
 
+@pytest.mark.parametrize("Pp", [2, 6, 54, 162, 1458, 4374, 65534])
+def test_phase_values_are_the_nearest_binary64(Pp):
+    """Every entry of the oracle's table is the binary64 number nearest to cos / sin(2 pi k / P):
+    an independent 60-digit evaluation (mpmath) must be closer to it than to either neighbour
+    (a 1-ulp error anywhere in the decimal series fails this)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    tab = Pr.phase_values(Pp)
+    ks = range(Pp) if Pp <= 4374 else list(range(0, Pp, 97)) + [1, 2, Pp // 4 - 1, Pp // 2 + 1, Pp - 1]
+    for k in ks:
+        x = 2 * mp.pi * k / Pp
+        for j, true in enumerate((mp.cos(x), mp.sin(x))):
+            v = float(tab[k, j])
+            if abs(true) < mp.mpf(10) ** -50:       # an exact zero
+                assert v == 0.0, (k, j, v)
+                continue
+            err = abs(mp.mpf(v) - true)
+            for nb in (np.nextafter(v, np.inf), np.nextafter(v, -np.inf)):
+                assert err < abs(mp.mpf(float(nb)) - true), (Pp, k, j, v)
+
+
 def test_basis_sizes_for_lattices():
     b = Pr.LatticeBasis((12, 12, 12, 12))
     assert b.radices == [2] * 8 + [3, 27] and b.P == 54 and b.n_vectors == 20736
