@@ -659,6 +659,112 @@ def run_variance(args):
     print(json.dumps(out), flush=True)
 
 
+def _laplacian_exact_trace(dims, mass):
+    """Tr A^-1 of the shifted periodic Laplacian: A is diagonal in Fourier space."""
+    k = [2 * np.pi * np.arange(L) / L for L in dims]
+    lam = mass + sum(4 * np.sin(kk / 2) ** 2 for kk in np.meshgrid(*k, indexing="ij"))
+    return float(np.sum(1.0 / lam))
+
+
+def run_study(args):
+    """Sections 5.2 and 5.3 on synthetic data, every solve on the GPU (statistics on the host):
+    (a) speed-up ratio R_s = V_stoc / (V_hp(s) s) with jackknife errors over z_0 draws, on the
+        16^4 Wilson lattice (kappa 0.115, eps 0.3, link seed 1002), FP16 even-odd BiCGStab to 1e-10,
+        full spin-colour dilution;
+    (b) convergence of hierarchical probing, natural-order Hadamard and Z_2 noise (one z_0 each,
+        Z_2 with its +-2 (Var/s)^{1/2} interval) on the Laplacians of Section 5.2: 64^3 at
+        condition ~1e2, 32^4 at ~1e4 and 64 x 128^2 at ~1e6 (m = 4d / (cond - 1));
+    (c) the spread of T_s over many z_0 draws of hierarchical probing on the 64^3 Laplacian
+        (Section 5.2's 100 draws x 2048 vectors; +-2 sigma intervals).
+    value = probing solves/s over the whole study."""
+    import torch
+
+    from paper_1302_4018_gb300 import hprobe, study, synth
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = hprobe.Context(0, stream=stream.cuda_stream)
+    solves = 0
+    t_all = time.perf_counter()
+    # (a) Wilson speed-up ratio
+    dims_w = (16, 16, 16, 16)
+    U = synth.gauge_links(dims_w, 0.3, 1002, device="cuda:0")
+    links = torch.from_numpy(U.view(np.float64).reshape(-1)).to("cuda:0")
+    del U
+    opw = ctx.make_operator(hprobe.OP_WILSON, 0.0, 0.115, links, None)
+    S_w, n_w = args.study_wilson_vectors, args.study_seeds
+    rows = []
+    t0 = time.perf_counter()
+    for i in range(n_w):
+        T, _, st = ctx.trace_inv(opw, dims_w, S_w, 1e-10, ctx.make_opts("fp16", z0_seed=2002 + i, rhs_block=96,
+                                                                         even_odd=1))
+        rows.append(T)
+        solves += st["rhs_solved"]
+    t_w = time.perf_counter() - t0
+    Tw = np.array(rows)
+    R, eR = study.jackknife_speedup(Tw)
+    Vh, eV = study.jackknife_variance(Tw)
+    pts = [s for s in (1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024) if s <= S_w]
+    wilson = {"lattice": list(dims_w), "kappa": 0.115, "eps": 0.3, "z0_draws": n_w, "vectors": S_w,
+              "completion_points": [2, 32, 512], "seconds": t_w,
+              "s": pts, "V_hp": [float(Vh[s - 1]) for s in pts], "V_hp_err": [float(eV[s - 1]) for s in pts],
+              "R_s": [float(R[s - 1]) for s in pts], "R_s_err": [float(eR[s - 1]) for s in pts],
+              "max_R_s": float(np.max(R)), "argmax_s": int(np.argmax(R)) + 1,
+              "mean_T": [float(Tw[:, s - 1].real.mean()) for s in pts]}
+    del links, opw
+    # (b) Laplacian convergence at three condition numbers
+    lap = []
+    for dims, cond, S in (((64, 64, 64), 1e2, args.study_lap_vectors), ((32, 32, 32, 32), 1e4, args.study_lap_vectors),
+                          ((64, 128, 128), 1e6, max(16, args.study_lap_vectors // 4))):
+        mass = 4.0 * len(dims) / (cond - 1.0)
+        op = ctx.make_operator(hprobe.OP_LAPLACIAN, mass)
+        exact = _laplacian_exact_trace(dims, mass)
+        rec = {"lattice": list(dims), "mass": mass, "condition": cond, "exact_trace": exact, "vectors": S}
+        pts = [s for s in (1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048) if s <= S]
+        t0 = time.perf_counter()
+        for kind in ("hp", "natural", "z2"):
+            q = np.zeros(S, dtype=np.complex128)
+            T, q, st = ctx.trace_inv(op, dims, S, 1e-10, ctx.make_opts("fp64", z0_seed=7, rhs_block=128,
+                                                                        probe_kind=kind), q_inout=q)
+            solves += st["rhs_solved"]
+            rec[kind] = {"rel_error": [float(abs(T[s - 1].real - exact) / exact) for s in pts],
+                         "iters_per_solve": st["iterations_total"] / max(1, st["rhs_solved"])}
+            if kind == "z2":
+                w = study.z2_interval(q.real)
+                rec[kind]["rel_interval"] = [float(w[s - 1] / exact) if s > 1 else None for s in pts]
+        rec["s"] = pts
+        rec["seconds"] = time.perf_counter() - t0
+        lap.append(rec)
+    # (c) many z_0 draws of hierarchical probing on the 64^3 Laplacian
+    dims, mass = (64, 64, 64), 12.0 / 99.0
+    op = ctx.make_operator(hprobe.OP_LAPLACIAN, mass)
+    exact = _laplacian_exact_trace(dims, mass)
+    S_c, n_c = args.study_draw_vectors, args.study_draws
+    t0 = time.perf_counter()
+    rows = []
+    for i in range(n_c):
+        T, _, st = ctx.trace_inv(op, dims, S_c, 1e-10, ctx.make_opts("fp64", z0_seed=5000 + i, rhs_block=128))
+        rows.append(T.real)
+        solves += st["rhs_solved"]
+    Tc = np.array(rows)
+    pts = [s for s in (1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048) if s <= S_c]
+    draws = {"lattice": list(dims), "mass": mass, "exact_trace": exact, "z0_draws": n_c, "vectors": S_c,
+             "seconds": time.perf_counter() - t0, "s": pts,
+             "mean_rel_error": [float(abs(Tc[:, s - 1].mean() - exact) / exact) for s in pts],
+             "rel_2sigma": [float(2 * Tc[:, s - 1].std(ddof=1) / exact) for s in pts]}
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_all
+    out = {"metric": "probing solves/s, Sections 5.2-5.3 variance study (Wilson 16^4 speed-up ratio, Laplacians "
+                     "at condition 1e2 / 1e4 / 1e6, z_0 draws)",
+           "value": solves / wall, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16-storage/f32-math + f64",
+           "data": "synthetic (seeded SU(3) links; shifted periodic Laplacians with closed-form traces)",
+           "config": {"workload": "variance study: Wilson 16^4 R_s over %d z_0 x %d vectors; Laplacian convergence "
+                                  "64^3 / 32^4 / 64x128^2; %d z_0 x %d vectors on 64^3" % (n_w, S_w, n_c, S_c)},
+           "solves": solves, "wilson_speedup": wilson, "laplacian_convergence": lap, "z0_draws": draws}
+    print(json.dumps(out), flush=True)
+
+
 SPARSE_DIMS = (64, 64, 64)
 SPARSE_SEED = 4242
 
@@ -851,7 +957,13 @@ def main():
     ap.add_argument("--fp64-probes", type=int, default=1)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="headline", choices=["headline", "batch", "grad", "variance", "sparse"])
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "batch", "grad", "variance", "sparse", "study"])
+    ap.add_argument("--study-seeds", type=int, default=32, help="z_0 draws of the Wilson speed-up ratio")
+    ap.add_argument("--study-wilson-vectors", type=int, default=512)
+    ap.add_argument("--study-lap-vectors", type=int, default=1024)
+    ap.add_argument("--study-draws", type=int, default=100)
+    ap.add_argument("--study-draw-vectors", type=int, default=2048)
     ap.add_argument("--sparse-vectors", type=int, default=128)
     ap.add_argument("--sparse-rhs-block", type=int, default=64)
     ap.add_argument("--sparse-precision", default="fp32", choices=["fp64", "fp32"])
@@ -882,6 +994,8 @@ def main():
         run_variance(args)
     elif args.workload == "sparse":
         run_sparse(args)
+    elif args.workload == "study":
+        run_study(args)
     else:
         run_ours(args)
 

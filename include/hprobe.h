@@ -177,10 +177,17 @@ typedef struct {
                                links, + 100 for 18-real links, + 1000 G to sweep the lattice
                                in groups of G slots (0: autotune)                           */
     int32_t even_odd;       /* Wilson: 1 = iterate on the odd-site Schur complement
-                               d_o - kappa^2 H_oe d_e^-1 H_eo (needs L_1 even; the certified
+                               d_o - kappa^2 H_oe d_e^-1 H_eo (needs every extent even, the
+                               lattice padded to four dimensions included, else the full
+                               lattice is iterated; the certified
                                residual is still that of the full system)                   */
     int32_t probe_kind;     /* hp_probe_kind: the probing sequence (0: hierarchical probing) */
-    int32_t reserved[2];
+    int32_t eo_kernel;      /* even-odd iteration in FP32 / FP16 / BF16: the V and T step kernels --
+                               1 one right-hand side per thread, 3 or 4 two right-hand sides per
+                               thread (packed FP32x2 arithmetic) with 3 or 4 resident blocks of 128
+                               threads per SM; 0: the fastest of the three, timed on the problem's
+                               largest lattice and cached in the context                    */
+    int32_t reserved[1];
 } hp_solver_opts;
 
 typedef struct {
@@ -376,8 +383,9 @@ hp_status hp_operator_apply(hp_ctx* ctx, const hp_operator* op, const hp_lattice
  * canonical layout of hp_operator_apply (host or device; the even sites of in
  * are ignored), computed by the kernels and the precision the iteration uses
  * (precision as hp_operator_apply: the input is rounded to that storage, the
- * result returned in FP64).  Errors: HP_EINVAL for a Laplacian, L_1 odd (the
- * half-lattice numbering needs L_1 even), kappa = 0, nrhs outside [1, 65532]. */
+ * result returned in FP64).  Errors: HP_EINVAL for a Laplacian, an odd extent
+ * or fewer than four dimensions (then some hop joins sites of one parity and
+ * the split does not exist), kappa = 0, nrhs outside [1, 65532]. */
 hp_status hp_schur_apply(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t nrhs,
                          int32_t precision, const double* in, double* out);
 

@@ -53,6 +53,41 @@ def z0_variance(B: np.ndarray, Z: np.ndarray, s: int) -> float:
     return float(np.sum(np.triu(W, 1))) / s ** 2
 
 
+# ------------------------------------------------------------------ Section 5.3 statistics
+def sample_variance(x: np.ndarray, ddof: int = 1) -> float:
+    """(1/(n - ddof)) sum_i |x_i - mean|^2 over the n entries of x, written out."""
+    x = np.asarray(x)
+    n = x.shape[0]
+    m = sum(x) / n
+    return float(sum(abs(v - m) ** 2 for v in x) / (n - ddof))
+
+
+def speedup_ratio(T: np.ndarray, V_stoc: float | None = None, ddof: int = 1) -> np.ndarray:
+    """Section 5.3: R_s = V_stoc / (V_hp(s) s) for s = 1..S, from the estimates T[i, s-1] of n runs
+    (one row per bias-removal vector z_0^(i), one column per s).  V_hp(s) is the variance over the
+    runs of T_s; V_stoc, the variance of the standard Z_2 estimator with one vector, defaults to
+    V_hp(1): the first probing vector is z_0 (.) h_0 = z_0, a Z_2 noise vector itself.  The factor s
+    compares equal work: n s noise vectors would divide V_stoc by s."""
+    T = np.asarray(T)
+    S = T.shape[1]
+    v_hp = np.array([sample_variance(T[:, s], ddof) for s in range(S)])
+    v0 = v_hp[0] if V_stoc is None else V_stoc
+    return np.array([v0 / (v_hp[s] * (s + 1)) for s in range(S)])
+
+
+def jackknife(samples: np.ndarray, stat) -> tuple[float, float]:
+    """Delete-one jackknife (the error estimate of Section 5.3): stat over all n samples, and
+    err = sqrt((n - 1)/n sum_i (stat_(i) - mean_i stat_(i))^2) with stat_(i) computed without
+    sample i."""
+    samples = np.asarray(samples)
+    n = samples.shape[0]
+    full = stat(samples)
+    loo = [stat(np.concatenate([samples[:i], samples[i + 1:]])) for i in range(n)]
+    m = sum(loo) / n
+    err = np.sqrt((n - 1) / n * sum((v - m) ** 2 for v in loo))
+    return full, err
+
+
 # ------------------------------------------------------------------ prefix
 def trace_prefix(q: Sequence[complex]) -> np.ndarray:
     """T_s = (1/s) sum_{m<s} q_m, s = 1..len(q), plain sequential FP64 sums."""

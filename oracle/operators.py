@@ -223,7 +223,10 @@ def wilson_schur_apply(x: np.ndarray, U: np.ndarray, dims: Sequence[int], kappa:
     Returns S x_o on the odd sites and 0 on the even ones (x [V, 4, 3]; its even sites are
     ignored), from two applications of D and the diagonal blocks A_e solved site by site:
     y = D x_o has y_o = A_o x_o and y_e = -kappa H_eo x_o; w = A_e^-1 y_e on the even sites;
-    z = D w has z_o = -kappa H_oe w = kappa^2 H_oe A_e^-1 H_eo x_o; so S x_o = y_o - z_o."""
+    z = D w has z_o = -kappa H_oe w = kappa^2 H_oe A_e^-1 H_eo x_o; so S x_o = y_o - z_o.
+    The split needs every extent even: an odd extent wraps around between sites of one parity."""
+    if any(int(L) % 2 for L in dims):
+        raise ValueError("the even-odd split needs every lattice extent even: %s" % (tuple(dims),))
     par = site_parity(dims)
     odd = (par == 1)[:, None, None]
     y = wilson_apply(np.where(odd, x, 0), U, dims, kappa, mass, mass_field, clover=clover)

@@ -383,6 +383,7 @@ struct LaplaceEngine {
   hp_ctx* ctx;
   LArgs a;
   int nslots, gy;
+  int big_lat = 0;   // index of the largest lattice (set by the scheduler; unused here)
   int defl_k = 0;
   // A sparse matrix runs with slots along y: the blocks of one slot are scheduled together,
   // so the vector its rows gather from stays in L2 while the slot runs (slots along x would
@@ -1049,6 +1050,7 @@ struct BlockedSparseEngine {
   int kernels_per_iteration() const { return MIXED ? 5 : 4; }
   hp_ctx* ctx;
   BArgs a;
+  int big_lat = 0;          // index of the largest lattice (set by the scheduler; unused here)
   int ntrue = 1;            // row blocks of the true-residual kernel (per slot)
   double* tpart = nullptr;  // its partial sums [B][ntrue]
   unsigned int* tcnt = nullptr;

@@ -56,6 +56,7 @@ hp_status run_schedule(hp_ctx* ctx, Engine& eng, SolveProblem& pb, SolveResult& 
   int* dev_slots = (int*)p;
   std::vector<SlotState> host(nslots);
   memset(host.data(), 0, sizeof(SlotState) * nslots);
+  eng.big_lat = big;
   HP_TRY(eng.setup(nslots, Vmax, lats_dev, st_dev, pb.opts, pb.tol, delta, pb.lats[big]));
   const int G = eng.group();   // slots refilled together (one lattice per group: the stencil shares links)
 
@@ -88,13 +89,18 @@ hp_status run_schedule(hp_ctx* ctx, Engine& eng, SolveProblem& pb, SolveResult& 
   while (true) {
     bool any_init = false, any_run = false;
     for (int g0 = 0; g0 < nslots; g0 += G) {
-      bool empty = true;
-      for (int r = 0; r < G; ++r) empty = empty && host[g0 + r].status == SLOT_EMPTY;
-      if (!empty || qpos >= queue.size()) continue;
-      const int L = queue[qpos].lat;
-      for (int r = 0; r < G && qpos < queue.size() && queue[qpos].lat == L; ++r) {
-        const Item& it = queue[qpos++];
+      // the slots of a group hold right-hand sides of one lattice: an empty slot whose partners are
+      // still running takes the next item only if it belongs to their lattice (the queue runs
+      // through the lattices in order, so otherwise none of theirs is left)
+      int L = -1;
+      for (int r = 0; r < G; ++r)
+        if (host[g0 + r].status != SLOT_EMPTY) L = host[g0 + r].lat;
+      for (int r = 0; r < G && qpos < queue.size(); ++r) {
         SlotState& S = host[g0 + r];
+        if (S.status != SLOT_EMPTY) continue;
+        if (L >= 0 && queue[qpos].lat != L) break;
+        L = queue[qpos].lat;
+        const Item& it = queue[qpos++];
         memset(&S, 0, sizeof(SlotState));
         S.status = SLOT_INIT;
         S.lat = it.lat;

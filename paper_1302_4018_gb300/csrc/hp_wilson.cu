@@ -170,10 +170,21 @@ hp_status hp_apply_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrh
   return HP_EINVAL;
 }
 
+// The red-black split behind the even-odd iteration: every hop must join sites of opposite parity,
+// which holds when all four extents are even (an odd extent wraps around between sites of one
+// parity; a padded extent 1 hops onto the site itself); the half-site numbering site >> 1 then
+// needs L_1 even as well.
+static bool eo_lattice(const LatGeom& g) {
+  for (int j = 0; j < 4; ++j)
+    if (g.L[j] % 2) return false;
+  return true;
+}
+
 hp_status hp_schur_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrhs, int prec, const double* in,
                           double* out) {
-  if (g.L[0] % 2) {
-    hp_set_error("the even-odd numbering (half-site index site >> 1) needs L_1 even (L_1 = %d)", g.L[0]);
+  if (!eo_lattice(g)) {
+    hp_set_error("the even-odd split needs every extent even (lattice %d x %d x %d x %d; an odd or a padded "
+                 "extent joins sites of one parity)", g.L[0], g.L[1], g.L[2], g.L[3]);
     return HP_EINVAL;
   }
   if (op->kappa == 0.0) {
@@ -216,7 +227,7 @@ hp_status hp_solve_wilson(hp_ctx* ctx, SolveProblem& pb, SolveResult& res) {
   double delta = pb.opts.delta;
   bool eo = pb.opts.even_odd != 0, clover = false;
   for (auto& g : pb.lats) {
-    if (g.L[0] % 2) eo = false;   // parity numbering by site >> 1 needs L_1 even
+    if (!eo_lattice(g)) eo = false;   // odd or padded extents: no red-black split, full-lattice iteration
     clover = clover || g.clover;
   }
   // default group-update thresholds per iteration precision (measured on the 32^3x64 workload)

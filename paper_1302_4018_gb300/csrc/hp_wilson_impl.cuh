@@ -816,7 +816,7 @@ static __global__ void k_w_grad(WArgs a, int lat, const int* __restrict__ slots,
 // half follows as x_e = d_e^-1 (b_e + k H_eo x_o), and then the odd part of the full residual
 // is  r_o = b_o - d_o x_o + k H_oe x_e  while the even part vanishes by construction: the
 // certified residual is the residual of the full system.  Sites of one parity are numbered
-// by site >> 1 (needs L_1 even).
+// by site >> 1 (every extent even: otherwise some hop joins sites of one parity and the split fails).
 enum { MASK_RUN = 0, MASK_GROUP = 1, MASK_EXACT = 2, MASK_FRESH = 3 };
 
 __device__ __forceinline__ bool eo_mask(const SlotState* S, int mask) {
@@ -911,9 +911,9 @@ __device__ __forceinline__ double leading_part(ffl v) { return (double)v.hi; }
 // the iteration's launches -- left alone the compiler takes 160 and halves the warps; four for the
 // group update)
 template <int SIN, int LPR, int REC, int SOUT, int NT, int MASK, bool CL>
-__global__ void __launch_bounds__(NT, MASK == MASK_RUN ? 6 : 4) k_eo_even(WArgs a, FieldPtr in, FieldPtr mid, int nslots) {
+__global__ void __launch_bounds__(NT, SIN == PR64 ? 2 : (MASK == MASK_RUN ? 6 : 4)) k_eo_even(WArgs a, FieldPtr in, FieldPtr mid, int nslots) {
   EO_PREAMBLE(MASK)
-  typedef float R;
+  typedef typename Real_of<SIN>::T R;   // FP64 for the FP64 solver, FP32 arithmetic otherwise
   for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
     const int h = tile * NT + threadIdx.x;
     if (h >= nsite) continue;
@@ -946,12 +946,13 @@ enum { EPI_G = 3 };
 
 // resident blocks of 128 threads: six (<= 85 registers) with 18-real links, five (<= 102) with the
 // reconstructing 12-real form; the odd-site kernels are latency-bound, and the register count the
-// compiler picks unconstrained halves the warps an SM holds
-#define EO_ODD_MINB(REC) ((REC) == 18 ? 6 : 5)
+// compiler picks unconstrained halves the warps an SM holds; the FP64 solver's FP64 arithmetic gets two
+// (<= 256 registers: its twelve complex accumulators alone take 48)
+#define EO_ODD_MINB(SIN, REC) ((SIN) == PR64 ? 2 : (REC) == 18 ? 6 : 5)
 template <int SIN, int SMID, int LPR, int REC, int NT, int EPI, bool CL>
-__global__ void __launch_bounds__(NT, EO_ODD_MINB(REC)) k_eo_odd(WArgs a, FieldPtr in, FieldPtr mid, FieldPtr out, int nslots) {
+__global__ void __launch_bounds__(NT, EO_ODD_MINB(SIN, REC)) k_eo_odd(WArgs a, FieldPtr in, FieldPtr mid, FieldPtr out, int nslots) {
   EO_PREAMBLE(EPI == EPI_G ? MASK_GROUP : MASK_RUN)
-  typedef float R;
+  typedef typename Real_of<SIN>::T R;   // FP64 for the FP64 solver, FP32 arithmetic otherwise
   constexpr int NQ = EPI == EPI_V ? 2 : 3;
   R dots[NQ];
 #pragma unroll
@@ -1417,6 +1418,9 @@ static __global__ void k_w_keep(WArgs a, const int* __restrict__ slots, const in
   }
 }
 
+// the even-odd V and T steps with two right-hand sides per thread (FP16 / BF16 / FP32 iteration)
+#include "hp_eo2.cuh"
+
 // ================================================================ the engine
 template <int SPR>
 static hp_status tune_rpt(hp_ctx* ctx, const LatGeom& g, FieldPtr fi, FieldPtr fo, int nrhs, int Vmax, int* best);
@@ -1434,13 +1438,15 @@ struct WilsonEngine {
   bool clover = false; // some lattice of the problem carries the clover term; set before setup
   WArgs a;
   int nslots, gy, gyb, rpt = 1, variant = 10;
+  int eo_kernel = 4;   // even-odd V / T steps: 1 one right-hand side per thread, 3 / 4 pair kernels
+  int big_lat = 0;     // index of the largest lattice of the problem (set before setup)
   int kernels_per_iteration() const { return eo ? (SPR == PR64 ? 10 : 12) : (SPR == PR64 ? 7 : 8); }
   // streaming kernels: grid-stride with 8 blocks per SM per slot (few partial sums and atomic tickets);
   // stencil kernels: one block per tile (gy) so that the lattice is swept once in site order
   dim3 grid() const { return dim3(nslots, gyb); }
   dim3 grid_stencil() const { return dim3(nslots, gy); }
   // slots refilled together (the right-hand sides one thread carries must share a lattice)
-  int group() const { return rpt; }
+  int group() const { return (eo && SPR != PR64) ? 2 : rpt; }   // pairs also for eo_kernel 1 (any choice)
 
   hp_status setup(int ns, int Vmax, const LatGeom* lats_dev, SlotState* st, const hp_solver_opts& o, double tol,
                   double delta, const LatGeom& gbig) {
@@ -1513,6 +1519,11 @@ struct WilsonEngine {
     if (eo) {   // the even-odd kernels take one right-hand side per thread; keep the group and link form
       variant = 100 * variant_group(variant) + 10 + (variant % 10);
       rpt = 1;
+      if (SPR != PR64) {
+        const int k = o.eo_kernel;
+        if (k == 1 || k == 3 || k == 4) eo_kernel = k;
+        else HP_TRY(tune_eo(gbig));
+      }
     }
     return HP_OK;
   }
@@ -1523,6 +1534,9 @@ struct WilsonEngine {
   hp_status eo_schur(int which) {   // which: 0 v = S p, 1 t = S s, 2 group update with e
     dim3 gr = eo_grid();
     constexpr int LPR = LinkPrecOf<SPR>::v;
+    if constexpr (SPR != PR64) {   // two right-hand sides per thread, all slot pairs of a tile together
+      if (which < 2 && eo_kernel >= 3) return eo_kernel == 3 ? eo_pair<3, CL>(which) : eo_pair<4, CL>(which);
+    }
     if (which == 0) {
       {
         ProfScope ps(ctx, "k_eo_even");
@@ -1549,6 +1563,83 @@ struct WilsonEngine {
       k_eo_odd<EPR, PR32, PR32, 12, NT, EPI_G, CL><<<gr, NT, 0, ctx->stream>>>(a, a.e, a.mid32, a.rg, nslots);
     }
     HP_LAUNCH_CHECK();
+    return HP_OK;
+  }
+  // the V (which 0) or T (1) step with the pair kernels under a register budget of MINB blocks per SM
+  template <int MINB, bool CL>
+  hp_status eo_pair(int which) {
+    static_assert(SPR != PR64, "the pair kernels serve the FP32 / FP16 / BF16 iteration");
+    const dim3 g2((nslots + 1) / 2, gy, 1);
+    FieldPtr in = which == 0 ? a.p : a.s, out = which == 0 ? a.v : a.t;
+    {
+      ProfScope ps(ctx, "k_eo_even");
+      k_eo2_even<SPR, NT, MINB, CL><<<g2, NT, 0, ctx->stream>>>(a, in, a.mid, nslots);
+    }
+    HP_LAUNCH_CHECK();
+    if (which == 0) {
+      ProfScope ps(ctx, SPR == PR32 ? "k_eo_odd_v<fp32>" : SPR == PR16 ? "k_eo_odd_v<fp16>" : "k_eo_odd_v<bf16>");
+      k_eo2_odd<SPR, NT, MINB, EPI_V, CL><<<g2, NT, 0, ctx->stream>>>(a, in, a.mid, out, nslots);
+    } else {
+      ProfScope ps(ctx, SPR == PR32 ? "k_eo_odd_t<fp32>" : SPR == PR16 ? "k_eo_odd_t<fp16>" : "k_eo_odd_t<bf16>");
+      k_eo2_odd<SPR, NT, MINB, EPI_T, CL><<<g2, NT, 0, ctx->stream>>>(a, in, a.mid, out, nslots);
+    }
+    HP_LAUNCH_CHECK();
+    return HP_OK;
+  }
+  // Autotuner of the even-odd iteration kernels: times the V step (k_eo_even + k_eo_odd) of every
+  // variant -- one right-hand side per thread (1), the pair kernels at 3 or 4 resident blocks --
+  // on this engine's fields with all slots marked running (a scratch copy of the slot states), and
+  // keeps the fastest per (precision, lattice, slots).
+  hp_status tune_eo(const LatGeom& gbig) {
+    char key[160];
+    snprintf(key, sizeof(key), "eo:%d:%d,%d,%d,%d:%d", SPR, gbig.L[0], gbig.L[1], gbig.L[2], gbig.L[3], nslots);
+    auto it = ctx->autotune.find(key);
+    if (it != ctx->autotune.end()) {
+      eo_kernel = it->second;
+      return HP_OK;
+    }
+    SlotState* keep = a.st;
+    void* p = nullptr;
+    HP_TRY(hp_ws(ctx, "solve.tune_state", sizeof(SlotState) * nslots, &p));
+    std::vector<SlotState> st(nslots);
+    memset(st.data(), 0, sizeof(SlotState) * nslots);
+    for (auto& S : st) {   // every slot running on the largest lattice of the problem
+      S.status = SLOT_RUN;
+      S.lat = big_lat;
+    }
+    HP_CUDA(cudaMemcpyAsync(p, st.data(), sizeof(SlotState) * nslots, cudaMemcpyHostToDevice, ctx->stream));
+    a.st = (SlotState*)p;
+    cudaEvent_t e0, e1;
+    HP_CUDA(cudaEventCreate(&e0));
+    HP_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int choice = 4;
+    const bool prof = ctx->profiling;
+    ctx->profiling = false;
+    hp_status status = HP_OK;
+    for (int c : {1, 3, 4}) {
+      eo_kernel = c;
+      status = eo_step(0);
+      if (status != HP_OK) break;
+      cudaEventRecord(e0, ctx->stream);
+      for (int i = 0; i < 3 && status == HP_OK; ++i) status = eo_step(0);
+      cudaEventRecord(e1, ctx->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        choice = c;
+      }
+    }
+    ctx->profiling = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    a.st = keep;
+    HP_TRY(status);
+    HP_CUDA(cudaMemsetAsync(a.cnt, 0, sizeof(unsigned int) * nslots, ctx->stream));
+    eo_kernel = choice;
+    ctx->autotune[key] = choice;
     return HP_OK;
   }
   hp_status eo_step(int which) {

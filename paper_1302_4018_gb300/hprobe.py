@@ -68,7 +68,7 @@ class SolverOpts(C.Structure):
                 ("dilution", C.c_int32), ("z0_seed", C.c_uint64), ("first", C.c_int64), ("delta", C.c_double),
                 ("check_every", C.c_int32), ("use_graph", C.c_int32), ("block_threads", C.c_int32),
                 ("rhs_per_thread", C.c_int32), ("even_odd", C.c_int32), ("probe_kind", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("eo_kernel", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class SolveStats(C.Structure):
@@ -254,9 +254,10 @@ class Context:
     @staticmethod
     def make_opts(precision="fp64", rhs_block=0, maxiter=0, z0_seed=0, first=0, delta=0.0, check_every=0,
                   use_graph=0, block_threads=0, dilution=0, rhs_per_thread=0, even_odd=0,
-                  probe_kind=0) -> SolverOpts:
+                  probe_kind=0, eo_kernel=0) -> SolverOpts:
         """probe_kind: 0 / "hp" hierarchical probing, 1 / "natural" Hadamard vectors in natural
-        order, 2 / "z2" Z_2 noise vectors (seeded by z0_seed)."""
+        order, 2 / "z2" Z_2 noise vectors (seeded by z0_seed).  eo_kernel: the even-odd V / T step
+        kernels (1 one right-hand side per thread, 3 / 4 pair kernels, 0 autotuned)."""
         o = SolverOpts()
         o.precision = PREC[precision] if isinstance(precision, str) else int(precision)
         o.rhs_block = rhs_block
@@ -271,6 +272,7 @@ class Context:
         o.rhs_per_thread = rhs_per_thread
         o.even_odd = even_odd
         o.probe_kind = PROBE_KINDS[probe_kind] if isinstance(probe_kind, str) else int(probe_kind)
+        o.eo_kernel = eo_kernel
         return o
 
     def operator_apply(self, op: Operator, dims, nrhs: int, precision, inp, out):

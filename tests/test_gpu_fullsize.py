@@ -58,7 +58,7 @@ def site_max_err(got, ref, sites=None):
 
 
 SCHUR_CASES = [((4, 4, 4, 4), 1, 0.0), ((4, 4, 4, 4), 5, 0.0), ((6, 2, 4, 6), 3, 0.0), ((2, 2, 2, 2), 2, 0.0),
-               ((8, 4, 6, 2), 4, 0.0), ((4, 4, 4, 4), 3, 1.0), ((6, 4, 2, 4), 2, 0.8), ((2, 6), 2, 0.0)]
+               ((8, 4, 6, 2), 4, 0.0), ((4, 4, 4, 4), 3, 1.0), ((6, 4, 2, 4), 2, 0.8), ((2, 6, 2, 2), 2, 0.0)]
 
 
 @pytest.mark.parametrize("dims,nrhs,csw", SCHUR_CASES)
@@ -79,11 +79,13 @@ def test_schur_apply_matches_oracle(ctx, hp, dims, nrhs, csw, prec):
         assert not np.any(got[r][O.site_parity(d4) == 0])
 
 
-def test_schur_apply_rejects_odd_first_dimension(ctx, hp):
-    dims = (3, 4, 2, 2)
+@pytest.mark.parametrize("dims", [(3, 4, 2, 2), (4, 3, 2, 2), (2, 2, 2, 5), (2, 6)])
+def test_schur_apply_rejects_lattices_without_a_red_black_split(ctx, hp, dims):
+    """An odd extent (or a padded one of size 1) makes some hop join sites of one parity."""
+    V = int(np.prod(dims))
     U = synth.gauge_links(dims, 0.3, 1)
     op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.12, dev(U.view(np.float64).reshape(-1)), None)
-    x = torch.zeros(48 * 24, dtype=torch.float64, device="cuda:0")
+    x = torch.zeros(V * 24, dtype=torch.float64, device="cuda:0")
     with pytest.raises(hp.HProbeError) as e:
         ctx.schur_apply(op, dims, 1, "fp64", x, torch.empty_like(x))
     assert e.value.status == hp.HP_EINVAL
@@ -160,3 +162,15 @@ def test_headline_solutions_against_the_oracle(ctx, hp, headline):
         r = b - O.wilson_apply(xs[a], U, dims, 0.12)
         res = np.linalg.norm(r) / np.linalg.norm(b)
         assert res <= 1e-10, (a, res)
+
+
+@pytest.mark.parametrize("dims", [(4, 3, 2, 2), (2, 2, 2, 5)])
+def test_even_odd_request_on_an_odd_extent_iterates_the_full_lattice(ctx, hp, dims):
+    """With an odd extent the wrap-around joins sites of one parity, so the even-odd split does not
+    exist: the solver iterates the full lattice instead and the trace still matches dense LU."""
+    U = synth.gauge_links(dims, 0.4, 3)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.12, dev(U.view(np.float64).reshape(-1)), None)
+    T, _, st = ctx.trace_inv(op, dims, 3, 1e-10, ctx.make_opts("fp16", z0_seed=7, even_odd=1))
+    T_ref = E.trace_prefix(E.wilson_quadratures(dims, U, 0.12, 0, 3, 7, method="dense"))
+    assert np.all(np.abs(T - T_ref) <= 1e-9 * np.abs(T_ref)), (T, T_ref)
+    assert st["max_true_residual"] <= 1e-10

@@ -263,3 +263,43 @@ def test_deflating_the_lowest_modes_reduces_the_z0_variance():
     Z = 1 - 2 * ph
     for s in (8, 16, 64):
         assert E.z0_variance(Bd, Z, s) < 0.5 * E.z0_variance(B, Z, s)
+
+
+def test_speedup_ratio_of_all_z0_is_the_closed_form_ratio():
+    """R_s over every one of the 2^16 vectors z_0 of the 2^4 torus (population variances) equals
+    z0_variance(1) / (z0_variance(s) s) from the closed form; R_1 = 1; at s = N the estimate is
+    exact for every z_0 (infinite ratio)."""
+    from oracle import probing as Pr
+
+    dims = (2, 2, 2, 2)
+    V = 16
+    B = np.linalg.inv(O.laplacian_dense(dims, 0.3))
+    ph, _ = Pr.probe_phases(dims, 0, V, 0)
+    Z = 1 - 2 * ph
+    bits = (np.arange(2 ** V)[:, None] >> np.arange(V)[None, :]) & 1
+    Z0 = 1 - 2 * bits
+    svals = (1, 2, 3, 4, 8)
+    T = np.stack([np.einsum("ki,ij,kj->k", Z0, B * (Z[:s].T @ Z[:s]), Z0) / s for s in svals], 1)
+    # columns are s = 1, 2, 3, 4, 8: rescale the generic definition by the actual s
+    v = [E.sample_variance(T[:, j], ddof=0) for j in range(len(svals))]
+    for j, s in enumerate(svals):
+        closed = E.z0_variance(B, Z, 1) / (E.z0_variance(B, Z, s) * s)
+        assert abs(v[0] / (v[j] * s) - closed) <= 1e-9 * closed
+    R = E.speedup_ratio(T[:, :2], ddof=0)
+    assert R[0] == 1.0
+    assert abs(R[1] - E.z0_variance(B, Z, 1) / (E.z0_variance(B, Z, 2) * 2)) <= 1e-9 * R[1]
+
+
+def test_jackknife_of_the_mean_is_the_standard_error():
+    """For the mean, the delete-one jackknife error equals the textbook standard error
+    std(ddof = 1) / sqrt(n) exactly; for a constant statistic it is zero."""
+    x = np.random.default_rng(3).normal(2.0, 0.7, 41)
+    m, err = E.jackknife(x, lambda a: a.mean())
+    assert abs(m - x.mean()) <= 1e-15 * abs(m)
+    assert abs(err - x.std(ddof=1) / np.sqrt(41)) <= 1e-12 * err
+    assert E.jackknife(x, lambda a: 5.0)[1] == 0.0
+    # the variance statistic: its jackknife error shrinks like 1 / sqrt(n)
+    y = np.random.default_rng(4).normal(0, 1, 4000)
+    _, e_small = E.jackknife(y[:400], lambda a: a.var(ddof=1))
+    _, e_big = E.jackknife(y, lambda a: a.var(ddof=1))
+    assert 2.0 < e_small / e_big < 5.0

@@ -244,3 +244,11 @@ def test_schur_complement_matches_dense_partition(dims, csw, with_mf):
     for idx in (e, o):
         blk = D[np.ix_(idx, idx)]
         assert not np.any(blk[site[idx][:, None] != site[idx][None, :]])
+
+
+def test_schur_complement_needs_even_extents():
+    from paper_1302_4018_gb300 import synth
+
+    U = synth.gauge_links((4, 3, 2, 2), 0.3, 1)
+    with pytest.raises(ValueError):
+        O.wilson_schur_apply(np.zeros((48, 4, 3), complex), U, (4, 3, 2, 2), 0.12)
