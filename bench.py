@@ -51,11 +51,12 @@ def hbm_peak():
 
 
 def source_hash(kernel):
-    """Hash of the sources a kernel is built from: the shared field and geometry headers and the
-    kernel's own definition in the solver templates (its DRAM traffic below is valid for them only)."""
+    """Hash of the sources a kernel is built from: the shared field and geometry headers, the
+    two-right-hand-side even-odd kernels, and the kernel's own definition in the solver templates
+    (its DRAM traffic below is valid for them only)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1302_4018_gb300", "csrc")
-    for f in ("hp_fields.cuh", "hp_internal.h"):
+    for f in ("hp_fields.cuh", "hp_internal.h", "hp_eo2.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     with open(os.path.join(csrc, "hp_wilson_impl.cuh")) as fh:
@@ -238,7 +239,8 @@ def run_ours(args):
         op = ctx.make_operator(hprobe.OP_WILSON, 0.0, KAPPA, links, None, csw=args.csw)
         s_max = first + probes
         opts = ctx.make_opts(precision, z0_seed=Z0_SEED, first=first, rhs_block=rhs_block,
-                             even_odd=1 if args.even_odd else 0)
+                             even_odd=1 if args.even_odd else 0, eo_kernel=args.eo_kernel,
+                             rhs_per_thread=args.rhs_per_thread, use_graph=args.use_graph)
         qq = q[:s_max].copy()
         T, qq, st = ctx.trace_inv(op, DIMS, s_max, TOL, opts, q_inout=qq)
         q[:s_max] = qq
@@ -370,6 +372,21 @@ def run_ours(args):
                 "mean_launch_ms": top_rec["ms"] / top_rec["launches"],
                 "traffic": trace_ncu}
 
+    # the same kernel against the FP32 arithmetic peak: the even-odd stencils of the mixed iteration
+    # keep the FP32 FMA pipe busy (binary16 storage, FP32 arithmetic; ncu: pipe_fmaheavy ~65 %), so
+    # their ALU roofline is the FP32 rate: 152 SMs x 128 lanes x 2 flop x the SM clock under load
+    roof_fp32 = None
+    if top_name == "k_eo_even" and prec in ("fp16", "bf16", "fp32"):
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = clk.get("sm_mhz") or 2070.0
+        peak_tf = sms * 128 * 2 * mhz * 1e6 / 1e12
+        flops = (V // 2) * 1320 * 2 * iters   # the hop of every even site, V and T steps, per right-hand side
+        ach = flops / (top_rec["ms"] / 1e3) / 1e12
+        roof_fp32 = {"kernel": top_name, "bound": "alu", "achieved": ach, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": ach / peak_tf, "flops_per_site_rhs": 1320,
+                     "peak_source": "%d SMs x 128 FP32 lanes x 2 flop x %.0f MHz (median SM clock of the timed steps)"
+                                    % (sms, mhz)}
+
     cpu = None   # (the oracle's clover term is a per-site Python loop: no sampled baseline with --csw)
     if rank == 0 and not args.no_cpu_baseline and ws == 1 and not args.csw:
         cpu = cpu_baseline(FP64_ITERS_PER_SOLVE)
@@ -390,11 +407,13 @@ def run_ours(args):
                    "even_odd": bool(args.even_odd),
                    "lattice": list(DIMS), "probes_per_step": P, "rhs_per_step": 12 * P, "rhs_block": args.rhs_block,
                    "precision": prec, "tol": TOL, "l2": "inputs larger than L2 (each field >= 100 MB)",
+                   "eo_kernel": args.eo_kernel, "rhs_per_thread": args.rhs_per_thread, "use_graph": args.use_graph,
                    "parallelism": "dp%d over probe blocks" % ws},
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "roofline": roofline,
+        "roofline_fp32": roof_fp32,
         "cpu_baseline": cpu,
         "solver": {"rhs": rhs, "iters_per_solve": iters / max(1, rhs), "reliable_updates_per_solve": updates / max(1, rhs),
                    "max_true_residual": max_res},
@@ -442,16 +461,88 @@ def _links_device():
         return "cpu"
 
 
+def host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    return os.cpu_count() or 1, model or "unknown"
+
+
+def _oracle_worker(path, reps, out_q):
+    """One host core: the oracle's BiCGStab iterations on the shared links (memory-mapped)."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    U = np.load(path, mmap_mode="r")
+    out_q.put(oracle_iteration_time(np.asarray(U), reps))
+
+
+def oracle_all_cores(U, reps=1, workers=None):
+    """The oracle on every host core at once: one process per core, each running `reps` BiCGStab
+    iterations on its own right-hand side (the links shared through a memory-mapped file); returns
+    (seconds per iteration of the slowest worker, workers)."""
+    import multiprocessing as mp
+    import tempfile
+
+    n = workers or os.cpu_count() or 1
+    d = "/dev/shm" if os.path.isdir("/dev/shm") else None
+    with tempfile.NamedTemporaryFile(suffix=".npy", dir=d, delete=False) as f:
+        path = f.name
+    try:
+        np.save(path, np.ascontiguousarray(U))
+        ctx = mp.get_context("spawn")   # a fork after CUDA initialisation would hang
+        q = ctx.Queue()
+        procs = [ctx.Process(target=_oracle_worker, args=(path, reps, q)) for _ in range(n)]
+        for p in procs:
+            p.start()
+        times = []
+        t0 = time.time()
+        while len(times) < n:
+            try:
+                times.append(q.get(timeout=5))
+            except Exception:
+                dead = [p for p in procs if p.exitcode not in (None, 0)]
+                if dead or time.time() - t0 > 1800:
+                    for p in procs:
+                        if p.is_alive():
+                            p.terminate()
+                    raise RuntimeError("oracle worker failed (exit codes %s)" % [p.exitcode for p in procs])
+        for p in procs:
+            p.join(timeout=60)
+        return max(times), n
+    finally:
+        os.unlink(path)
+
+
 def cpu_baseline(iters_per_solve, reps=2):
     from paper_1302_4018_gb300 import synth
 
     U = synth.gauge_links(DIMS, EPS, LINK_SEED, device=_links_device())
-    t_it = oracle_iteration_time(U, reps)
     n_it = iters_per_solve or FP64_ITERS_PER_SOLVE or 100.0
-    return {"value": 1.0 / (t_it * n_it), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d oracle BiCGStab iterations (2 Wilson applications each, numpy FP64, one thread) on one "
-                      "right-hand side of the 32^3x64 workload: %.2f s per iteration, extrapolated to %.1f "
-                      "iterations per solve (the FP64 iteration count of this workload)" % (reps, t_it, n_it)}
+    nproc, model = host_cpu()
+    t_it = oracle_iteration_time(U, reps)
+    t_all, n = oracle_all_cores(U, 1)
+    return {"value": n / (t_all * n_it), "unit": UNIT, "cores": n, "kind": "oracle",
+            "host": {"nproc": nproc, "cpu_model": model},
+            "single_thread": {"value": 1.0 / (t_it * n_it), "unit": UNIT, "cores": 1, "s_per_iteration": t_it},
+            "sample": "the oracle's BiCGStab (2 Wilson applications per iteration, numpy FP64) on the 32^3x64 "
+                      "workload: %d processes at once, one right-hand side and one iteration each (%.1f s per "
+                      "iteration, slowest process), and one process alone (%d iterations, %.1f s each); both "
+                      "extrapolated to %.1f iterations per solve (the FP64 iteration count of this workload)"
+                      % (n, t_all, reps, t_it, n_it)}
 
 
 def run_reference(args):
@@ -664,6 +755,58 @@ def _laplacian_exact_trace(dims, mass):
     k = [2 * np.pi * np.arange(L) / L for L in dims]
     lam = mass + sum(4 * np.sin(kk / 2) ** 2 for kk in np.meshgrid(*k, indexing="ij"))
     return float(np.sum(1.0 / lam))
+
+
+def run_config2(args):
+    """The 16^4 Wilson-Dirac configuration: kappa 0.115, eps 0.3, link seed 1002, z_0 seed 2002,
+    s = 1..512 probing vectors with full dilution (6144 right-hand sides), BiCGStab to 1e-10 in the
+    chosen precision on the even-odd Schur complement; one step = the whole sequence in one call."""
+    import torch
+
+    from paper_1302_4018_gb300 import hprobe, synth
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = hprobe.Context(0, stream=stream.cuda_stream)
+    dims = (16, 16, 16, 16)
+    U = synth.gauge_links(dims, 0.3, 1002, device="cuda:0")
+    links = torch.from_numpy(U.view(np.float64).reshape(-1)).to("cuda:0")
+    del U
+    op = ctx.make_operator(hprobe.OP_WILSON, 0.0, 0.115, links, None)
+    S = args.config2_vectors
+    opts = ctx.make_opts(args.precision, z0_seed=2002, rhs_block=args.rhs_block * 4, even_odd=args.even_odd,
+                         eo_kernel=args.eo_kernel)
+    for _ in range(max(1, args.warmup)):
+        ctx.trace_inv(op, dims, 8, 1e-10, opts)
+    clocks = Clocks(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        T, _, st = ctx.trace_inv(op, dims, S, 1e-10, opts)
+        stats.append(st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    rhs = sum(st["rhs_solved"] for st in stats)
+    pts = [s for s in (1, 2, 32, 64, 128, 256, 512, 1024) if s <= S]
+    out = {"metric": "probing solves/s (16^4 Wilson, true residual 1e-10, s = 1..%d)" % S,
+           "value": rhs / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": {"fp32": "f32", "fp16": "f16-storage/f32-math", "bf16": "bf16-storage/f32-math",
+                     "fp64": "f64"}[args.precision] + " + f64-class true residual",
+           "data": "synthetic: SU(3) links exp(i eps H), seeded",
+           "config": {"workload": "16^4 Wilson-Dirac, kappa 0.115, eps 0.3, %d probes x 12 dilutions, BiCGStab %s "
+                                  "on the even-odd Schur complement, tol 1e-10" % (S, args.precision),
+                      "rhs_block": args.rhs_block * 4},
+           "clocks": clk,
+           "solver": {"rhs": rhs, "iters_per_solve": sum(st["iterations_total"] for st in stats) / max(1, rhs),
+                      "max_true_residual": max(st["max_true_residual"] for st in stats)},
+           "T_s": {str(s): [float(T[s - 1].real), float(T[s - 1].imag)] for s in pts}}
+    print(json.dumps(out), flush=True)
 
 
 def run_study(args):
@@ -958,7 +1101,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "batch", "grad", "variance", "sparse", "study"])
+                    choices=["headline", "batch", "grad", "variance", "sparse", "study", "config2"])
+    ap.add_argument("--config2-vectors", type=int, default=512)
     ap.add_argument("--study-seeds", type=int, default=32, help="z_0 draws of the Wilson speed-up ratio")
     ap.add_argument("--study-wilson-vectors", type=int, default=512)
     ap.add_argument("--study-lap-vectors", type=int, default=1024)
@@ -977,6 +1121,11 @@ def main():
                          "not the benchmark workload)")
     ap.add_argument("--csw", type=float, default=0.0,
                     help="clover coefficient of the Clover-Wilson operator (0: plain Wilson, the headline)")
+    ap.add_argument("--eo-kernel", type=int, default=0,
+                    help="even-odd V / T step kernels (hp_solver_opts.eo_kernel; 0: autotuned)")
+    ap.add_argument("--rhs-per-thread", type=int, default=0,
+                    help="hp_solver_opts.rhs_per_thread (with --eo-kernel 1: 1 = 12-real links, 101 = 18-real)")
+    ap.add_argument("--use-graph", type=int, default=0, help="replay the iteration chunks from CUDA graphs")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-dslash", action="store_true")
     args = ap.parse_args()
@@ -996,6 +1145,8 @@ def main():
         run_sparse(args)
     elif args.workload == "study":
         run_study(args)
+    elif args.workload == "config2":
+        run_config2(args)
     else:
         run_ours(args)
 

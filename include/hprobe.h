@@ -183,10 +183,11 @@ typedef struct {
                                residual is still that of the full system)                   */
     int32_t probe_kind;     /* hp_probe_kind: the probing sequence (0: hierarchical probing) */
     int32_t eo_kernel;      /* even-odd iteration in FP32 / FP16 / BF16: the V and T step kernels --
-                               1 one right-hand side per thread, 3 or 4 two right-hand sides per
+                               1 one right-hand side per thread; 3, 4 two right-hand sides per
                                thread (packed FP32x2 arithmetic) with 3 or 4 resident blocks of 128
-                               threads per SM; 0: the fastest of the three, timed on the problem's
-                               largest lattice and cached in the context                    */
+                               threads per SM; 13, 14 the same with FP32 links; 5 the two-sided
+                               even-site kernel with the one-sided odd-site kernel; 0: the fastest,
+                               timed on the problem's largest lattice and cached in the context */
     int32_t reserved[1];
 } hp_solver_opts;
 

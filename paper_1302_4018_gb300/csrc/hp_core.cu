@@ -143,6 +143,16 @@ hp_status hp_device_view(hp_ctx* ctx, const void* p, size_t bytes, const char* n
   return HP_OK;
 }
 
+hp_status hp_stream_view(hp_ctx* ctx, const void* p, size_t bytes, const char* name, const void** out) {
+  cudaPointerAttributes a;
+  if (p && cudaPointerGetAttributes(&a, p) == cudaSuccess && a.type == cudaMemoryTypeHost && a.devicePointer) {
+    *out = a.devicePointer;   // pinned host memory mapped into the device: read in place
+    return HP_OK;
+  }
+  cudaGetLastError();
+  return hp_device_view(ctx, p, bytes, name, out);
+}
+
 // ---------------------------------------------------------------- profiling
 static cudaEvent_t take_event(hp_ctx* ctx) {
   if (!ctx->event_pool.empty()) {

@@ -166,6 +166,51 @@ __device__ __forceinline__ float load_norm(FieldPtr f, int Vmax, int slot, int h
   else return __ldg(f.nrm + (size_t)slot * Vmax + h);
 }
 
+// ---------------------------------------------------------------- asynchronous copies to shared memory
+// The odd-site kernels need the site's own input (and r^) only after the hop: the thread copies
+// them to its slice of shared memory with cp.async before the hop, so the loads overlap the hop's
+// arithmetic without holding registers.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// one stored spinor in shared memory: its 16-byte words and its norm
+template <int SPR>
+struct SmemSpinor {
+  static constexpr int W = SPR == PR32 ? 6 : 3;
+  uint4 w[W];
+  float n;
+  __device__ __forceinline__ void fetch(FieldPtr f, int Vmax, int slot, int h) {
+    const uint4* b = (const uint4*)f.p + (size_t)slot * W * Vmax + h;
+#pragma unroll
+    for (int k = 0; k < W; ++k) cp_async16(&w[k], b + (size_t)k * Vmax);
+    if (SPR == PR32) n = 1.0f;
+    else cp_async4(&n, f.nrm + (size_t)slot * Vmax + h);
+  }
+  // components 4k .. 4k+3 in FP32, without the norm
+  __device__ __forceinline__ void comp4(int k, float (&re)[4], float (&im)[4]) const {
+    if constexpr (SPR == PR32) {
+      const float4 u = *reinterpret_cast<const float4*>(&w[2 * k]), v = *reinterpret_cast<const float4*>(&w[2 * k + 1]);
+      re[0] = u.x, im[0] = u.y, re[1] = u.z, im[1] = u.w, re[2] = v.x, im[2] = v.y, re[3] = v.z, im[3] = v.w;
+    } else {
+      RawHalf<SPR> r;
+      r.c[0] = w[k];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        re[j] = r.re(j);
+        im[j] = r.im(j);
+      }
+    }
+  }
+};
+
 // ---------------------------------------------------------------- spin projection
 // (1 -+ g_mu) psi = [h ; -+A^H h] with h = psi_up -+ A psi_dn (chiral basis): for the upper spin
 // s in {0, 1}, h_s = p_s + coef p_t with partner spin t and coef in {+1, -1, +i, -i}
@@ -398,10 +443,9 @@ __device__ __forceinline__ void lane_of(const c2 (&acc)[12], int L, cplx<float> 
 
 // ---- even sites: mid = A_e^-1 hop(in_o) for two right-hand sides per thread (MINB: resident blocks of
 // NT threads the register budget allows, 4 -> 128 registers, 3 -> 168; chosen by timing)
-template <int SPR, int NT, int MINB, bool CL>
+template <int SPR, int LPR, int NT, int MINB, bool CL>
 __global__ void __launch_bounds__(NT, MINB) k_eo2_even(WArgs a, FieldPtr in, FieldPtr mid, int nslots) {
   EO2_PREAMBLE(MASK_RUN)
-  constexpr int LPR = SPR == PR32 ? PR32 : PR16;
   for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
     const int h = tile * NT + threadIdx.x;
     if (h >= nsite) continue;
@@ -463,27 +507,51 @@ __device__ __forceinline__ void reduce_pair(const float (&v)[2][NQ], double* par
 
 // ---- odd sites: out = A_o in - k^2 hop(mid) with the solver epilogues, two right-hand sides per thread
 //   EPI_V: v = S p, (r^, v), alpha       EPI_T: t = S s, (t, s), (t, t), omega
-template <int SPR, int NT, int MINB, int EPI, bool CL>
+template <int SPR, int LPR, int NT, int MINB, int EPI, bool CL, int TPB>
 __global__ void __launch_bounds__(NT, MINB) k_eo2_odd(WArgs a, FieldPtr in, FieldPtr mid, FieldPtr out, int nslots) {
-  EO2_PREAMBLE(MASK_RUN)
-  constexpr int LPR = SPR == PR32 ? PR32 : PR16;
+  // TPB consecutive tiles per block (one reduction per TPB tiles; consecutive, so that the sweep
+  // of the lattice stays one front and the neighbours of a tile are still in L2)
+  const int pair = blockIdx.z * gridDim.x + blockIdx.x;
+  const int s0 = 2 * pair, s1 = 2 * pair + 1;
+  if (s0 >= nslots) return;
+  const bool on0 = eo_mask(a.st + s0, MASK_RUN), on1 = s1 < nslots && eo_mask(a.st + s1, MASK_RUN);
+  if (!on0 && !on1) return;
+  const int sa = on0 ? s0 : s1, sb = (on0 && on1) ? s1 : sa;
+  const bool two = sb != sa;
+  const LatGeom g = a.lats[a.st[sa].lat];
+  const int nsite = g.V >> 1;
+  const int ntiles = (nsite + NT - 1) / NT;
+  const int nchunks = (ntiles + TPB - 1) / TPB;
+  if ((int)blockIdx.y >= nchunks) return;
+  const int nparts = min((int)gridDim.y, nchunks);
   constexpr int NQ = EPI == EPI_V ? 2 : 3;
+  constexpr int NF = 1;   // own-site field prefetched: the input (r^ of the V step is loaded after the hop)
+  // (binary16 fields: 16 KB per field and block; the FP32 iteration's would exceed the 48 KB of
+  // static shared memory, so it loads them after the hop)
+  constexpr bool PREF = SPR != PR32;
+  __shared__ SmemSpinor<SPR> own[PREF ? NT : 1][NF][2];
   float dots[2][NQ];
 #pragma unroll
   for (int L = 0; L < 2; ++L)
 #pragma unroll
     for (int q = 0; q < NQ; ++q) dots[L][q] = 0.f;
   const float mk2 = -(float)(g.kappa * g.kappa);
-  for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
+  for (int tile = blockIdx.y * TPB; tile < min(ntiles, (int)(blockIdx.y + 1) * TPB); ++tile) {
     const int h = tile * NT + threadIdx.x;
     if (h >= nsite) continue;
     int x[4], st[4];
     const int site = eo_site(g, h, 1, x, st);
+    const bool clov = CL && g.clover;
+    if (PREF && !clov) {
+      own[threadIdx.x][0][0].fetch(in, a.Vmax, sa, h);
+      own[threadIdx.x][0][1].fetch(in, a.Vmax, sb, h);
+      cp_async_commit();
+    }
     c2 acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k].re = acc[k].im = make_float2(0.f, 0.f);
     eo_hop2<SPR, LPR>(g, mid, a.Vmax, sa, sb, site, x, st, bc2(mk2), acc);
-    if (CL && g.clover) {   // the 6x6 clover blocks need the whole spinor: lane by lane
+    if (clov) {   // the 6x6 clover blocks need the whole spinor: lane by lane
 #pragma unroll
       for (int L = 0; L < 2; ++L) {
         if (L == 1 && !two) break;
@@ -520,16 +588,23 @@ __global__ void __launch_bounds__(NT, MINB) k_eo2_odd(WArgs a, FieldPtr in, Fiel
     }
     // diagonal term and dot products four components at a time (few live registers):
     // v = acc + d n c (c the stored input, n its norm), then (r^, v) or (v, n c) and (v, v)
+    if (PREF) cp_async_wait_all();
+    const SmemSpinor<SPR>(&my)[NF][2] = own[PREF ? threadIdx.x : 0];
     const float dg = site_diag<float>(g, site);
-    const f2 ncs = make_float2(load_norm<SPR>(in, a.Vmax, sa, h), load_norm<SPR>(in, a.Vmax, sb, h));
+    const f2 ncs = PREF ? make_float2(my[0][0].n, my[0][1].n) : make_float2(1.0f, 1.0f);
     const f2 nd = mul2(bc2(dg), ncs);
     f2 q0 = make_float2(0.f, 0.f), q1 = q0, q2 = q0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       float ar[4], ai[4], br[4], bi[4];
-      load_comp4<SPR>(in, a.Vmax, sa, h, k, ar, ai);
-      load_comp4<SPR>(in, a.Vmax, sb, h, k, br, bi);
       float rr[2][4], ri[2][4];
+      if (PREF) {
+        my[0][0].comp4(k, ar, ai);
+        my[0][1].comp4(k, br, bi);
+      } else {
+        load_comp4<SPR>(in, a.Vmax, sa, h, k, ar, ai);
+        load_comp4<SPR>(in, a.Vmax, sb, h, k, br, bi);
+      }
       if (EPI == EPI_V) {
         load_comp4<SPR>(a.rh, a.Vmax, sa, h, k, rr[0], ri[0]);
         load_comp4<SPR>(a.rh, a.Vmax, sb, h, k, rr[1], ri[1]);

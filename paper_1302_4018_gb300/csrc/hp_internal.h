@@ -204,6 +204,10 @@ hp_status hp_get_lattice(hp_ctx* ctx, const std::vector<int64_t>& dims, LatticeS
 // host/device buffers: returns a device pointer to the data (copying host data
 // into workspace `name` when needed)
 hp_status hp_device_view(hp_ctx* ctx, const void* p, size_t bytes, const char* name, const void** out);
+// A view of p for ONE streaming read by a kernel: device memory as is; pinned host memory that is
+// mapped into the device address space (cudaHostAlloc, cudaHostRegister) is read in place over the
+// host link, with no staging copy; other host memory is copied like hp_device_view.
+hp_status hp_stream_view(hp_ctx* ctx, const void* p, size_t bytes, const char* name, const void** out);
 bool hp_is_device_ptr(const void* p);
 
 // operator preparation (hp_wilson.cu): converts links to the internal

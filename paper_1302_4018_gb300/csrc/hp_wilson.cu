@@ -108,7 +108,8 @@ hp_status hp_prepare_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom* g, cons
   const size_t V = (size_t)g->V;
   std::string base(tag);
   const void* src = nullptr;
-  HP_TRY(hp_device_view(ctx, op->links, sizeof(double) * 72 * V, (base + ".links_in").c_str(), &src));
+  // read once, by the conversion below: pinned host links stream in over the host link directly
+  HP_TRY(hp_stream_view(ctx, op->links, sizeof(double) * 72 * V, (base + ".links_in").c_str(), &src));
   void *u64 = nullptr, *u32 = nullptr, *u16 = nullptr, *u32f = nullptr, *u32g = nullptr, *u16f = nullptr,
        *u16g = nullptr, *u32fl = nullptr, *u32gl = nullptr;
   HP_TRY(hp_ws(ctx, (base + ".U64").c_str(), sizeof(double2) * 36 * V, &u64));   // always: true residual

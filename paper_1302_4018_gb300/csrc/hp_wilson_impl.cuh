@@ -892,27 +892,34 @@ __device__ __forceinline__ void eo_hop(const LatGeom& g, FieldPtr in, int Vs, in
 __device__ __forceinline__ double leading_part(double v) { return v; }
 __device__ __forceinline__ double leading_part(ffl v) { return (double)v.hi; }
 
-// slot of a stencil block (same grid as k_wds, one slot per block)
-#define EO_PREAMBLE(MASK)                                                 \
-  const int slot = blockIdx.z * gridDim.x + blockIdx.x;                   \
-  if (slot >= nslots) return;                                             \
-  SlotState* S = a.st + slot;                                             \
-  if (!eo_mask(S, MASK)) return;                                          \
-  const LatGeom g = a.lats[S->lat];                                       \
-  const int nsite = g.V >> 1;                                             \
-  const int ntiles = (nsite + NT - 1) / NT;                               \
-  if ((int)blockIdx.y >= ntiles) return;                                  \
-  const int nparts = min((int)gridDim.y, ntiles);                         \
-  double* part = a.part + (size_t)slot * 4 * a.gy;                        \
-  (void)nparts;                                                           \
-  (void)part;
+// The slots of an even-odd launch.  LOOP = false: one slot per block (grid x/z: the slot, y: the
+// tile), for launches that serve most slots; LOOP = true: one block per tile (grid 1 x tiles) that
+// loops over the slots its mask selects, for launches that serve a few slots at a time (the exact
+// and group steps, fresh starts): an unselected slot then costs a flag test, not a block.  Every
+// block of a tile reads a slot's mask before that slot's finalisation (the last block to finish
+// it), so the loop is uniform over the block.
+#define EO_SLOTS_BEGIN(MASK, LOOP)                                                  \
+  const int s_first = (LOOP) ? 0 : (int)(blockIdx.z * gridDim.x + blockIdx.x);     \
+  const int s_last = (LOOP) ? nslots : min(s_first + 1, nslots);                    \
+  for (int slot = s_first; slot < s_last; ++slot) {                                 \
+    SlotState* S = a.st + slot;                                                     \
+    if (!eo_mask(S, MASK)) continue;                                                \
+    const LatGeom g = a.lats[S->lat];                                               \
+    const int nsite = g.V >> 1;                                                     \
+    const int ntiles = (nsite + NT - 1) / NT;                                       \
+    if ((int)blockIdx.y >= ntiles) continue;                                        \
+    const int nparts = min((int)gridDim.y, ntiles);                                 \
+    double* part = a.part + (size_t)slot * 4 * a.gy;                                \
+    (void)nparts;                                                                   \
+    (void)part;
+#define EO_SLOTS_END }
 
 // ---- even sites: mid = d_e^-1 hop(in_o)  (register caps: six resident blocks, <= 85 registers, for
 // the iteration's launches -- left alone the compiler takes 160 and halves the warps; four for the
 // group update)
 template <int SIN, int LPR, int REC, int SOUT, int NT, int MASK, bool CL>
 __global__ void __launch_bounds__(NT, SIN == PR64 ? 2 : (MASK == MASK_RUN ? 6 : 4)) k_eo_even(WArgs a, FieldPtr in, FieldPtr mid, int nslots) {
-  EO_PREAMBLE(MASK)
+  EO_SLOTS_BEGIN(MASK, MASK != MASK_RUN)
   typedef typename Real_of<SIN>::T R;   // FP64 for the FP64 solver, FP32 arithmetic otherwise
   for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
     const int h = tile * NT + threadIdx.x;
@@ -937,6 +944,7 @@ __global__ void __launch_bounds__(NT, SIN == PR64 ? 2 : (MASK == MASK_RUN ? 6 : 
     eo_hop<SIN, LPR, REC, R>(g, in, a.Vmax, slot, site, x, st, inv, acc);
     SpinorIO<SOUT>::store(mid, a.Vmax, slot, h, acc);
   }
+  EO_SLOTS_END
 }
 
 // ---- odd sites: out = d_o in - k^2 hop(mid), with the solver epilogues
@@ -951,7 +959,7 @@ enum { EPI_G = 3 };
 #define EO_ODD_MINB(SIN, REC) ((SIN) == PR64 ? 2 : (REC) == 18 ? 6 : 5)
 template <int SIN, int SMID, int LPR, int REC, int NT, int EPI, bool CL>
 __global__ void __launch_bounds__(NT, EO_ODD_MINB(SIN, REC)) k_eo_odd(WArgs a, FieldPtr in, FieldPtr mid, FieldPtr out, int nslots) {
-  EO_PREAMBLE(EPI == EPI_G ? MASK_GROUP : MASK_RUN)
+  EO_SLOTS_BEGIN(EPI == EPI_G ? MASK_GROUP : MASK_RUN, EPI == EPI_G)
   typedef typename Real_of<SIN>::T R;   // FP64 for the FP64 solver, FP32 arithmetic otherwise
   constexpr int NQ = EPI == EPI_V ? 2 : 3;
   R dots[NQ];
@@ -1036,6 +1044,7 @@ __global__ void __launch_bounds__(NT, EO_ODD_MINB(SIN, REC)) k_eo_odd(WArgs a, F
       a.cnt[slot] = 0;
     }
   }
+  EO_SLOTS_END
 }
 
 // the exact steps: at least EO_X_MINB resident blocks of 128 threads (register cap)
@@ -1043,7 +1052,7 @@ __global__ void __launch_bounds__(NT, EO_ODD_MINB(SIN, REC)) k_eo_odd(WArgs a, F
 // ---- exact step 1: x_e = d_e^-1 (b_e + k hop(x_o))   (FP64 or float-float)
 template <int PX, int NT>
 __global__ void __launch_bounds__(NT, EO_X_MINB) k_eo_x1(WArgs a, int nslots) {
-  EO_PREAMBLE(MASK_EXACT)
+  EO_SLOTS_BEGIN(MASK_EXACT, true)
   typedef typename Real_of<PX>::T R;
   const int comp = S->a, m = S->m;
   FieldPtr xo = PX == PR64 ? FieldPtr{a.x, nullptr, nullptr} : a.xff;
@@ -1079,12 +1088,13 @@ __global__ void __launch_bounds__(NT, EO_X_MINB) k_eo_x1(WArgs a, int nslots) {
     }
     SpinorIO<PX>::store(xe, a.Vmax, slot, h, acc);
   }
+  EO_SLOTS_END
 }
 
 // ---- exact step 2: r_o = b_o - d_o x_o + k hop(x_e); a fresh slot also sets r^ = p = r
 template <int SPR, int PX, int NT>
 __global__ void __launch_bounds__(NT, EO_X_MINB) k_eo_x2(WArgs a, int nslots) {
-  EO_PREAMBLE(MASK_EXACT)
+  EO_SLOTS_BEGIN(MASK_EXACT, true)
   typedef typename Real_of<PX>::T R;
   typedef typename Real_of<SPR>::T RS;
   const int comp = S->a, m = S->m;
@@ -1165,6 +1175,7 @@ __global__ void __launch_bounds__(NT, EO_X_MINB) k_eo_x2(WArgs a, int nslots) {
       }
     }
   }
+  EO_SLOTS_END
 }
 
 // ---- init: x_o = 0, e = 0, ||b||^2 over the whole lattice; the exact steps then set
@@ -1250,7 +1261,7 @@ __global__ void __launch_bounds__(NT) k_eo_init(WArgs a, int nslots) {
 // tolerance is handed to the exact steps, which certify or continue it.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_eo_src(WArgs a, int nslots) {
-  EO_PREAMBLE(MASK_FRESH)
+  EO_SLOTS_BEGIN(MASK_FRESH, true)
   const int comp = S->a, m = S->m;
   for (int tile = blockIdx.y; tile < ntiles; tile += gridDim.y) {
     const int h = tile * NT + threadIdx.x;
@@ -1271,11 +1282,12 @@ __global__ void __launch_bounds__(NT) k_eo_src(WArgs a, int nslots) {
     }
     SpinorIO<PR32>::store(a.mid32, a.Vmax, slot, h, z);
   }
+  EO_SLOTS_END
 }
 
 template <int SPR, int NT>
 __global__ void __launch_bounds__(NT) k_eo_r0(WArgs a, int nslots) {
-  EO_PREAMBLE(MASK_FRESH)
+  EO_SLOTS_BEGIN(MASK_FRESH, true)
   typedef typename Real_of<SPR>::T RS;
   const int comp = S->a, m = S->m;
   const float kap = (float)g.kappa;
@@ -1321,6 +1333,7 @@ __global__ void __launch_bounds__(NT) k_eo_r0(WArgs a, int nslots) {
       a.cnt[slot] = 0;
     }
   }
+  EO_SLOTS_END
 }
 
 // one component of the converged solution at a full site, from the parity fields
@@ -1438,7 +1451,8 @@ struct WilsonEngine {
   bool clover = false; // some lattice of the problem carries the clover term; set before setup
   WArgs a;
   int nslots, gy, gyb, rpt = 1, variant = 10;
-  int eo_kernel = 4;   // even-odd V / T steps: 1 one right-hand side per thread, 3 / 4 pair kernels
+  int eo_kernel = 4;   // even-odd V / T steps: 1 one right-hand side per thread, 10 L + B pair kernels
+                       // (B = 3 or 4 resident blocks per SM, L = 1: FP32 links), 5 pair even + single odd
   int big_lat = 0;     // index of the largest lattice of the problem (set before setup)
   int kernels_per_iteration() const { return eo ? (SPR == PR64 ? 10 : 12) : (SPR == PR64 ? 7 : 8); }
   // streaming kernels: grid-stride with 8 blocks per SM per slot (few partial sums and atomic tickets);
@@ -1521,7 +1535,7 @@ struct WilsonEngine {
       rpt = 1;
       if (SPR != PR64) {
         const int k = o.eo_kernel;
-        if (k == 1 || k == 3 || k == 4) eo_kernel = k;
+        if (k == 1 || k == 3 || k == 4 || k == 5 || k == 13 || k == 14) eo_kernel = k;
         else HP_TRY(tune_eo(gbig));
       }
     }
@@ -1530,12 +1544,15 @@ struct WilsonEngine {
   // ---- even-odd steps
   // grid of the even-odd kernels: one slot per block along x/z, tiles of NT sites along y
   dim3 eo_grid() const { return stencil_grid(variant, nslots, gy); }
+  // masked launches that serve a few slots (exact and group steps, fresh starts): one block per
+  // tile looping over the selected slots
+  dim3 tile_grid() const { return dim3(1, gy, 1); }
   template <int REC, bool CL>
   hp_status eo_schur(int which) {   // which: 0 v = S p, 1 t = S s, 2 group update with e
     dim3 gr = eo_grid();
     constexpr int LPR = LinkPrecOf<SPR>::v;
     if constexpr (SPR != PR64) {   // two right-hand sides per thread, all slot pairs of a tile together
-      if (which < 2 && eo_kernel >= 3) return eo_kernel == 3 ? eo_pair<3, CL>(which) : eo_pair<4, CL>(which);
+      if (which < 2 && eo_kernel >= 3) return eo_pair_v<CL>(which);
     }
     if (which == 0) {
       {
@@ -1556,38 +1573,76 @@ struct WilsonEngine {
     } else if (SPR != PR64) {
       {
         ProfScope ps(ctx, "k_eo_even<grp>");
-        k_eo_even<EPR, PR32, 12, PR32, NT, MASK_GROUP, CL><<<gr, NT, 0, ctx->stream>>>(a, a.e, a.mid32, nslots);
+        k_eo_even<EPR, PR32, 12, PR32, NT, MASK_GROUP, CL><<<tile_grid(), NT, 0, ctx->stream>>>(a, a.e, a.mid32, nslots);
       }
       HP_LAUNCH_CHECK();
       ProfScope ps(ctx, "k_eo_odd<grp>");
-      k_eo_odd<EPR, PR32, PR32, 12, NT, EPI_G, CL><<<gr, NT, 0, ctx->stream>>>(a, a.e, a.mid32, a.rg, nslots);
+      k_eo_odd<EPR, PR32, PR32, 12, NT, EPI_G, CL><<<tile_grid(), NT, 0, ctx->stream>>>(a, a.e, a.mid32, a.rg, nslots);
     }
     HP_LAUNCH_CHECK();
     return HP_OK;
   }
-  // the V (which 0) or T (1) step with the pair kernels under a register budget of MINB blocks per SM
-  template <int MINB, bool CL>
+  // the V (which 0) or T (1) step with the pair kernels under a register budget of MINB blocks per SM,
+  // links in LPR (binary16, or FP32: no conversions); the odd-site kernels sweep TPB tiles per block
+  // (one partial-sum reduction per TPB tiles)
+  template <int LPR, int MINB, bool CL>
   hp_status eo_pair(int which) {
     static_assert(SPR != PR64, "the pair kernels serve the FP32 / FP16 / BF16 iteration");
-    const dim3 g2((nslots + 1) / 2, gy, 1);
+    constexpr int TPB = 2;
+    const dim3 g2((nslots + 1) / 2, gy, 1), g2o((nslots + 1) / 2, (gy + TPB - 1) / TPB, 1);
     FieldPtr in = which == 0 ? a.p : a.s, out = which == 0 ? a.v : a.t;
     {
       ProfScope ps(ctx, "k_eo_even");
-      k_eo2_even<SPR, NT, MINB, CL><<<g2, NT, 0, ctx->stream>>>(a, in, a.mid, nslots);
+      k_eo2_even<SPR, LPR, NT, MINB, CL><<<g2, NT, 0, ctx->stream>>>(a, in, a.mid, nslots);
     }
     HP_LAUNCH_CHECK();
     if (which == 0) {
       ProfScope ps(ctx, SPR == PR32 ? "k_eo_odd_v<fp32>" : SPR == PR16 ? "k_eo_odd_v<fp16>" : "k_eo_odd_v<bf16>");
-      k_eo2_odd<SPR, NT, MINB, EPI_V, CL><<<g2, NT, 0, ctx->stream>>>(a, in, a.mid, out, nslots);
+      k_eo2_odd<SPR, LPR, NT, MINB, EPI_V, CL, TPB><<<g2o, NT, 0, ctx->stream>>>(a, in, a.mid, out, nslots);
     } else {
       ProfScope ps(ctx, SPR == PR32 ? "k_eo_odd_t<fp32>" : SPR == PR16 ? "k_eo_odd_t<fp16>" : "k_eo_odd_t<bf16>");
-      k_eo2_odd<SPR, NT, MINB, EPI_T, CL><<<g2, NT, 0, ctx->stream>>>(a, in, a.mid, out, nslots);
+      k_eo2_odd<SPR, LPR, NT, MINB, EPI_T, CL, TPB><<<g2o, NT, 0, ctx->stream>>>(a, in, a.mid, out, nslots);
     }
     HP_LAUNCH_CHECK();
     return HP_OK;
   }
+  // eo_kernel 5: the even-site pair kernel with the one-right-hand-side odd-site kernel
+  template <bool CL>
+  hp_status eo_mixed(int which) {
+    constexpr int L16 = SPR == PR32 ? PR32 : PR16;
+    const dim3 g2((nslots + 1) / 2, gy, 1), gr = eo_grid();
+    FieldPtr in = which == 0 ? a.p : a.s, out = which == 0 ? a.v : a.t;
+    {
+      ProfScope ps(ctx, "k_eo_even");
+      k_eo2_even<SPR, L16, NT, 4, CL><<<g2, NT, 0, ctx->stream>>>(a, in, a.mid, nslots);
+    }
+    HP_LAUNCH_CHECK();
+    constexpr int LPR = LinkPrecOf<SPR>::v;
+    if (which == 0) {
+      ProfScope ps(ctx, SPR == PR32 ? "k_eo_odd_v<fp32>" : SPR == PR16 ? "k_eo_odd_v<fp16>" : "k_eo_odd_v<bf16>");
+      k_eo_odd<SPR, SPR, LPR, 18, NT, EPI_V, CL><<<gr, NT, 0, ctx->stream>>>(a, in, a.mid, out, nslots);
+    } else {
+      ProfScope ps(ctx, SPR == PR32 ? "k_eo_odd_t<fp32>" : SPR == PR16 ? "k_eo_odd_t<fp16>" : "k_eo_odd_t<bf16>");
+      k_eo_odd<SPR, SPR, LPR, 18, NT, EPI_T, CL><<<gr, NT, 0, ctx->stream>>>(a, in, a.mid, out, nslots);
+    }
+    HP_LAUNCH_CHECK();
+    return HP_OK;
+  }
+  template <bool CL>
+  hp_status eo_pair_v(int which) {   // eo_kernel = 10 L + B: B resident blocks, L = 1 FP32 links
+    constexpr int L16 = SPR == PR32 ? PR32 : PR16;
+    switch (eo_kernel) {
+      case 5: return eo_mixed<CL>(which);
+      case 3: return eo_pair<L16, 3, CL>(which);
+      case 13: return eo_pair<PR32, 3, CL>(which);
+      case 14: return eo_pair<PR32, 4, CL>(which);
+      default: return eo_pair<L16, 4, CL>(which);
+    }
+  }
   // Autotuner of the even-odd iteration kernels: times the V step (k_eo_even + k_eo_odd) of every
-  // variant -- one right-hand side per thread (1), the pair kernels at 3 or 4 resident blocks --
+  // variant -- one right-hand side per thread (1), the pair kernels at 3 or 4 resident blocks with
+  // binary16 or FP32 links (3, 4, 13, 14), the even-site pair kernel with the one-right-hand-side
+  // odd-site kernel (5) --
   // on this engine's fields with all slots marked running (a scratch copy of the slot states), and
   // keeps the fastest per (precision, lattice, slots).
   hp_status tune_eo(const LatGeom& gbig) {
@@ -1617,7 +1672,8 @@ struct WilsonEngine {
     const bool prof = ctx->profiling;
     ctx->profiling = false;
     hp_status status = HP_OK;
-    for (int c : {1, 3, 4}) {
+    for (int c : {1, 3, 4, 5, 13, 14}) {
+      if (SPR == PR32 && c > 10) continue;   // FP32 iteration: FP32 links already
       eo_kernel = c;
       status = eo_step(0);
       if (status != HP_OK) break;
@@ -1651,12 +1707,12 @@ struct WilsonEngine {
     dim3 gr = eo_grid();
     {
       ProfScope ps(ctx, PX == PR64 ? "k_eo_x1<fp64>" : "k_eo_x1<ff>");
-      k_eo_x1<PX, NT><<<gr, NT, 0, ctx->stream>>>(a, nslots);
+      k_eo_x1<PX, NT><<<tile_grid(), NT, 0, ctx->stream>>>(a, nslots);
     }
     HP_LAUNCH_CHECK();
     {
       ProfScope ps(ctx, PX == PR64 ? "k_eo_x2<fp64>" : "k_eo_x2<ff>");
-      k_eo_x2<SPR, PX, NT><<<gr, NT, 0, ctx->stream>>>(a, nslots);
+      k_eo_x2<SPR, PX, NT><<<tile_grid(), NT, 0, ctx->stream>>>(a, nslots);
     }
     HP_LAUNCH_CHECK();
     return HP_OK;
@@ -1693,12 +1749,12 @@ struct WilsonEngine {
         const dim3 gr = eo_grid();
         {
           ProfScope ps(ctx, "k_eo_src");
-          k_eo_src<NT><<<gr, NT, 0, ctx->stream>>>(a, nslots);
+          k_eo_src<NT><<<tile_grid(), NT, 0, ctx->stream>>>(a, nslots);
         }
         HP_LAUNCH_CHECK();
         {
           ProfScope ps(ctx, "k_eo_r0");
-          k_eo_r0<SPR, NT><<<gr, NT, 0, ctx->stream>>>(a, nslots);
+          k_eo_r0<SPR, NT><<<tile_grid(), NT, 0, ctx->stream>>>(a, nslots);
         }
         HP_LAUNCH_CHECK();
       }
