@@ -68,11 +68,13 @@ def source_hash(kernel):
     return h.hexdigest()[:12]
 
 
-# DRAM traffic of one launch with every slot active (24 on 32^3x64), from one ncu capture of the
-# same kernel on 32^3x16 with 12 slots (411.8 MB read + 146.2 MB written): the spinor part scaled
-# by the site-RHS ratio (8x), the links (read once per launch) by the site ratio (4x); valid only
-# for the kernel source it was taken on
-NCU_TRAFFIC = {("k_eo_even", "0f9f8db23114"): {"bytes_all_slots": 4.162e9, "alg_bytes_all_slots": 1048576 * 104 * 24 + 4 * 2097152 * 36}}
+# DRAM traffic of the dominant kernel per byte of algorithmic work, from one ncu capture of the
+# same kernel (k_eo2_even, the two-right-hand-side even-site stencil) on 32^3x16 with 12 slots:
+# 281.5 MB read + 143.4 MB written per launch against 402.7 MB algorithmic (both parts of the launch
+# -- spinors and links -- grow with the units processed, so the ratio carries over to the 32^3x64
+# launch); valid only for the kernel source it was taken on
+NCU_TRAFFIC = {("k_eo_even", "9b33a4878f26"): {"bytes_all_slots": 281.5e6 + 143.4e6,
+                                      "alg_bytes_all_slots": 262144 * 104 * 12 + 4 * 524288 * 36}}
 
 
 class Clocks:
