@@ -174,3 +174,25 @@ def test_even_odd_request_on_an_odd_extent_iterates_the_full_lattice(ctx, hp, di
     T_ref = E.trace_prefix(E.wilson_quadratures(dims, U, 0.12, 0, 3, 7, method="dense"))
     assert np.all(np.abs(T - T_ref) <= 1e-9 * np.abs(T_ref)), (T, T_ref)
     assert st["max_true_residual"] <= 1e-10
+
+
+def test_trace_prefix_of_gathered_blocks_equals_one_call(ctx, hp):
+    """The multi-rank path on one GPU: two probe blocks solved by separate calls (the second
+    without the first's quadratures, as another rank would), concatenated, and the prefix
+    formed by hp_trace_prefix, against one call over the whole sequence."""
+    dims = (4, 4, 4, 8)
+    U = synth.gauge_links(dims, 0.3, 41)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.12, dev(U.view(np.float64).reshape(-1)), None)
+
+    def opts(first):
+        return ctx.make_opts("fp64", z0_seed=9, first=first, even_odd=1)
+
+    T1, q1, _ = ctx.trace_inv(op, dims, 6, 1e-12, opts(0), q_inout=np.zeros(6, dtype=np.complex128))
+    _, qa, _ = ctx.trace_inv(op, dims, 3, 1e-12, opts(0), q_inout=np.zeros(3, dtype=np.complex128))
+    _, qb, _ = ctx.trace_inv(op, dims, 6, 1e-12, opts(3), q_inout=np.zeros(6, dtype=np.complex128))
+    gathered = np.concatenate([qa, qb[3:]])
+    assert np.allclose(gathered, q1, rtol=1e-13, atol=0)
+    assert ctx.trace_prefix(q1).tobytes() == T1.tobytes()       # same kernel, same order
+    Tg = ctx.trace_prefix(gathered)
+    assert np.allclose(Tg, T1, rtol=1e-13, atol=0)
+    assert np.allclose(Tg, E.trace_prefix(gathered), rtol=1e-15, atol=0)
