@@ -750,6 +750,15 @@ def run_variance(args):
               "iters_per_solve": st_b["iterations_total"] / max(1, st_b["rhs_solved"]),
               "iters_per_solve_residual_stop": st_res["iterations_total"] / max(1, st_res["rhs_solved"]),
               "T_S": float(Tb[-1].real), "T_S_lower": float(lo[-1]), "T_S_upper": float(hi[-1])}
+    # the same 7 lowest modes computed by the library (Chebyshev-filtered subspace iteration)
+    torch.cuda.synchronize()
+    t_e = time.perf_counter()
+    lam_lib, V_lib, res_lib = ctx.laplacian_eigs(op, dims, 7, tol=1e-10)
+    t_e = time.perf_counter() - t_e
+    P_lib = torch.from_numpy(V_lib).cuda()
+    overlap = torch.linalg.svdvals(P_lib @ evecs.T).min().item()   # cosine of the largest principal angle
+    eigs = {"k": 7, "seconds": t_e, "max_rel_eigenvalue_error": float(np.max(np.abs(lam_lib - lams) / lams)),
+            "max_rel_residual": float(res_lib.max()), "min_cos_principal_angle_to_exact": overlap}
     out = {"metric": "probing solves/s, Section 5.2 variance study (64^3 Laplacian, cond ~100, CG 1e-10)",
            "value": solves / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -757,7 +766,7 @@ def run_variance(args):
            "config": {"workload": "64^3 Laplacian m = 12/99, %d vectors of hierarchical probing (plain and with "
                                   "the 7 lowest modes deflated), natural-order Hadamard and Z_2 noise per z_0 seed, "
                                   "%d seeds" % (S, args.steps)},
-           "exact_trace": exact, "study": study, "quadrature_bounds": bounds}
+           "exact_trace": exact, "study": study, "quadrature_bounds": bounds, "laplacian_eigs": eigs}
     print(json.dumps(out), flush=True)
 
 

@@ -287,6 +287,26 @@ hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, const hp_lat
                                 const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
                                 hp_solve_stats* stats);
 
+/* The k lowest eigenpairs of the shifted Laplacian (real symmetric positive
+ * definite; mass field allowed): the eigenvectors hp_trace_inv_deflated removes
+ * exactly (the paper's conclusions name deflation as the step after probing).
+ * Chebyshev-filtered subspace iteration on a block of b = k + max(8, k/2)
+ * vectors: each sweep applies the degree-12 Chebyshev polynomial in A that
+ * damps [theta_b, lambda_max] (theta_b the block's largest Ritz value,
+ * lambda_max = 16 + mass + max mu(s), Gershgorin), orthonormalises the block
+ * (Cholesky QR, shifted once, then twice plain) and rotates it onto the Ritz
+ * vectors (Rayleigh-Ritz); it stops when each of the k lowest pairs has
+ * ||A v - lambda v|| <= tol lambda.  Everything is FP64; the start block is
+ * seeded (the result is deterministic).  Vectors of an eigenvalue that repeats
+ * across index k are one basis of a subspace the method does not fix.
+ * evecs (host or device, double[k][V], lexicographic sites): orthonormal;
+ * evals (host, double[k]): ascending; resid (host, nullable, double[k]): the
+ * relative residuals reached.  max_sweeps <= 0: 200.
+ * Errors: HP_EINVAL for a Wilson operator, k outside [1, V/2], tol <= 0, NULL
+ * outputs; HP_ENOCONV when max_sweeps pass first (outputs still written). */
+hp_status hp_laplacian_eigs(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k, double tol,
+                            int32_t max_sweeps, double* evecs, double* evals, double* resid);
+
 /* hp_trace_inv plus the derivative of Re T_{s_max} with respect to the
  * per-site mass mu(s) (real):
  *   dT/dmu(s) = -(1/s_max) sum_{m,a} sum_c conj(y_{m,a}(s,c)) x_{m,a}(s,c),  y = A^-H v.

@@ -158,6 +158,14 @@ def laplacian_deflated_quadratures(dims, mass, evecs, first, count, z0_seed, mas
     return np.array([np.vdot(Wp[m], X[m]) for m in range(count)])
 
 
+def laplacian_lowest_eigenpairs(dims, mass, k, mass_field=None):
+    """The k lowest eigenpairs of the shifted Laplacian (the modes deflation removes): the dense
+    matrix of laplacian_dense diagonalised by numpy's symmetric eigensolver; returns (evals [k]
+    ascending, evecs [k][V] orthonormal rows)."""
+    lam, V = np.linalg.eigh(ops.laplacian_dense(dims, mass, mass_field))
+    return lam[:k], np.ascontiguousarray(V[:, :k].T)
+
+
 def deflated_trace_prefix(evals, q) -> np.ndarray:
     """T_s = sum_j 1/lambda_j + (1/s) sum_{m<s} q_m."""
     return float(np.sum(1.0 / np.asarray(evals, dtype=float))) + trace_prefix(q)

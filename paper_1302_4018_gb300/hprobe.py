@@ -45,7 +45,7 @@ EXPORTED = ["hp_ctx_create", "hp_ctx_destroy", "hp_last_error", "hp_ctx_synchron
             "hp_operator_apply", "hp_dslash_bench", "hp_profile_enable", "hp_profile_report",
             "hp_launch_count", "hp_operator_apply_noalloc", "hp_probe_sequence", "hp_trace_inv_bounds",
             "hp_sparse_coloring", "hp_sparse_probe_vectors", "hp_trace_inv_sparse", "hp_trace_inv_deflated",
-            "hp_trace_inv_solutions", "hp_trace_prefix", "hp_schur_apply"]
+            "hp_trace_inv_solutions", "hp_trace_prefix", "hp_schur_apply", "hp_laplacian_eigs"]
 
 
 class Lattice(C.Structure):
@@ -120,6 +120,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                                              C.POINTER(SolverOpts), I64, P, P, P, C.POINTER(SolveStats)]),
         "hp_trace_prefix": (C.c_int, [P, I64, P, P]),
         "hp_schur_apply": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I64, I32, P, P]),
+        "hp_laplacian_eigs": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I32, D, I32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -287,6 +288,18 @@ class Context:
         _check(lib().hp_schur_apply(self._h, C.byref(op), C.byref(make_lattice(dims)), int(nrhs), prec, _ptr(inp),
                                     _ptr(out)))
         return out
+
+    def laplacian_eigs(self, op: Operator, dims, k: int, tol: float = 1e-10, max_sweeps: int = 0, evecs=None):
+        """The k lowest eigenpairs of the Laplacian operator: (evals [k], evecs, resid [k]); evecs is
+        written into the given float64 array / tensor of k * V values (host array by default)."""
+        V = int(np.prod(dims))
+        if evecs is None:
+            evecs = np.zeros((k, V))
+        evals = np.zeros(k)
+        resid = np.zeros(k)
+        _check(lib().hp_laplacian_eigs(self._h, C.byref(op), C.byref(make_lattice(dims)), int(k), float(tol),
+                                       int(max_sweeps), _ptr(evecs), _ptr(evals), _ptr(resid)))
+        return evals, evecs, resid
 
     def trace_inv(self, op: Operator, dims, s_max: int, tol: float, opts: SolverOpts, q_inout=None):
         """Returns (T [s_max] complex, q [s_max] complex or None, stats dict).  ``q_inout``: host

@@ -78,3 +78,67 @@ def test_deflated_errors(ctx, hp):
     with pytest.raises(hp.HProbeError) as e:
         ctx.trace_inv_deflated(opw, dims, Vt, lam, 8, 1e-10, ctx.make_opts("fp64"))
     assert e.value.status == hp.HP_EINVAL
+
+
+# ------------------------------------------------------------------ eigenpairs computed by the library
+def _projector(Vt):
+    return Vt.T @ Vt
+
+
+@pytest.mark.parametrize("dims,mass,k", [((8, 8, 8), 0.1, 7), ((4, 4, 4, 4), 0.3, 9), ((6, 6, 4, 2), 0.2, 1)])
+def test_laplacian_eigs_match_the_oracle(ctx, hp, dims, mass, k):
+    """k at a gap of the spectrum (8^3: the constant mode and the six waves of the first shell;
+    4^4: 1 + 8): eigenvalues within 1e-10, the spanned subspace equal to the oracle's (the
+    eigenvectors of a repeated eigenvalue are a basis the method does not fix)."""
+    op = ctx.make_operator(hp.OP_LAPLACIAN, mass)
+    lam, V, res = ctx.laplacian_eigs(op, dims, k, tol=1e-10)
+    lam_o, V_o = E.laplacian_lowest_eigenpairs(dims, mass, k)
+    assert np.allclose(lam, lam_o, rtol=1e-10, atol=0), (lam, lam_o)
+    assert np.all(res <= 1e-10)
+    assert np.allclose(V @ V.T, np.eye(k), atol=1e-12)
+    assert np.abs(_projector(V) - _projector(V_o)).max() <= 1e-8
+    A = O.laplacian_dense(dims, mass)
+    assert np.abs(A @ V.T - V.T * lam[None, :]).max() <= 1e-9 * lam.max()
+
+
+def test_laplacian_eigs_with_a_mass_field_and_device_output(ctx, hp):
+    """A random mass field splits every degeneracy: each eigenvector agrees with the oracle's up
+    to its sign; the vectors are written to device memory."""
+    dims, mass, k = (4, 4, 4, 4), 0.3, 6
+    from paper_1302_4018_gb300 import synth
+
+    mf = 0.2 * synth.mass_field(dims, 1.0, 77)
+    op = ctx.make_operator(hp.OP_LAPLACIAN, mass, 0.0, None, torch.from_numpy(mf).cuda())
+    out = torch.zeros(k * 256, dtype=torch.float64, device="cuda:0")
+    lam, _, res = ctx.laplacian_eigs(op, dims, k, tol=1e-11, evecs=out)
+    V = out.cpu().numpy().reshape(k, 256)
+    lam_o, V_o = E.laplacian_lowest_eigenpairs(dims, mass, k, mf)
+    assert np.allclose(lam, lam_o, rtol=1e-10, atol=0)
+    assert np.all(res <= 1e-11)
+    for j in range(k):
+        assert abs(abs(V[j] @ V_o[j]) - 1.0) <= 1e-9, j
+
+
+def test_deflation_with_library_eigenvectors(ctx, hp):
+    """Deflated probing with the library's own eigenpairs equals the oracle's deflated estimate
+    with the exact eigenpairs (the deflated subspace is the same)."""
+    dims, mass, k, s = (8, 8, 8), 0.1, 7, 32
+    op = ctx.make_operator(hp.OP_LAPLACIAN, mass)
+    lam, V, _ = ctx.laplacian_eigs(op, dims, k, tol=1e-11)
+    q = np.zeros(s, dtype=np.complex128)
+    T, q, _ = ctx.trace_inv_deflated(op, dims, V, lam, s, 1e-12, ctx.make_opts("fp64", z0_seed=4), q_inout=q)
+    lam_o, V_o = E.laplacian_lowest_eigenpairs(dims, mass, k)
+    To = E.deflated_trace_prefix(lam_o, E.laplacian_deflated_quadratures(dims, mass, V_o.T, 0, s, 4))
+    assert np.abs(T - To).max() <= 1e-9 * np.abs(To).max()
+
+
+def test_laplacian_eigs_errors(ctx, hp):
+    dims = (4, 4, 2, 2)
+    op = ctx.make_operator(hp.OP_LAPLACIAN, 0.3)
+    with pytest.raises(hp.HProbeError) as e:
+        ctx.laplacian_eigs(op, dims, 40)                       # k > V / 2
+    assert e.value.status == hp.HP_EINVAL
+    links = torch.zeros(64 * 72, dtype=torch.float64, device="cuda:0")
+    with pytest.raises(hp.HProbeError) as e:
+        ctx.laplacian_eigs(ctx.make_operator(hp.OP_WILSON, 0.0, 0.1, links), dims, 2)
+    assert e.value.status == hp.HP_EINVAL

@@ -303,3 +303,18 @@ def test_jackknife_of_the_mean_is_the_standard_error():
     _, e_small = E.jackknife(y[:400], lambda a: a.var(ddof=1))
     _, e_big = E.jackknife(y, lambda a: a.var(ddof=1))
     assert 2.0 < e_small / e_big < 5.0
+
+
+def test_lowest_eigenpairs_match_the_fourier_spectrum():
+    """Without a mass field the Laplacian's spectrum is m + sum_j 4 sin^2(pi k_j / L_j) over all
+    wave vectors; the oracle's k lowest pairs carry exactly those values, are orthonormal and
+    satisfy A v = lambda v."""
+    dims, mass = (6, 4, 4), 0.2
+    lam, V = E.laplacian_lowest_eigenpairs(dims, mass, 9)
+    k = [np.arange(L) for L in dims]
+    spec = np.sort((mass + sum(4 * np.sin(np.pi * kk / L) ** 2
+                               for kk, L in zip(np.meshgrid(*k, indexing="ij"), dims))).ravel())
+    assert np.allclose(lam, spec[:9], rtol=0, atol=1e-12)
+    assert np.allclose(V @ V.T, np.eye(9), atol=1e-12)
+    A = O.laplacian_dense(dims, mass)
+    assert np.abs(A @ V.T - V.T * lam[None, :]).max() <= 1e-12
