@@ -69,11 +69,11 @@ def source_hash(kernel):
 
 
 # DRAM traffic of the dominant kernel per byte of algorithmic work, from one ncu capture of the
-# same kernel (k_eo2_even, the two-right-hand-side even-site stencil) on 32^3x16 with 12 slots:
-# 281.5 MB read + 143.4 MB written per launch against 402.7 MB algorithmic (both parts of the launch
-# -- spinors and links -- grow with the units processed, so the ratio carries over to the 32^3x64
-# launch); valid only for the kernel source it was taken on
-NCU_TRAFFIC = {("k_eo_even", "9b33a4878f26"): {"bytes_all_slots": 281.5e6 + 143.4e6,
+# same kernel (k_eo2_even, the two-right-hand-side even-site stencil, eo_kernel 4) on 32^3x16 with
+# 12 slots: 278.3 MB read + 142.6 MB written per launch against 402.7 MB algorithmic (both parts of
+# the launch -- spinors and links -- grow with the units processed, so the ratio carries over to the
+# 32^3x64 launch); valid only for the kernel source it was taken on
+NCU_TRAFFIC = {("k_eo_even", "2cd1ee671099"): {"bytes_all_slots": 278.3e6 + 142.6e6,
                                       "alg_bytes_all_slots": 262144 * 104 * 12 + 4 * 524288 * 36}}
 
 

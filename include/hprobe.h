@@ -186,8 +186,12 @@ typedef struct {
                                1 one right-hand side per thread; 3, 4 two right-hand sides per
                                thread (packed FP32x2 arithmetic) with 3 or 4 resident blocks of 128
                                threads per SM; 13, 14 the same with FP32 links; 5 the two-sided
-                               even-site kernel with the one-sided odd-site kernel; 0: the fastest,
-                               timed on the problem's largest lattice and cached in the context */
+                               even-site kernel with the one-sided odd-site kernel; 6 the even-site
+                               hop on the tensor cores (mma.sync, FP16 x FP16 -> FP32; FP16
+                               iterations of one lattice without the clover term, up to 32 slots,
+                               else 0) with the two-sided odd-site kernel -- slower than 4 on GB300
+                               and never the autotuner's choice; 0: the fastest of 1, 3, 4, 5, 13,
+                               14, timed on the problem's largest lattice and cached in the context */
     int32_t reserved[1];
 } hp_solver_opts;
 
@@ -351,6 +355,27 @@ hp_status hp_trace_inv_batch(hp_ctx* ctx, int32_t nlat, const hp_operator* ops, 
 hp_status hp_sparse_coloring(hp_ctx* ctx, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
                              int32_t max_levels, int32_t* paths, int32_t* radices, int32_t* n_levels);
 
+/* Algorithm 1's own outputs from a colour hierarchy (Section 2.1): perm, the
+ * order Colors2Perm leaves the rows in (the rows of one colour adjacent, level
+ * after level inside every block, the original order inside a block that
+ * stopped), and colorOffsets, the (start, end, level) record of every block
+ * the recursion visits, in the order it visits them (0-based positions of
+ * perm, end inclusive; the matrix itself is (0, n - 1, 1)).
+ * paths / n_levels as hp_sparse_coloring returns them (int32[n_levels][n],
+ * host or device; the colours of a block are 0 .. k - 1).  perm: int32[n],
+ * host or device, perm[k] = the row at position k (NULL: not wanted).
+ * offsets: int32[offsets_cap][3], host or device (NULL: count only);
+ * *n_offsets (host) = the number of blocks, at most 2n - 1.  Under
+ * hp_sparse_coloring's max_levels cap a block of the last coloured level
+ * whose colouring splits it records its colour classes one level deeper,
+ * where the recursion visits them and stops.  Computed on the GPU: the blocks
+ * level by level from the paths, then stable radix sorts.  Errors: HP_EINVAL
+ * for n < 1, n_levels outside [0, 32], no output, a colour outside [0, size of
+ * its block), or more blocks than offsets_cap (*n_offsets then holds the
+ * count). */
+hp_status hp_sparse_ordering(hp_ctx* ctx, int32_t n, const int32_t* paths, int32_t n_levels, int32_t* perm,
+                             int32_t* offsets, int64_t offsets_cap, int64_t* n_offsets);
+
 /* The probing vectors of a colour hierarchy (Section 2.2, Eq. Hperm-general-
  * recursive, with the Fourier factor F_c(l) at every level): vector m has the
  * mixed-radix digits d_l(m) (radix c(l), level 1 least significant) and
@@ -404,11 +429,13 @@ hp_status hp_operator_apply(hp_ctx* ctx, const hp_operator* op, const hp_lattice
  * canonical layout of hp_operator_apply (host or device; the even sites of in
  * are ignored), computed by the kernels and the precision the iteration uses
  * (precision as hp_operator_apply: the input is rounded to that storage, the
- * result returned in FP64).  Errors: HP_EINVAL for a Laplacian, an odd extent
+ * result returned in FP64) and the kernel variant eo_kernel (as
+ * hp_solver_opts.eo_kernel; 0 or an unknown value: the autotuner's choice;
+ * FP64 has one variant).  Errors: HP_EINVAL for a Laplacian, an odd extent
  * or fewer than four dimensions (then some hop joins sites of one parity and
  * the split does not exist), kappa = 0, nrhs outside [1, 65532]. */
 hp_status hp_schur_apply(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t nrhs,
-                         int32_t precision, const double* in, double* out);
+                         int32_t precision, int32_t eo_kernel, const double* in, double* out);
 
 /* y = D x for the Wilson operator in FP64, allocating nothing (the paper has
  * no counterpart: this serves callers that cannot let a library allocate GPU

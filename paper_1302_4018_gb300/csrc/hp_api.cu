@@ -12,8 +12,8 @@
 hp_status hp_apply_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrhs, int prec, const double* in,
                           double* out);
 hp_status hp_apply_laplace(hp_ctx* ctx, LatGeom g, int nrhs, const double* in, double* out);
-hp_status hp_schur_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrhs, int prec, const double* in,
-                          double* out);
+hp_status hp_schur_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrhs, int prec, int eo_kernel,
+                          const double* in, double* out);
 hp_status hp_bench_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int prec, int nrhs, int iters, double* ms,
                           double* bytes, double* flops);
 
@@ -581,7 +581,7 @@ extern "C" hp_status hp_operator_apply(hp_ctx* ctx, const hp_operator* op, const
 }
 
 extern "C" hp_status hp_schur_apply(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int64_t nrhs,
-                                    int32_t precision, const double* in, double* out) {
+                                    int32_t precision, int32_t eo_kernel, const double* in, double* out) {
   HP_TRY(check_ctx(ctx));
   LatGeom g;
   HP_TRY(operator_geom(ctx, op, lat, &g, nullptr));
@@ -597,7 +597,7 @@ extern "C" hp_status hp_schur_apply(hp_ctx* ctx, const hp_operator* op, const hp
     hp_set_error("unknown precision %d", precision);
     return HP_EINVAL;
   }
-  return hp_schur_wilson(ctx, op, g, (int)nrhs, precision, in, out);
+  return hp_schur_wilson(ctx, op, g, (int)nrhs, precision, eo_kernel, in, out);
 }
 
 extern "C" hp_status hp_dslash_bench(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t precision,

@@ -38,8 +38,9 @@ struct RawHalf {
     n = __ldg(f.nrm + (size_t)slot * Vmax + h);
   }
   __device__ __forceinline__ unsigned word(int idx) const {   // complex component idx = 3 spin + colour
-    const uint4& q = c[idx >> 2];
-    return (idx & 3) == 0 ? q.x : (idx & 3) == 1 ? q.y : (idx & 3) == 2 ? q.z : q.w;
+    const uint4& q = c[idx % 3];                               // chunk = colour, word = spin
+    const int j = idx / 3;
+    return j == 0 ? q.x : j == 1 ? q.y : j == 2 ? q.z : q.w;
   }
   // real and imaginary part in FP32
   __device__ __forceinline__ float re(int idx) const;
@@ -142,7 +143,27 @@ struct Raw2<PR32> {
   __device__ __forceinline__ float im_sub(int idx, float b) const { return im(idx) - b; }
 };
 
-// components 4k .. 4k+3 of a stored spinor in FP32, without the per-site norm
+// the canonical component (3 spin + colour) of word j of 16-byte chunk k of a stored spinor:
+// FP32 chunks hold components 4k .. 4k+3, binary16 / bfloat16 chunks colour k of spins 0-3
+template <int SPR>
+__device__ __forceinline__ constexpr int chunk_comp(int k, int j) {
+  return SPR == PR32 ? 4 * k + j : 3 * j + k;
+}
+
+// the four (re, im) binary16 / bfloat16 pairs of one 16-byte chunk in FP32
+template <int SPR>
+__device__ __forceinline__ void chunk_words(const uint4& q, float (&re)[4], float (&im)[4]) {
+  const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float2 v = Half2Ops<SPR>::to_f2(w[j]);
+    re[j] = v.x;
+    im[j] = v.y;
+  }
+}
+
+// words 0-3 of chunk k (FP32: chunks 2k, 2k+1) of a stored spinor in FP32, without the per-site
+// norm: the components chunk_comp<SPR>(k, 0..3)
 template <int SPR>
 __device__ __forceinline__ void load_comp4(FieldPtr f, int Vmax, int slot, int h, int k, float (&re)[4],
                                            float (&im)[4]) {
@@ -151,13 +172,8 @@ __device__ __forceinline__ void load_comp4(FieldPtr f, int Vmax, int slot, int h
     const float4 u = __ldg(b + (size_t)(2 * k) * Vmax), v = __ldg(b + (size_t)(2 * k + 1) * Vmax);
     re[0] = u.x, im[0] = u.y, re[1] = u.z, im[1] = u.w, re[2] = v.x, im[2] = v.y, re[3] = v.z, im[3] = v.w;
   } else {
-    RawHalf<SPR> r;
-    r.c[0] = __ldg((const uint4*)f.p + ((size_t)slot * 3 + k) * Vmax + h);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      re[j] = r.re(j);
-      im[j] = r.im(j);
-    }
+    const uint4 q = __ldg((const uint4*)f.p + ((size_t)slot * 3 + k) * Vmax + h);
+    chunk_words<SPR>(q, re, im);
   }
 }
 template <int SPR>
@@ -194,19 +210,13 @@ struct SmemSpinor {
     if (SPR == PR32) n = 1.0f;
     else cp_async4(&n, f.nrm + (size_t)slot * Vmax + h);
   }
-  // components 4k .. 4k+3 in FP32, without the norm
+  // the components chunk_comp<SPR>(k, 0..3) in FP32, without the norm
   __device__ __forceinline__ void comp4(int k, float (&re)[4], float (&im)[4]) const {
     if constexpr (SPR == PR32) {
       const float4 u = *reinterpret_cast<const float4*>(&w[2 * k]), v = *reinterpret_cast<const float4*>(&w[2 * k + 1]);
       re[0] = u.x, im[0] = u.y, re[1] = u.z, im[1] = u.w, re[2] = v.x, im[2] = v.y, re[3] = v.z, im[3] = v.w;
     } else {
-      RawHalf<SPR> r;
-      r.c[0] = w[k];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        re[j] = r.re(j);
-        im[j] = r.im(j);
-      }
+      chunk_words<SPR>(w[k], re, im);
     }
   }
 };
@@ -611,7 +621,7 @@ __global__ void __launch_bounds__(NT, MINB) k_eo2_odd(WArgs a, FieldPtr in, Fiel
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        c2& t = acc[4 * k + j];
+        c2& t = acc[chunk_comp<SPR>(k, j)];
         const f2 cr = make_float2(ar[j], br[j]), ci = make_float2(ai[j], bi[j]);
         t.re = fma2(nd, cr, t.re);
         t.im = fma2(nd, ci, t.im);

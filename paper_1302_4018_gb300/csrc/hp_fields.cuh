@@ -7,7 +7,10 @@
 //   FP64: 12 chunks of double2 (one complex each)
 //   FP32:  6 chunks of float4  (two complex each)
 //   FP16 / BF16: 3 chunks of uint4 (four complex each, scaled by a per-site
-//         FP32 norm = max |component| so the stored values lie in [-1, 1])
+//         FP32 norm = max |component| so the stored values lie in [-1, 1]);
+//         chunk c holds colour c, its words the spins 0-3 (component 3 s + c),
+//         so that one 16-byte load gives a tensor-core lane the four spins of
+//         one colour
 // Links of one lattice ([4][chunks][V], same coalescing):
 //   FP64: 9 double2 per link (full 3x3)
 //   FP32, 12 reals: 3 float4 per link (rows 1-2); row 3 = conj(row1 x row2)
@@ -249,13 +252,13 @@ struct SpinorIOHalf {
   template <typename R>
   __device__ static __forceinline__ void unpack(const uint4 (&c)[3], float n, cplx<R> (&s)[12]) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 3; ++k) {   // chunk k = colour k, word j = spin j
       float2 a = Half2Ops<PR>::to_f2(c[k].x), b = Half2Ops<PR>::to_f2(c[k].y);
       float2 d = Half2Ops<PR>::to_f2(c[k].z), e = Half2Ops<PR>::to_f2(c[k].w);
-      s[4 * k + 0] = {a.x * n, a.y * n};
-      s[4 * k + 1] = {b.x * n, b.y * n};
-      s[4 * k + 2] = {d.x * n, d.y * n};
-      s[4 * k + 3] = {e.x * n, e.y * n};
+      s[k + 0] = {a.x * n, a.y * n};
+      s[k + 3] = {b.x * n, b.y * n};
+      s[k + 6] = {d.x * n, d.y * n};
+      s[k + 9] = {e.x * n, e.y * n};
     }
   }
   template <typename R>
@@ -295,10 +298,10 @@ struct SpinorIOHalf {
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       uint4 c;
-      c.x = Half2Ops<PR>::from_f2((float)s[4 * k].x * inv, (float)s[4 * k].y * inv);
-      c.y = Half2Ops<PR>::from_f2((float)s[4 * k + 1].x * inv, (float)s[4 * k + 1].y * inv);
-      c.z = Half2Ops<PR>::from_f2((float)s[4 * k + 2].x * inv, (float)s[4 * k + 2].y * inv);
-      c.w = Half2Ops<PR>::from_f2((float)s[4 * k + 3].x * inv, (float)s[4 * k + 3].y * inv);
+      c.x = Half2Ops<PR>::from_f2((float)s[k].x * inv, (float)s[k].y * inv);
+      c.y = Half2Ops<PR>::from_f2((float)s[k + 3].x * inv, (float)s[k + 3].y * inv);
+      c.z = Half2Ops<PR>::from_f2((float)s[k + 6].x * inv, (float)s[k + 6].y * inv);
+      c.w = Half2Ops<PR>::from_f2((float)s[k + 9].x * inv, (float)s[k + 9].y * inv);
       b[(size_t)k * Vmax] = c;
     }
     f.nrm[(size_t)slot * Vmax + site] = m;

@@ -384,6 +384,7 @@ struct LaplaceEngine {
   LArgs a;
   int nslots, gy;
   int big_lat = 0;   // index of the largest lattice (set by the scheduler; unused here)
+  bool one_lat = false;   // one lattice in the problem (set by the scheduler; unused here)
   int defl_k = 0;
   // A sparse matrix runs with slots along y: the blocks of one slot are scheduled together,
   // so the vector its rows gather from stays in L2 while the slot runs (slots along x would
@@ -1051,6 +1052,7 @@ struct BlockedSparseEngine {
   hp_ctx* ctx;
   BArgs a;
   int big_lat = 0;          // index of the largest lattice (set by the scheduler; unused here)
+  bool one_lat = false;     // one lattice in the problem (set by the scheduler; unused here)
   int ntrue = 1;            // row blocks of the true-residual kernel (per slot)
   double* tpart = nullptr;  // its partial sums [B][ntrue]
   unsigned int* tcnt = nullptr;

@@ -57,6 +57,7 @@ hp_status run_schedule(hp_ctx* ctx, Engine& eng, SolveProblem& pb, SolveResult& 
   std::vector<SlotState> host(nslots);
   memset(host.data(), 0, sizeof(SlotState) * nslots);
   eng.big_lat = big;
+  eng.one_lat = nl == 1;
   HP_TRY(eng.setup(nslots, Vmax, lats_dev, st_dev, pb.opts, pb.tol, delta, pb.lats[big]));
   const int G = eng.group();   // slots refilled together (one lattice per group: the stencil shares links)
 

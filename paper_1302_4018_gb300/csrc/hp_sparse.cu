@@ -440,6 +440,194 @@ hp_status csr_view(hp_ctx* ctx, int n, const int32_t* row_ptr, const int32_t* co
   return HP_OK;
 }
 
+// ------------------------------------------------------------ Colors2Perm and colorOffsets
+// Stable LSD radix sort of (key, value) pairs, 8 key bits per pass: per tile of RS_T items a
+// digit histogram (digit-major over tiles), its exclusive scan, and a scatter in which an item's
+// place among equal digits of its tile counts the items of earlier warps and earlier lanes.
+constexpr int RS_T = 256;
+static_assert(RS_T == 256, "one thread per digit in the histogram");
+
+__global__ void __launch_bounds__(RS_T) k_rs_hist(const unsigned long long* __restrict__ key, long long n, int shift,
+                                                  int ntiles, int* __restrict__ hist) {
+  __shared__ int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const long long i = (long long)blockIdx.x * RS_T + threadIdx.x;
+  if (i < n) atomicAdd(&h[(int)((key[i] >> shift) & 255u)], 1);
+  __syncthreads();
+  hist[(long long)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_T) k_rs_scatter(const unsigned long long* __restrict__ kin,
+                                                     const int* __restrict__ vin, long long n, int shift, int ntiles,
+                                                     const int* __restrict__ off, unsigned long long* __restrict__ kout,
+                                                     int* __restrict__ vout) {
+  __shared__ int wc[RS_T / 32][256];
+  for (int t = threadIdx.x; t < (RS_T / 32) * 256; t += RS_T) (&wc[0][0])[t] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long i = (long long)blockIdx.x * RS_T + threadIdx.x;
+  const bool ok = i < n;
+  unsigned long long k = 0;
+  int d = 0;
+  if (ok) {
+    k = kin[i];
+    d = (int)((k >> shift) & 255u);
+  }
+  const unsigned int m = __match_any_sync(0xffffffffu, ok ? d : 256 + lane);   // idle lanes match nobody
+  const int rank = __popc(m & ((1u << lane) - 1u));
+  if (ok && rank == 0) wc[w][d] = __popc(m);
+  __syncthreads();
+  if (ok) {
+    int before = rank;
+    for (int u = 0; u < w; ++u) before += wc[u][d];
+    const long long dst = (long long)off[(long long)d * ntiles + blockIdx.x] + before;
+    kout[dst] = k;
+    vout[dst] = vin[i];
+  }
+}
+
+// sorts (key[i], val[i]), i < n, stably by the low `bits` bits of key; the result replaces the input
+hp_status radix_sort_pairs(hp_ctx* ctx, unsigned long long* key, int* val, long long n, int bits, const char* tag) {
+  if (n <= 1 || bits <= 0) return HP_OK;
+  const long long ntiles = (n + RS_T - 1) / RS_T;
+  unsigned long long* k2;
+  int *v2, *hist, *off;
+  const std::string t(tag);
+  HP_TRY(ws_arr(ctx, (t + ".k2").c_str(), (size_t)n, &k2));
+  HP_TRY(ws_arr(ctx, (t + ".v2").c_str(), (size_t)n, &v2));
+  HP_TRY(ws_arr(ctx, (t + ".hist").c_str(), (size_t)(256 * ntiles), &hist));
+  HP_TRY(ws_arr(ctx, (t + ".off").c_str(), (size_t)(256 * ntiles + 1), &off));
+  unsigned long long *ka = key, *kb = k2;
+  int *va = val, *vb = v2;
+  for (int shift = 0; shift < bits; shift += 8) {
+    {
+      ProfScope ps(ctx, "k_rs_hist");
+      k_rs_hist<<<(unsigned)ntiles, RS_T, 0, ctx->stream>>>(ka, n, shift, (int)ntiles, hist);
+    }
+    HP_LAUNCH_CHECK();
+    HP_TRY(excl_scan(ctx, hist, 256 * ntiles, off, (t + ".scan").c_str()));
+    {
+      ProfScope ps(ctx, "k_rs_scatter");
+      k_rs_scatter<<<(unsigned)ntiles, RS_T, 0, ctx->stream>>>(ka, va, n, shift, (int)ntiles, off, kb, vb);
+    }
+    HP_LAUNCH_CHECK();
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  if (ka != key) {
+    HP_CUDA(cudaMemcpyAsync(key, ka, sizeof(unsigned long long) * (size_t)n, cudaMemcpyDeviceToDevice, ctx->stream));
+    HP_CUDA(cudaMemcpyAsync(val, va, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  return HP_OK;
+}
+
+// The blocks of Algorithm 1 replayed from the colour paths, one level at a time: every row
+// knows the first position of its block (bst, in the coordinates of the final permutation)
+// and every block its size (bsz at that position).  Level 1 is the whole matrix, recorded as
+// (0, n - 1, 1).
+__global__ void k_ord_init(int n, int* __restrict__ bst, unsigned char* __restrict__ act, int* __restrict__ bsz,
+                           int* __restrict__ ostart, int* __restrict__ oend, int* __restrict__ olev) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    bst[v] = 0;
+    act[v] = 1;
+    if (v == 0) {
+      bsz[0] = n;
+      ostart[0] = 0;
+      oend[0] = n - 1;
+      olev[0] = 1;
+    }
+  }
+}
+
+// colour count of every block of the level (colours 0 .. k - 1); a colour outside [0, block size)
+// is an invalid hierarchy (flagged, not used)
+__global__ void k_ord_ncol(int n, const int* __restrict__ col, const unsigned char* __restrict__ act,
+                           const int* __restrict__ bst, const int* __restrict__ bsz, int* __restrict__ ncol,
+                           int* __restrict__ bad) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    if (!act[v]) continue;
+    const int c = col[v], b = bst[v];
+    if (c < 0 || c >= bsz[b]) atomicOr(bad, 1);
+    else atomicMax(ncol + b, c + 1);
+  }
+}
+
+// a block recurses unless it has one colour or as many colours as rows (line 4 of the algorithm);
+// the rows of each colour class of a recursing block count at slot start + colour, those of a
+// stopped block at its start, so that the prefix sum keeps every block's range
+__global__ void k_ord_count(int n, const int* __restrict__ col, const unsigned char* __restrict__ act,
+                            const int* __restrict__ bst, const int* __restrict__ bsz, const int* __restrict__ ncol,
+                            unsigned char* __restrict__ rec, int* __restrict__ cnt) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    const int b = bst[v];
+    bool r = false;
+    if (act[v]) {
+      const int c = col[v], nc = ncol[b];
+      r = c >= 0 && c < bsz[b] && nc != 1 && nc != bsz[b];
+    }
+    rec[v] = r ? 1 : 0;
+    atomicAdd(cnt + b + (r ? col[v] : 0), 1);
+  }
+}
+
+// the child blocks (level + 1) at their places S[slot]; the first row to reach a new block
+// records (start, end, level + 1)
+__global__ void k_ord_relabel(int n, int level, const int* __restrict__ col, const unsigned char* __restrict__ rec,
+                              const int* __restrict__ bst, const int* __restrict__ cnt, const int* __restrict__ S,
+                              int* __restrict__ nbst, int* __restrict__ nbsz, unsigned char* __restrict__ act,
+                              int* __restrict__ mark, int* __restrict__ nblk, int cap, int* __restrict__ ostart,
+                              int* __restrict__ oend, int* __restrict__ olev, int* __restrict__ bad) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    const bool r = rec[v] != 0;
+    const int slot = bst[v] + (r ? col[v] : 0);
+    const int s = S[slot], sz = cnt[slot];
+    nbst[v] = s;
+    nbsz[s] = sz;
+    act[v] = r ? 1 : 0;
+    if (r && atomicExch(mark + s, 1) == 0) {
+      const int idx = atomicAdd(nblk, 1);
+      if (idx < cap) {
+        ostart[idx] = s;
+        oend[idx] = s + sz - 1;
+        olev[idx] = level + 1;
+      } else {
+        atomicOr(bad, 2);
+      }
+    }
+  }
+}
+
+__global__ void k_ord_keys(int n, const int* __restrict__ a, const int* __restrict__ lev, unsigned long long* __restrict__ key,
+                           int* __restrict__ val) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    key[i] = lev ? (((unsigned long long)a[i] << 6) | (unsigned long long)lev[i]) : (unsigned long long)a[i];
+    val[i] = i;
+  }
+}
+
+__global__ void k_ord_gather(int m, const int* __restrict__ idx, const int* __restrict__ ostart,
+                             const int* __restrict__ oend, const int* __restrict__ olev, int* __restrict__ out) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+    const int i = idx[j];
+    out[3 * (size_t)j] = ostart[i];
+    out[3 * (size_t)j + 1] = oend[i];
+    out[3 * (size_t)j + 2] = olev[i];
+  }
+}
+
+int bits_for(long long v) {   // bits needed for values 0 .. v
+  int b = 0;
+  while (b < 62 && (1LL << b) <= v) ++b;
+  return b;
+}
+
 }  // namespace
 
 extern "C" hp_status hp_sparse_coloring(hp_ctx* ctx, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
@@ -577,6 +765,112 @@ extern "C" hp_status hp_sparse_coloring(hp_ctx* ctx, int32_t n, const int32_t* r
   HP_CUDA(cudaStreamSynchronize(ctx->stream));
   for (int l = 0; l < max_levels; ++l) radices[l] = l < levels ? rad[l] : 0;
   *n_levels = levels;
+  return HP_OK;
+}
+
+extern "C" hp_status hp_sparse_ordering(hp_ctx* ctx, int32_t n, const int32_t* paths, int32_t n_levels,
+                                        int32_t* perm, int32_t* offsets, int64_t offsets_cap, int64_t* n_offsets) {
+  if (!ctx) {
+    hp_set_error("NULL context");
+    return HP_EINVAL;
+  }
+  if (n < 1 || n_levels < 0 || n_levels > HP_MAX_LEVELS || (n_levels > 0 && !paths) || (!perm && !offsets) ||
+      (offsets && (offsets_cap < 0 || !n_offsets))) {
+    hp_set_error("hp_sparse_ordering: n >= 1, n_levels in [0, %d], paths for n_levels > 0, an output, and "
+                 "n_offsets with offsets required", HP_MAX_LEVELS);
+    return HP_EINVAL;
+  }
+  HP_CUDA(cudaSetDevice(ctx->device));
+  const size_t N = (size_t)n;
+  const int* P = nullptr;
+  if (n_levels > 0) {
+    const void* p = nullptr;
+    HP_TRY(hp_device_view(ctx, paths, sizeof(int32_t) * N * n_levels, "ord.paths", &p));
+    P = (const int*)p;
+  }
+  const int cap = 2 * n;   // a tree whose inner nodes have >= 2 children and <= n leaves has < 2n nodes
+  unsigned char *act, *rec;
+  int *bst[2], *bsz[2], *ncol, *cnt, *S, *mark, *nblk, *bad, *ostart, *oend, *olev, *val;
+  unsigned long long* key;
+  HP_TRY(ws_arr(ctx, "ord.act", N, &act));
+  HP_TRY(ws_arr(ctx, "ord.rec", N, &rec));
+  HP_TRY(ws_arr(ctx, "ord.bst0", N, &bst[0]));
+  HP_TRY(ws_arr(ctx, "ord.bst1", N, &bst[1]));
+  HP_TRY(ws_arr(ctx, "ord.bsz0", N, &bsz[0]));
+  HP_TRY(ws_arr(ctx, "ord.bsz1", N, &bsz[1]));
+  HP_TRY(ws_arr(ctx, "ord.ncol", N, &ncol));
+  HP_TRY(ws_arr(ctx, "ord.cnt", N, &cnt));
+  HP_TRY(ws_arr(ctx, "ord.S", N + 1, &S));
+  HP_TRY(ws_arr(ctx, "ord.mark", N, &mark));
+  HP_TRY(ws_arr(ctx, "ord.nblk", 1, &nblk));
+  HP_TRY(ws_arr(ctx, "ord.bad", 1, &bad));
+  HP_TRY(ws_arr(ctx, "ord.ostart", (size_t)cap, &ostart));
+  HP_TRY(ws_arr(ctx, "ord.oend", (size_t)cap, &oend));
+  HP_TRY(ws_arr(ctx, "ord.olev", (size_t)cap, &olev));
+  HP_TRY(ws_arr(ctx, "ord.key", (size_t)cap, &key));
+  HP_TRY(ws_arr(ctx, "ord.val", (size_t)cap, &val));
+  const int one = 1;
+  HP_CUDA(cudaMemcpyAsync(nblk, &one, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  HP_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), ctx->stream));
+  const int nb = blocks_for(ctx, n, ST);
+  k_ord_init<<<nb, ST, 0, ctx->stream>>>(n, bst[0], act, bsz[0], ostart, oend, olev);
+  HP_LAUNCH_CHECK();
+  int cur = 0;
+  for (int l = 0; l < n_levels; ++l) {
+    const int* col = P + (size_t)l * N;
+    HP_CUDA(cudaMemsetAsync(ncol, 0, sizeof(int) * N, ctx->stream));
+    HP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * N, ctx->stream));
+    HP_CUDA(cudaMemsetAsync(mark, 0, sizeof(int) * N, ctx->stream));
+    {
+      ProfScope ps(ctx, "k_ord_level");
+      k_ord_ncol<<<nb, ST, 0, ctx->stream>>>(n, col, act, bst[cur], bsz[cur], ncol, bad);
+      k_ord_count<<<nb, ST, 0, ctx->stream>>>(n, col, act, bst[cur], bsz[cur], ncol, rec, cnt);
+    }
+    HP_LAUNCH_CHECK();
+    HP_TRY(excl_scan(ctx, cnt, n, S, "ord.scan"));
+    {
+      ProfScope ps(ctx, "k_ord_level");
+      k_ord_relabel<<<nb, ST, 0, ctx->stream>>>(n, l + 1, col, rec, bst[cur], cnt, S, bst[cur ^ 1], bsz[cur ^ 1], act,
+                                                mark, nblk, cap, ostart, oend, olev, bad);
+    }
+    HP_LAUNCH_CHECK();
+    cur ^= 1;
+  }
+  int flags = 0, m = 0;
+  HP_TRY(read_scalar(ctx, bad, &flags));
+  HP_TRY(read_scalar(ctx, nblk, &m));
+  if (flags) {
+    hp_set_error("hp_sparse_ordering: %s", (flags & 1) ? "a colour lies outside [0, size of its block)"
+                                                       : "more blocks than a hierarchy of n rows has");
+    return HP_EINVAL;
+  }
+  if (perm) {   // rows by the first position of their last block, ties (rows of one block) by index
+    k_ord_keys<<<nb, ST, 0, ctx->stream>>>(n, bst[cur], nullptr, key, val);
+    HP_LAUNCH_CHECK();
+    HP_TRY(radix_sort_pairs(ctx, key, val, n, bits_for(n), "ord.rs"));
+    HP_CUDA(cudaMemcpyAsync(perm, val, sizeof(int) * N, cudaMemcpyDefault, ctx->stream));
+  }
+  if (offsets) {   // pre-order of the recursion: by start, a block before its first child (level)
+    *n_offsets = m;
+    if (m > offsets_cap) {
+      HP_CUDA(cudaStreamSynchronize(ctx->stream));
+      hp_set_error("hp_sparse_ordering: %d blocks, offsets_cap %lld (2n - 1 always suffices)", m,
+                   (long long)offsets_cap);
+      return HP_EINVAL;
+    }
+    k_ord_keys<<<blocks_for(ctx, m, ST), ST, 0, ctx->stream>>>(m, ostart, olev, key, val);
+    HP_LAUNCH_CHECK();
+    HP_TRY(radix_sort_pairs(ctx, key, val, m, bits_for(n) + 6, "ord.rs"));
+    int* out = offsets;
+    const bool host = !hp_is_device_ptr(offsets);
+    if (host) HP_TRY(ws_arr(ctx, "ord.out", 3 * (size_t)m, &out));
+    k_ord_gather<<<blocks_for(ctx, m, ST), ST, 0, ctx->stream>>>(m, val, ostart, oend, olev, out);
+    HP_LAUNCH_CHECK();
+    if (host) HP_CUDA(cudaMemcpyAsync(offsets, out, sizeof(int) * 3 * (size_t)m, cudaMemcpyDeviceToHost, ctx->stream));
+  } else if (n_offsets) {
+    *n_offsets = m;
+  }
+  HP_CUDA(cudaStreamSynchronize(ctx->stream));
   return HP_OK;
 }
 

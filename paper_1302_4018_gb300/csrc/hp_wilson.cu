@@ -149,7 +149,8 @@ hp_status hp_prepare_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom* g, cons
 #define HP_WILSON_DECLARE(SUFFIX)                                                                             \
   hp_status hp_wilson_apply_##SUFFIX(hp_ctx* ctx, const LatGeom& g, int nrhs, const double* in, double* out); \
   hp_status hp_wilson_bench_##SUFFIX(hp_ctx* ctx, const LatGeom& g, int nrhs, int iters, double* ms);         \
-  hp_status hp_wilson_schur_##SUFFIX(hp_ctx* ctx, const LatGeom& g, int nrhs, const double* in, double* out); \
+  hp_status hp_wilson_schur_##SUFFIX(hp_ctx* ctx, const LatGeom& g, int nrhs, int eo_kernel, const double* in,   \
+                                      double* out);                                                           \
   hp_status hp_wilson_solve_##SUFFIX(hp_ctx* ctx, SolveProblem& pb, SolveResult& res, bool eo, bool clover,   \
                                      double delta);
 HP_WILSON_DECLARE(fp64)
@@ -181,8 +182,8 @@ static bool eo_lattice(const LatGeom& g) {
   return true;
 }
 
-hp_status hp_schur_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrhs, int prec, const double* in,
-                          double* out) {
+hp_status hp_schur_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrhs, int prec, int eo_kernel,
+                          const double* in, double* out) {
   if (!eo_lattice(g)) {
     hp_set_error("the even-odd split needs every extent even (lattice %d x %d x %d x %d; an odd or a padded "
                  "extent joins sites of one parity)", g.L[0], g.L[1], g.L[2], g.L[3]);
@@ -195,10 +196,10 @@ hp_status hp_schur_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrh
   HP_TRY(hp_prepare_mass(ctx, op, &g, "schur"));
   HP_TRY(hp_prepare_wilson(ctx, op, &g, "schur", (1 << PR64) | (1 << PR32) | (1 << PR16)));
   switch (prec) {
-    case HP_PREC_FP64: return hp_wilson_schur_fp64(ctx, g, nrhs, in, out);
-    case HP_PREC_MIXED_FP32: return hp_wilson_schur_fp32(ctx, g, nrhs, in, out);
-    case HP_PREC_MIXED_FP16: return hp_wilson_schur_fp16(ctx, g, nrhs, in, out);
-    case HP_PREC_MIXED_BF16: return hp_wilson_schur_bf16(ctx, g, nrhs, in, out);
+    case HP_PREC_FP64: return hp_wilson_schur_fp64(ctx, g, nrhs, eo_kernel, in, out);
+    case HP_PREC_MIXED_FP32: return hp_wilson_schur_fp32(ctx, g, nrhs, eo_kernel, in, out);
+    case HP_PREC_MIXED_FP16: return hp_wilson_schur_fp16(ctx, g, nrhs, eo_kernel, in, out);
+    case HP_PREC_MIXED_BF16: return hp_wilson_schur_bf16(ctx, g, nrhs, eo_kernel, in, out);
   }
   hp_set_error("unknown precision %d", prec);
   return HP_EINVAL;

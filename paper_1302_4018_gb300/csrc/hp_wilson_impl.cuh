@@ -1433,6 +1433,7 @@ static __global__ void k_w_keep(WArgs a, const int* __restrict__ slots, const in
 
 // the even-odd V and T steps with two right-hand sides per thread (FP16 / BF16 / FP32 iteration)
 #include "hp_eo2.cuh"
+#include "hp_eo3.cuh"
 
 // ================================================================ the engine
 template <int SPR>
@@ -1452,8 +1453,10 @@ struct WilsonEngine {
   WArgs a;
   int nslots, gy, gyb, rpt = 1, variant = 10;
   int eo_kernel = 4;   // even-odd V / T steps: 1 one right-hand side per thread, 10 L + B pair kernels
-                       // (B = 3 or 4 resident blocks per SM, L = 1: FP32 links), 5 pair even + single odd
+                       // (B = 3 or 4 resident blocks per SM, L = 1: FP32 links), 5 pair even + single odd,
+                       // 6 tensor-core even + pair odd (binary16, one lattice, no clover)
   int big_lat = 0;     // index of the largest lattice of the problem (set before setup)
+  bool one_lat = false;   // the problem has one lattice (set before setup)
   int kernels_per_iteration() const { return eo ? (SPR == PR64 ? 10 : 12) : (SPR == PR64 ? 7 : 8); }
   // streaming kernels: grid-stride with 8 blocks per SM per slot (few partial sums and atomic tickets);
   // stencil kernels: one block per tile (gy) so that the lattice is swept once in site order
@@ -1535,7 +1538,7 @@ struct WilsonEngine {
       rpt = 1;
       if (SPR != PR64) {
         const int k = o.eo_kernel;
-        if (k == 1 || k == 3 || k == 4 || k == 5 || k == 13 || k == 14) eo_kernel = k;
+        if (k == 1 || k == 3 || k == 4 || k == 5 || k == 13 || k == 14 || (k == 6 && tc_ok())) eo_kernel = k;
         else HP_TRY(tune_eo(gbig));
       }
     }
@@ -1628,9 +1631,43 @@ struct WilsonEngine {
     HP_LAUNCH_CHECK();
     return HP_OK;
   }
+  // the tensor-core even-site kernel serves binary16 iterations of one lattice without the clover
+  // term, up to 32 slots (four MMA row groups)
+  bool tc_ok() const { return SPR == PR16 && !clover && one_lat && nslots <= 32; }
+  // eo_kernel 6: the tensor-core even-site kernel with the odd-site pair kernel (4 resident blocks)
+  template <bool CL>
+  hp_status eo_tc(int which) {
+    static_assert(SPR == PR16 && !CL, "binary16 without the clover term");
+    constexpr int TPB = 2;
+    const dim3 g2o((nslots + 1) / 2, (gy + TPB - 1) / TPB, 1);
+    FieldPtr in = which == 0 ? a.p : a.s, out = which == 0 ? a.v : a.t;
+    {
+      ProfScope ps(ctx, "k_eo_even");
+      const dim3 gt(ctx->num_sms * 4);
+      switch ((nslots + 7) / 8) {
+        case 1: k_eo3_even<1><<<gt, NT, 0, ctx->stream>>>(a, in, a.mid, nslots, big_lat); break;
+        case 2: k_eo3_even<2><<<gt, NT, 0, ctx->stream>>>(a, in, a.mid, nslots, big_lat); break;
+        case 3: k_eo3_even<3><<<gt, NT, 0, ctx->stream>>>(a, in, a.mid, nslots, big_lat); break;
+        default: k_eo3_even<4><<<gt, NT, 0, ctx->stream>>>(a, in, a.mid, nslots, big_lat); break;
+      }
+    }
+    HP_LAUNCH_CHECK();
+    if (which == 0) {
+      ProfScope ps(ctx, "k_eo_odd_v<fp16>");
+      k_eo2_odd<SPR, PR16, NT, 4, EPI_V, CL, TPB><<<g2o, NT, 0, ctx->stream>>>(a, in, a.mid, out, nslots);
+    } else {
+      ProfScope ps(ctx, "k_eo_odd_t<fp16>");
+      k_eo2_odd<SPR, PR16, NT, 4, EPI_T, CL, TPB><<<g2o, NT, 0, ctx->stream>>>(a, in, a.mid, out, nslots);
+    }
+    HP_LAUNCH_CHECK();
+    return HP_OK;
+  }
   template <bool CL>
   hp_status eo_pair_v(int which) {   // eo_kernel = 10 L + B: B resident blocks, L = 1 FP32 links
     constexpr int L16 = SPR == PR32 ? PR32 : PR16;
+    if constexpr (SPR == PR16 && !CL) {
+      if (eo_kernel == 6 && tc_ok()) return eo_tc<CL>(which);
+    }
     switch (eo_kernel) {
       case 5: return eo_mixed<CL>(which);
       case 3: return eo_pair<L16, 3, CL>(which);
@@ -2013,10 +2050,12 @@ __global__ void k_eo_to_canonical(FieldPtr f, LatGeom g, int Vmax, int nrhs, int
 // through the solver's own launches: a WilsonEngine set up for the right-hand sides as running slots
 // of one lattice, its V step v = S p, in the iteration precision SPR
 template <int SPR>
-static hp_status schur_apply_t(hp_ctx* ctx, const LatGeom& g, int nrhs, const double* in, double* out) {
+static hp_status schur_apply_t(hp_ctx* ctx, const LatGeom& g, int nrhs, int eo_kernel, const double* in,
+                               double* out) {
   WilsonEngine<SPR> e{ctx};
   e.eo = true;
   e.clover = g.clover != 0;
+  e.one_lat = true;
   const int ns = (nrhs + WilsonEngine<SPR>::GROUP_MAX - 1) / WilsonEngine<SPR>::GROUP_MAX * WilsonEngine<SPR>::GROUP_MAX;
   void* p = nullptr;
   HP_TRY(hp_ws(ctx, "schur.lat", sizeof(LatGeom), &p));
@@ -2030,6 +2069,7 @@ static hp_status schur_apply_t(hp_ctx* ctx, const LatGeom& g, int nrhs, const do
   HP_CUDA(cudaMemcpyAsync(st_dev, st.data(), sizeof(SlotState) * ns, cudaMemcpyHostToDevice, ctx->stream));
   hp_solver_opts o;
   memset(&o, 0, sizeof(o));
+  o.eo_kernel = eo_kernel;
   HP_TRY(e.setup(ns, g.V, lat_dev, st_dev, o, 1e-10, 0.0, g));
   size_t nb = 0;
   const size_t fb = field_bytes(SPR, ns, e.a.Vmax, &nb);
@@ -2155,8 +2195,8 @@ hp_status wilson_apply_prec(hp_ctx* ctx, const LatGeom& g, int nrhs, const doubl
   return apply_wilson_t<SPR>(ctx, g, nrhs, in, out);
 }
 template <int SPR>
-hp_status wilson_schur_prec(hp_ctx* ctx, const LatGeom& g, int nrhs, const double* in, double* out) {
-  return schur_apply_t<SPR>(ctx, g, nrhs, in, out);
+hp_status wilson_schur_prec(hp_ctx* ctx, const LatGeom& g, int nrhs, int eo_kernel, const double* in, double* out) {
+  return schur_apply_t<SPR>(ctx, g, nrhs, eo_kernel, in, out);
 }
 template <int SPR>
 hp_status wilson_bench_prec(hp_ctx* ctx, const LatGeom& g, int nrhs, int iters, double* ms) {
@@ -2177,8 +2217,9 @@ hp_status wilson_solve_prec(hp_ctx* ctx, SolveProblem& pb, SolveResult& res, boo
   hp_status hp_wilson_bench_##SUFFIX(hp_ctx* ctx, const LatGeom& g, int nrhs, int iters, double* ms) {        \
     return wilson_bench_prec<SPR>(ctx, g, nrhs, iters, ms);                                                   \
   }                                                                                                           \
-  hp_status hp_wilson_schur_##SUFFIX(hp_ctx* ctx, const LatGeom& g, int nrhs, const double* in, double* out) { \
-    return wilson_schur_prec<SPR>(ctx, g, nrhs, in, out);                                                     \
+  hp_status hp_wilson_schur_##SUFFIX(hp_ctx* ctx, const LatGeom& g, int nrhs, int eo_kernel, const double* in,  \
+                                      double* out) {                                                          \
+    return wilson_schur_prec<SPR>(ctx, g, nrhs, eo_kernel, in, out);                                          \
   }                                                                                                           \
   hp_status hp_wilson_solve_##SUFFIX(hp_ctx* ctx, SolveProblem& pb, SolveResult& res, bool eo, bool clover,   \
                                      double delta) {                                                          \

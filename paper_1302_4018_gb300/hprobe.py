@@ -44,7 +44,7 @@ EXPORTED = ["hp_ctx_create", "hp_ctx_destroy", "hp_last_error", "hp_ctx_synchron
             "hp_permutation", "hp_probe_vectors", "hp_trace_inv", "hp_trace_inv_grad", "hp_trace_inv_batch",
             "hp_operator_apply", "hp_dslash_bench", "hp_profile_enable", "hp_profile_report",
             "hp_launch_count", "hp_operator_apply_noalloc", "hp_probe_sequence", "hp_trace_inv_bounds",
-            "hp_sparse_coloring", "hp_sparse_probe_vectors", "hp_trace_inv_sparse", "hp_trace_inv_deflated",
+            "hp_sparse_coloring", "hp_sparse_ordering", "hp_sparse_probe_vectors", "hp_trace_inv_sparse", "hp_trace_inv_deflated",
             "hp_trace_inv_solutions", "hp_trace_prefix", "hp_schur_apply", "hp_laplacian_eigs"]
 
 
@@ -111,6 +111,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hp_operator_apply_noalloc": (C.c_int, [C.POINTER(Operator), C.POINTER(Lattice), I64, P, P, P]),
         "hp_profile_report": (C.c_int, [P, C.c_char_p, I64]),
         "hp_sparse_coloring": (C.c_int, [P, I32, P, P, I32, P, P, C.POINTER(I32)]),
+        "hp_sparse_ordering": (C.c_int, [P, I32, P, I32, P, P, I64, C.POINTER(I64)]),
         "hp_sparse_probe_vectors": (C.c_int, [P, I32, P, P, I32, I64, I64, C.c_uint64, P, C.POINTER(I32)]),
         "hp_trace_inv_sparse": (C.c_int, [P, I32, P, P, P, P, P, I32, I64, D, C.POINTER(SolverOpts), P, P,
                                           C.POINTER(SolveStats)]),
@@ -119,7 +120,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hp_trace_inv_solutions": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I64, D,
                                              C.POINTER(SolverOpts), I64, P, P, P, C.POINTER(SolveStats)]),
         "hp_trace_prefix": (C.c_int, [P, I64, P, P]),
-        "hp_schur_apply": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I64, I32, P, P]),
+        "hp_schur_apply": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I64, I32, I32, P, P]),
         "hp_laplacian_eigs": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I32, D, I32, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -282,11 +283,12 @@ class Context:
                                        _ptr(inp), _ptr(out)))
         return out
 
-    def schur_apply(self, op: Operator, dims, nrhs: int, precision, inp, out):
-        """out = S inp on the odd sites (the even-odd iteration's Schur complement), canonical layout."""
+    def schur_apply(self, op: Operator, dims, nrhs: int, precision, inp, out, eo_kernel: int = 0):
+        """out = S inp on the odd sites (the even-odd iteration's Schur complement), canonical layout;
+        eo_kernel as in make_opts (0: the autotuner's choice)."""
         prec = PREC[precision] if isinstance(precision, str) else int(precision)
-        _check(lib().hp_schur_apply(self._h, C.byref(op), C.byref(make_lattice(dims)), int(nrhs), prec, _ptr(inp),
-                                    _ptr(out)))
+        _check(lib().hp_schur_apply(self._h, C.byref(op), C.byref(make_lattice(dims)), int(nrhs), prec,
+                                    int(eo_kernel), _ptr(inp), _ptr(out)))
         return out
 
     def laplacian_eigs(self, op: Operator, dims, k: int, tol: float = 1e-10, max_sweeps: int = 0, evecs=None):
@@ -370,6 +372,18 @@ class Context:
         _check(lib().hp_sparse_coloring(self._h, n, rp, ci, int(max_levels), _ptr(paths_out), _ptr(rad),
                                         C.byref(nl)))
         return paths_out[:nl.value], [int(r) for r in rad[:nl.value]]
+
+    def sparse_ordering(self, paths, perm_out=None, offsets_out=None):
+        """Algorithm 1's perm and colorOffsets from colour paths [n_levels, n] (int32, host or device):
+        (perm [n], offsets [n_blocks, 3] of (start, end, level)).  Without ``perm_out`` /
+        ``offsets_out`` (host or device int32 arrays of n and of (2n - 1) x 3) host arrays are returned."""
+        n_levels, n = int(paths.shape[0]), int(paths.shape[1])
+        perm = np.zeros(n, dtype=np.int32) if perm_out is None else perm_out
+        offs = np.zeros((max(2 * n - 1, 1), 3), dtype=np.int32) if offsets_out is None else offsets_out
+        cnt = C.c_int64()
+        _check(lib().hp_sparse_ordering(self._h, n, _ptr(paths), n_levels, _ptr(perm), _ptr(offs),
+                                        int(offs.shape[0]), C.byref(cnt)))
+        return perm, offs[:cnt.value]
 
     def sparse_probe_vectors(self, paths, radices: Sequence[int], first: int, count: int, z0_seed: int, out) -> int:
         """uint16 phases of the path probing vectors into ``out`` (device tensor of count*n);

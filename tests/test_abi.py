@@ -136,6 +136,10 @@ def test_sparse_entry_points_reject_a_missing_context_without_gpu():
     nl = ctypes.c_int32()
     assert lib.hp_sparse_coloring(None, 2, rp.ctypes.data, ci.ctypes.data, 2, paths.ctypes.data, rad.ctypes.data,
                                   ctypes.byref(nl)) == hprobe.HP_EINVAL
+    perm = np.zeros(2, dtype=np.int32)
+    nb = ctypes.c_int64()
+    assert lib.hp_sparse_ordering(None, 2, paths.ctypes.data, 1, perm.ctypes.data, None, 0,
+                                  ctypes.byref(nb)) == hprobe.HP_EINVAL
     per = ctypes.c_int32()
     assert lib.hp_sparse_probe_vectors(None, 2, paths.ctypes.data, rad.ctypes.data, 1, 0, 1, 0, None,
                                        ctypes.byref(per)) == hprobe.HP_EINVAL

@@ -79,6 +79,32 @@ def test_schur_apply_matches_oracle(ctx, hp, dims, nrhs, csw, prec):
         assert not np.any(got[r][O.site_parity(d4) == 0])
 
 
+# every kernel variant of the V step (eo_kernel: 1 one right-hand side per thread, 3 / 4 / 13 / 14 the
+# pair kernels, 5 pair even + single odd, 6 the tensor-core even-site kernel for binary16 -- with
+# up to 32 right-hand sides in row groups of 8, so 3, 9, 20 and 30 fill one to four groups, the
+# last ragged; other precisions and the clover term run the pair kernels in its place)
+VARIANT_CASES = [("fp16", k) for k in (1, 3, 4, 5, 6, 13, 14)] + [("bf16", 1), ("bf16", 4), ("bf16", 6),
+                                                                   ("fp32", 1), ("fp32", 4), ("fp32", 6)]
+
+
+@pytest.mark.parametrize("dims,nrhs,csw", [((4, 4, 4, 4), 3, 0.0), ((6, 2, 4, 6), 9, 0.0), ((8, 4, 6, 2), 20, 0.0),
+                                           ((4, 6, 2, 4), 30, 0.0), ((4, 4, 2, 4), 9, 1.0)])
+@pytest.mark.parametrize("prec,kernel", VARIANT_CASES)
+def test_schur_apply_kernel_variants_match_oracle(ctx, hp, dims, nrhs, csw, prec, kernel):
+    U = synth.gauge_links(dims, 0.4, 27)
+    mf = synth.mass_field(dims, 0.02, 28)
+    psi = synth.random_spinors(dims, nrhs, 29)
+    op = ctx.make_operator(hp.OP_WILSON, 0.03, 0.12, dev(U.view(np.float64).reshape(-1)), dev(mf), csw=csw)
+    out = torch.full((psi.size * 2,), float("nan"), dtype=torch.float64, device="cuda:0")
+    ctx.schur_apply(op, dims, nrhs, prec, dev(psi.view(np.float64).reshape(-1)), out, eo_kernel=kernel)
+    got = out.cpu().numpy().view(np.complex128).reshape(psi.shape)
+    C = O.clover_term(U, dims, 0.12, csw) if csw else None
+    for r in range(nrhs):
+        ref = O.wilson_schur_apply(psi[r], U, dims, 0.12, 0.03, mf, clover=C)
+        assert site_max_err(got[r], ref) <= SCHUR_TOL[prec], (prec, kernel, r, site_max_err(got[r], ref))
+        assert not np.any(got[r][O.site_parity(dims) == 0])
+
+
 @pytest.mark.parametrize("dims", [(3, 4, 2, 2), (4, 3, 2, 2), (2, 2, 2, 5), (2, 6)])
 def test_schur_apply_rejects_lattices_without_a_red_black_split(ctx, hp, dims):
     """An odd extent (or a padded one of size 1) makes some hop join sites of one parity."""
@@ -111,11 +137,11 @@ def test_schur_apply_full_size(ctx, hp, headline):
     op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.12, links, None)
     out = torch.empty(V * 24, dtype=torch.float64, device="cuda:0")
     inp = dev(psi.view(np.float64).reshape(-1))
-    for prec in ("fp64", "fp32", "fp16", "bf16"):
-        ctx.schur_apply(op, dims, 1, prec, inp, out)
+    for prec, kernel in (("fp64", 0), ("fp32", 0), ("fp16", 0), ("bf16", 0), ("fp16", 4), ("fp16", 6)):
+        ctx.schur_apply(op, dims, 1, prec, inp, out, eo_kernel=kernel)
         got = out.cpu().numpy().view(np.complex128).reshape(V, 4, 3)
         err = site_max_err(got, ref, odd)
-        assert err <= SCHUR_TOL[prec], (prec, err)
+        assert err <= SCHUR_TOL[prec], (prec, kernel, err)
 
 
 def test_wilson_apply_full_size_per_site(ctx, hp, headline):

@@ -439,17 +439,19 @@ _ORACLE_CACHE = {}
 
 
 # variant 0: the default (slot groups of 4, 18-real links); 4001: 12-real links (row 3 rebuilt);
-# 2101: slot groups of 2
-@pytest.mark.parametrize("prec,variant", [("fp64", 0), ("fp32", 0), ("fp16", 0), ("bf16", 0), ("fp16", 4001),
-                                          ("fp32", 4001), ("bf16", 2101)])
-def test_even_odd_trace_parity(ctx, hp, prec, variant):
+# 2101: slot groups of 2; kernel: the V / T step kernels (0 autotuned, 1 one right-hand side per
+# thread, 4 the pair kernels, 6 the tensor-core even-site kernel)
+@pytest.mark.parametrize("prec,variant,kernel", [("fp64", 0, 0), ("fp32", 0, 0), ("fp16", 0, 0), ("bf16", 0, 0),
+                                                 ("fp16", 4001, 0), ("fp32", 4001, 0), ("bf16", 2101, 0),
+                                                 ("fp16", 0, 1), ("fp16", 0, 4), ("fp16", 0, 6), ("bf16", 0, 6)])
+def test_even_odd_trace_parity(ctx, hp, prec, variant, kernel):
     dims = (4, 4, 6, 4)   # 384 sites, 192 per parity: the second 128-site tile is ragged
     U = synth.gauge_links(dims, 0.3, 1002)
     mf = synth.mass_field(dims, 0.01, 77)
     op = ctx.make_operator(hp.OP_WILSON, 0.01, 0.115, links_dev(U), dev(mf))
     s = 6
     T, _, st = ctx.trace_inv(op, dims, s, 1e-10, ctx.make_opts(prec, z0_seed=2002, rhs_block=24, even_odd=1,
-                                                               rhs_per_thread=variant))
+                                                               rhs_per_thread=variant, eo_kernel=kernel))
     if "eo_parity" not in _ORACLE_CACHE:
         _ORACLE_CACHE["eo_parity"] = E.trace_prefix(E.wilson_quadratures(dims, U, 0.115, 0, s, 2002, mass=0.01,
                                                                          mass_field=mf, method="dense"))

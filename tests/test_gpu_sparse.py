@@ -83,7 +83,7 @@ def _oracle_levels(offsets, max_levels):
 def _check_against_oracle(ctx, rp, ci, max_levels, device):
     n = len(rp) - 1
     A = sp.csr_matrix((np.ones(len(ci)), ci, rp), shape=(n, n))
-    _, offsets, opaths = S.hierarchical_coloring(A, max_levels=max_levels)
+    operm, offsets, opaths = S.hierarchical_coloring(A, max_levels=max_levels)
     if device:
         rp_d, ci_d = torch.from_numpy(rp).cuda(), torch.from_numpy(ci).cuda()
         out = torch.full((max_levels, n), -7, dtype=torch.int32, device="cuda:0")
@@ -100,6 +100,17 @@ def _check_against_oracle(ctx, rp, ci, max_levels, device):
     assert rad == [int(opaths[:, l].max()) + 1 for l in range(nlev)]
     if full is not None:
         assert not full[nlev:].any()
+    # Algorithm 1's perm and colorOffsets from the GPU's paths, on the GPU (device arrays when the
+    # colouring ran on device arrays)
+    if device:
+        perm_d = torch.full((n,), -1, dtype=torch.int32, device="cuda:0")
+        offs_d = torch.full((2 * n - 1, 3), -1, dtype=torch.int32, device="cuda:0")
+        perm, offs = ctx.sparse_ordering(out[:nlev], perm_d, offs_d)
+        perm, offs = perm.cpu().numpy(), offs.cpu().numpy()
+    else:
+        perm, offs = ctx.sparse_ordering(np.ascontiguousarray(paths))
+    assert np.array_equal(perm, operm)
+    assert [tuple(int(v) for v in o) for o in offs] == [tuple(o) for o in offsets]
     return paths, rad
 
 
@@ -113,6 +124,31 @@ def test_sparse_coloring_bit_exact(ctx, name):
 def test_sparse_coloring_max_levels(ctx, max_levels):
     rp, ci = _pattern("grid6_renumbered")
     _check_against_oracle(ctx, rp, ci, max_levels, device=False)
+
+
+def test_sparse_ordering_properties_and_errors(ctx, hp):
+    """perm is a permutation that makes A(perm, perm) block diagonal per colour of level 1; every
+    recorded block lies inside its parent; a colour beyond its block and a short offsets array fail."""
+    rp, ci = _pattern("grid28_renumbered")
+    n = len(rp) - 1
+    paths, rad = ctx.sparse_coloring(rp, ci, 32)
+    perm, offs = ctx.sparse_ordering(np.ascontiguousarray(paths))
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    assert np.all(np.diff(paths[0][perm]) >= 0)   # level-1 colours in ascending runs
+    starts = {(int(s), int(lv)): int(e) for s, e, lv in offs}
+    for s, e, lv in offs:
+        if lv > 1:   # the enclosing block of the level above
+            parent = [(ps, pe) for (ps, plv), pe in starts.items() if plv == lv - 1 and ps <= s and e <= pe]
+            assert len(parent) == 1
+    bad = np.ascontiguousarray(paths.copy())
+    bad[0, 5] = n + 3
+    with pytest.raises(hp.HProbeError) as e:
+        ctx.sparse_ordering(bad)
+    assert e.value.status == hp.HP_EINVAL
+    short = np.zeros((3, 3), dtype=np.int32)
+    with pytest.raises(hp.HProbeError) as e:
+        ctx.sparse_ordering(np.ascontiguousarray(paths), offsets_out=short)
+    assert e.value.status == hp.HP_EINVAL and "offsets_cap" in str(e.value)
 
 
 def test_sparse_coloring_rerun_same_context(ctx):
