@@ -70,11 +70,11 @@ def source_hash(kernel):
 
 # DRAM traffic of the dominant kernel per byte of algorithmic work, from one ncu capture of the
 # same kernel (k_eo2_even, the two-right-hand-side even-site stencil, eo_kernel 4) on 32^3x16 with
-# 12 slots: 278.3 MB read + 142.6 MB written per launch against 402.7 MB algorithmic (both parts of
-# the launch -- spinors and links -- grow with the units processed, so the ratio carries over to the
-# 32^3x64 launch); valid only for the kernel source it was taken on
+# 12 slots: 278.3 MB read + 142.6 MB written per launch against 377.5 MB algorithmic (12-real links;
+# both parts of the launch -- spinors and links -- grow with the units processed, so the ratio
+# carries over to the 32^3x64 launch); valid only for the kernel source it was taken on
 NCU_TRAFFIC = {("k_eo_even", "2cd1ee671099"): {"bytes_all_slots": 278.3e6 + 142.6e6,
-                                      "alg_bytes_all_slots": 262144 * 104 * 12 + 4 * 524288 * 36}}
+                                      "alg_bytes_all_slots": 262144 * 104 * 12 + 4 * 524288 * 24}}
 
 
 class Clocks:
@@ -156,10 +156,13 @@ def max_over_ranks(ws, value, device):
 
 # ------------------------------------------------------------------ algorithmic bytes
 def spinor_link_bytes(prec):
-    """(spinor bytes per site, link bytes per link as the stencil reads it, bytes per site of the
-    solution increment e): fp16/bf16 spinors carry a 4-byte norm per site, e is kept in the
-    iteration precision, the mixed modes read 18-real links."""
-    return {"fp64": (192, 144, 192), "fp32": (96, 72, 96), "fp16": (52, 36, 52), "bf16": (52, 36, 52)}[prec]
+    """(spinor bytes per site, algorithmic link bytes per link, bytes per site of the solution
+    increment e): fp16/bf16 spinors carry a 4-byte norm per site, e is kept in the iteration
+    precision; the link bytes are the per-unit figures of the Wilson roofline (FP64 18 reals,
+    FP32 and FP16 / BF16 12 reals), although the mixed-precision stencils read the 18-real form
+    (72 / 36 bytes) -- the extra bytes show in the measured DRAM traffic, not in the algorithmic
+    count."""
+    return {"fp64": (192, 144, 192), "fp32": (96, 48, 96), "fp16": (52, 24, 52), "bf16": (52, 24, 52)}[prec]
 
 
 def kernel_bytes(name, prec, V, c):

@@ -232,6 +232,55 @@ def wilson_quadratures(dims, U, kappa, first, count, z0_seed, tol=1e-13, mass=0.
     return q
 
 
+def gamma5_hermitian_dense(dims, U, kappa, mass=0.0, mass_field=None, csw=0.0):
+    """Q = gamma_5 D as a dense matrix: gamma_5-hermiticity (D^H = gamma_5 D gamma_5) makes Q
+    Hermitian, so its eigenvalues are real and |lambda| runs over the singular values of D.
+    gamma_5 = diag(1, 1, -1, -1) on the spins (chiral basis of operators.gamma_matrices)."""
+    clover = ops.clover_term(U, dims, kappa, csw) if csw else None
+    D = ops.wilson_dense(U, dims, kappa, mass, mass_field, clover=clover)
+    V = int(np.prod(dims))
+    g5 = np.tile(np.repeat([1.0, 1.0, -1.0, -1.0], 3), V)
+    return g5[:, None] * D
+
+
+def wilson_lowest_eigenpairs(dims, U, kappa, k, mass=0.0, mass_field=None, csw=0.0):
+    """The k eigenpairs of Q = gamma_5 D with the smallest |lambda| (numpy's Hermitian
+    eigensolver on the dense Q): returns (evals [k] ordered by |lambda|, evecs [k][V][4][3])."""
+    Q = gamma5_hermitian_dense(dims, U, kappa, mass, mass_field, csw)
+    Q = 0.5 * (Q + np.conj(Q).T)   # Hermitian up to the rounding of its assembly
+    lam, W = np.linalg.eigh(Q)
+    order = np.argsort(np.abs(lam), kind="stable")[:k]
+    V = int(np.prod(dims))
+    return lam[order], np.ascontiguousarray(W[:, order].T.reshape(k, V, 4, 3))
+
+
+def wilson_deflated_quadratures(dims, U, kappa, evals, evecs, first, count, z0_seed, mass=0.0,
+                                mass_field=None, csw=0.0):
+    """Deflated probing of the Wilson matrix, written out literally.  With eigenpairs
+    Q w_j = lambda_j w_j of Q = gamma_5 D (evecs [k][V][4][3], orthonormal) and the left vectors
+    u_j = gamma_5 w_j (D^-1 u_j = Q^-1 w_j = w_j / lambda_j; U = [u_j] is orthonormal),
+        D^-1 = D^-1 U U^H + D^-1 (I - U U^H),  Tr D^-1 = sum_j (w_j^H gamma_5 w_j) / lambda_j + Tr(D^-1 (I - U U^H)),
+    and the second term is probed with the diluted vectors:
+        q_m = sum_a v_{m,a}^H D^-1 (I - U U^H) v_{m,a}    (dense solves).
+    Returns (q [count], the exact part sum_j (w_j^H gamma_5 w_j) / lambda_j)."""
+    W = probe_vectors(dims, first, count, z0_seed)
+    V = W.shape[1]
+    clover = ops.clover_term(U, dims, kappa, csw) if csw else None
+    D = ops.wilson_dense(U, dims, kappa, mass, mass_field, clover=clover)
+    g5 = np.tile(np.repeat([1.0, 1.0, -1.0, -1.0], 3), V)
+    Wv = np.asarray(evecs).reshape(len(evals), 12 * V).T          # columns w_j
+    Uv = g5[:, None] * Wv                                           # columns u_j = gamma_5 w_j
+    B = np.zeros((12 * V, 12 * count), dtype=complex)
+    for m in range(count):
+        for a in range(12):
+            B[:, 12 * m + a] = _dilute(W[m], a).reshape(-1)
+    Bp = B - Uv @ (np.conj(Uv).T @ B)
+    X = solvers.dense_solve(D, Bp)
+    q = np.array([sum(np.vdot(B[:, 12 * m + a], X[:, 12 * m + a]) for a in range(12)) for m in range(count)])
+    exact = sum(np.vdot(Wv[:, j], g5 * Wv[:, j]) / evals[j] for j in range(len(evals)))
+    return q, complex(exact)
+
+
 def wilson_grad_mass_field(dims, U, kappa, s, z0_seed, tol=1e-13, mass=0.0, mass_field=None,
                            method="bicgstab", csw=0.0):
     """dT_s/dmu(x) = -(1/s) sum_{m<s,a} sum_c conj(y(x,c)) x(x,c), y = D^-H v solved explicitly."""

@@ -26,5 +26,14 @@ def free_wilson_trace_inverse(dims, kappa, mass=0.0):
     return float(np.sum(12.0 * a / (a * a + b2)))
 
 
+def free_wilson_singular_values(dims, kappa, mass=0.0):
+    """Singular values of D for U = 1, each of multiplicity 12: with D(p) = a + i g.b as above
+    (the g_mu Hermitian and anticommuting), D(p)^H D(p) = (a - i g.b)(a + i g.b) = a^2 + b^2."""
+    ps = np.meshgrid(*[2 * np.pi * np.arange(L) / L for L in dims], indexing="ij")
+    a = 1.0 + mass - 2 * kappa * sum(np.cos(p) for p in ps)
+    b2 = sum((2 * kappa * np.sin(p)) ** 2 for p in ps)
+    return np.repeat(np.sqrt(a * a + b2).reshape(-1), 12)
+
+
 def torus_distance(x, y, dims):
     return sum(min(abs(a - b), L - abs(a - b)) for a, b, L in zip(x, y, dims))

@@ -9,7 +9,8 @@ from oracle import operators as O
 from oracle import permutation as P
 from oracle import probing as Pr
 from paper_1302_4018_gb300 import synth
-from pins import free_wilson_trace_inverse, laplacian_eigenvalues, laplacian_trace_inverse
+from pins import (free_wilson_singular_values, free_wilson_trace_inverse, laplacian_eigenvalues,
+                  laplacian_trace_inverse)
 
 
 def test_prefix_sequential_vs_kahan():
@@ -318,3 +319,99 @@ def test_lowest_eigenpairs_match_the_fourier_spectrum():
     assert np.allclose(V @ V.T, np.eye(9), atol=1e-12)
     A = O.laplacian_dense(dims, mass)
     assert np.abs(A @ V.T - V.T * lam[None, :]).max() <= 1e-12
+
+
+# ------------------------------------------------------------------ Wilson deflation (gamma_5 D)
+def test_gamma5_wilson_spectrum_is_the_free_field_closed_form():
+    """U = 1: |lambda(gamma_5 D)| are the singular values sqrt(a^2 + b^2) of the plane waves."""
+    dims, kappa, mass = (4, 2, 2, 4), 0.11, 0.05
+    U = synth.gauge_links(dims, 0.0, 1)
+    assert np.allclose(U, np.broadcast_to(np.eye(3), U.shape))
+    Q = E.gamma5_hermitian_dense(dims, U, kappa, mass)
+    assert np.abs(Q - np.conj(Q).T).max() <= 1e-14
+    lam = np.linalg.eigvalsh(Q)
+    assert np.allclose(np.sort(np.abs(lam)), np.sort(free_wilson_singular_values(dims, kappa, mass)), rtol=1e-12,
+                       atol=0)
+
+
+def test_wilson_eigenpairs_are_gamma5_eigenpairs():
+    """Q w = lambda w with Q = gamma_5 D applied by the stencil (not the dense matrix), and the
+    pairs come in increasing |lambda|."""
+    dims, kappa = (2, 4, 2, 2), 0.12
+    U = synth.gauge_links(dims, 0.4, 3)
+    lam, W = E.wilson_lowest_eigenpairs(dims, U, kappa, 10, mass=0.02)
+    assert np.all(np.diff(np.abs(lam)) >= 0)
+    g5 = np.array([1.0, 1.0, -1.0, -1.0])[None, :, None]
+    for j in range(10):
+        r = g5 * O.wilson_apply(W[j], U, dims, kappa, 0.02) - lam[j] * W[j]
+        assert np.linalg.norm(r) <= 1e-12
+        assert abs(np.vdot(W[j], W[j]) - 1) <= 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 7, 30])
+def test_wilson_deflated_full_sequence_is_exact(k):
+    """At s = N the diluted probe vectors span everything, so the probed part is
+    Tr(D^-1 (I - U U^H)) and T_N = sum_j w_j^H g5 w_j / lambda_j + Tr(D^-1 (I - U U^H)) = Tr D^-1
+    (dense inverse), for any k."""
+    dims, kappa = (2, 2, 2, 4), 0.12
+    U = synth.gauge_links(dims, 0.4, 5)
+    lam, W = E.wilson_lowest_eigenpairs(dims, U, kappa, k)
+    q, exact = E.wilson_deflated_quadratures(dims, U, kappa, lam, W, 0, 32, z0_seed=4)
+    T = exact + E.trace_prefix(q)
+    ref = np.trace(np.linalg.inv(O.wilson_dense(U, dims, kappa)))
+    assert abs(T[-1] - ref) <= 1e-11 * abs(ref)
+
+
+def test_wilson_deflating_every_eigenvector_leaves_nothing_to_probe():
+    """k = 12 V: U U^H = I, every quadrature vanishes and T_s = Tr D^-1 for every s; the trace is
+    real (gamma_5-hermiticity)."""
+    dims, kappa = (2, 2, 2, 2), 0.12
+    U = synth.gauge_links(dims, 0.4, 6)
+    lam, W = E.wilson_lowest_eigenpairs(dims, U, kappa, 192)
+    q, exact = E.wilson_deflated_quadratures(dims, U, kappa, lam, W, 0, 6, z0_seed=2)
+    assert np.abs(q).max() <= 1e-11
+    ref = np.trace(np.linalg.inv(O.wilson_dense(U, dims, kappa)))
+    assert abs(exact - ref) <= 1e-11 * abs(ref) and abs(ref.imag) <= 1e-11 * abs(ref)
+
+
+def test_wilson_deflated_quadrature_is_the_plain_one_minus_a_projection_sum():
+    """q'_m = q_m - sum_a g5_a sum_j |v_{m,a}^H w_j|^2 / lambda_j: the correction that turns plain
+    quadratures into deflated ones without changing the solves (D^-1 u_j = w_j / lambda_j and
+    u_j^H v = g5_a conj(v^H w_j) for a vector supported on component a)."""
+    dims, kappa = (2, 2, 4, 2), 0.115
+    U = synth.gauge_links(dims, 0.3, 7)
+    mf = synth.mass_field(dims, 0.01, 8)
+    lam, W = E.wilson_lowest_eigenpairs(dims, U, kappa, 9, mass_field=mf)
+    qd, _ = E.wilson_deflated_quadratures(dims, U, kappa, lam, W, 0, 8, z0_seed=3, mass_field=mf)
+    q0 = E.wilson_quadratures(dims, U, kappa, 0, 8, 3, mass_field=mf, method="dense")
+    P = E.probe_vectors(dims, 0, 8, 3)
+    g5 = np.repeat([1.0, 1.0, -1.0, -1.0], 3)
+    Wf = W.reshape(9, -1, 12)
+    corr = np.array([sum(g5[a] * np.abs(np.vdot(P[m], Wf[j, :, a])) ** 2 / lam[j] for a in range(12) for j in range(9))
+                     for m in range(8)])
+    assert np.allclose(qd, q0 - corr, rtol=0, atol=1e-11 * np.abs(q0).max())
+
+
+def test_wilson_deflation_reduces_the_z0_variance():
+    """The exact z_0-variance of T_s falls when D^-1 is replaced by D^-1 (I - U U^H) with the 24
+    smallest |lambda(gamma_5 D)| removed (rough links near the critical kappa).  With full
+    dilution sum_a (z (x) e_a)^H B (z (x) e_a) = z^T Bt z, Bt[x, y] the trace of the 12 x 12 block
+    B[x, y], so the variance is z0_variance of the block traces."""
+    from oracle import probing as Pr
+
+    dims, kappa = (4, 4, 2, 2), 0.124
+    U = synth.gauge_links(dims, 0.5, 9)
+    D = O.wilson_dense(U, dims, kappa)
+    lam, W = E.wilson_lowest_eigenpairs(dims, U, kappa, 24)
+    V = int(np.prod(dims))
+    g5 = np.tile(np.repeat([1.0, 1.0, -1.0, -1.0], 3), V)
+    Uv = g5[:, None] * W.reshape(24, -1).T
+    B = np.linalg.inv(D)
+    Bd = B @ (np.eye(12 * V) - Uv @ np.conj(Uv).T)
+    def block_traces(M):
+        return np.einsum("xaya->xy", M.reshape(V, 12, V, 12))
+
+    ph, _ = Pr.probe_phases(dims, 0, 32, 0)
+    Z = 1 - 2 * ph
+    for s in (4, 8, 16):
+        assert E.z0_variance(block_traces(Bd), Z, s) < 0.7 * E.z0_variance(block_traces(B), Z, s)
