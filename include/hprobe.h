@@ -271,9 +271,10 @@ hp_status hp_trace_inv_bounds(hp_ctx* ctx, const hp_operator* op, const hp_latti
                               double quad_tol, double lambda_min, const hp_solver_opts* opts,
                               double* trace_prefix, double* T_lower, double* T_upper, hp_solve_stats* stats);
 
-/* Deflated hierarchical probing of the (real symmetric positive definite)
- * Laplacian: the variance reduction that the paper's conclusions name as the
- * next step after probing.  With k orthonormal real eigenvectors V of A
+/* Deflated hierarchical probing: the variance reduction that the paper's
+ * conclusions name as the next step after probing.
+ *
+ * Laplacian (real symmetric positive definite).  With k orthonormal real eigenvectors V of A
  * (evecs: double[k][V] in the canonical site order, host or device) and their
  * eigenvalues (evals: host double[k], all > 0), P = I - V V^T and
  *   Tr A^-1 = sum_j 1/lambda_j + Tr(A^-1 P),
@@ -283,13 +284,54 @@ hp_status hp_trace_inv_bounds(hp_ctx* ctx, const hp_operator* op, const hp_latti
  * The identity needs V to span an invariant subspace (eigenvectors): other
  * vectors give a biased estimate.  Removing the lowest modes removes the long-
  * range part of A^-1 that the colouring cannot, so T_s converges faster.
- * q_inout, trace_prefix, stats as hp_trace_inv; opts->first must be 0.
- * Errors: HP_EINVAL for a Wilson operator, k outside [1, V], NULL arrays or an
- * eigenvalue <= 0; as hp_trace_inv otherwise. */
+ *
+ * Wilson.  With k orthonormal eigenvectors w_j of the Hermitian Q = gamma_5 D
+ * (gamma_5-hermiticity; evecs: complex double[k][V][4][3], host or device) and
+ * their real eigenvalues lambda_j (host double[k], non-zero; hp_wilson_eigs
+ * computes them), the left vectors u_j = gamma_5 w_j are orthonormal and
+ * D^-1 u_j = w_j / lambda_j, so
+ *   Tr D^-1 = sum_j (w_j^H gamma_5 w_j) / lambda_j + Tr(D^-1 (I - U U^H)),
+ * and the second term is probed: q_m = sum_a v_{m,a}^H D^-1 (I - U U^H) v_{m,a}.
+ * The solves are the plain ones of hp_trace_inv (any precision and options);
+ * each quadrature is then corrected on the device by
+ *   - sum_a gamma_5(a) sum_j |v_{m,a}^H w_j|^2 / lambda_j,
+ * whose projections of the first s_max vectors onto the w_j follow from sums
+ * of the w_j over the blocks of hierarchical positions the vectors are
+ * constant on (Walsh-Hadamard sums; every position its own block past the
+ * binary levels).  Hierarchical vectors only (probe_kind 0).
+ *
+ * q_inout (the deflated quadratures), trace_prefix, stats as hp_trace_inv;
+ * opts->first must be 0.  Errors: HP_EINVAL for k outside [1, V] (Laplacian)
+ * or [1, 12 V] (Wilson), NULL arrays, a Laplacian eigenvalue <= 0 or a Wilson
+ * eigenvalue 0; HP_EUNSUPPORTED for another probe kind (Wilson); as
+ * hp_trace_inv otherwise. */
 hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k,
                                 const double* evecs, const double* evals, int64_t s_max, double tol,
                                 const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
                                 hp_solve_stats* stats);
+
+/* The k eigenpairs of Q = gamma_5 D (Wilson or Clover-Wilson; Hermitian by
+ * gamma_5-hermiticity, real eigenvalues of either sign) with the smallest
+ * |lambda| -- the smallest singular values of D, the modes hp_trace_inv_deflated
+ * removes from the Wilson trace.  Chebyshev-filtered subspace iteration on
+ * complex spinor blocks of b = k + max(8, k/2) vectors: each sweep filters the
+ * block with a degree-12 Chebyshev polynomial of Q^2 = D^H D (positive
+ * semidefinite, the same eigenvectors) damping [largest Ritz value of Q^2 on
+ * the block, ||D||^2 bound], orthonormalises it (Cholesky QR), and takes the
+ * Rayleigh-Ritz pairs of Q^2 on the block, then those of Q inside the span of
+ * the k lowest (Q is indefinite: its Ritz values on a block that mixes both
+ * ends of the spectrum can fall anywhere, near 0 included); k should sit at a
+ * gap of |lambda| (a +-pair of nearly equal |lambda| split by k converges
+ * slowly).  FP64 throughout (the FP64 Wilson stencil, complex Gram
+ * matrices and block rotations on the device; b x b Hermitian Cholesky and
+ * Jacobi on the host).  Stops when ||Q w_j - lambda_j w_j|| <= tol |lambda_j|
+ * for j < k, or after max_sweeps (0: 200; then HP_ENOCONV, outputs hold the
+ * last iterate).  evecs: complex double[k][V][4][3] (host or device), w_j
+ * orthonormal; evals (host double[k]): lambda_j ordered by |lambda_j|; resid
+ * (host double[k], nullable): the relative residuals.  Errors: HP_EINVAL for a
+ * Laplacian, k outside [1, 6 V], tol <= 0, NULL outputs. */
+hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k, double tol,
+                         int32_t max_sweeps, double* evecs, double* evals, double* resid);
 
 /* The k lowest eigenpairs of the shifted Laplacian (real symmetric positive
  * definite; mass field allowed): the eigenvectors hp_trace_inv_deflated removes

@@ -12,6 +12,8 @@
 hp_status hp_apply_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrhs, int prec, const double* in,
                           double* out);
 hp_status hp_apply_laplace(hp_ctx* ctx, LatGeom g, int nrhs, const double* in, double* out);
+hp_status hp_wilson_deflation(hp_ctx* ctx, const LatGeom& g, int k, const double2* W, const double* lam,
+                              int64_t s_max, double2* q, double* exact_dev);
 hp_status hp_schur_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrhs, int prec, int eo_kernel,
                           const double* in, double* out);
 hp_status hp_bench_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int prec, int nrhs, int iters, double* ms,
@@ -22,9 +24,9 @@ hp_status hp_bench_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int pre
 // sum_j 1/lambda_j (nlam eigenvalues lam) to every T_s.
 __global__ void k_trace_prefix(const double2* __restrict__ qj, int dof, const double2* __restrict__ q_prev,
                                int first, int s_max, double2* __restrict__ q_out, double2* __restrict__ T,
-                               const double* __restrict__ lam, int nlam) {
+                               const double* __restrict__ lam, int nlam, const double* __restrict__ exact0) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  double exact = 0.0;
+  double exact = exact0 ? *exact0 : 0.0;
   for (int j = 0; j < nlam; ++j) exact += 1.0 / lam[j];
   double2 acc = make_double2(0.0, 0.0);
   for (int m = 0; m < s_max; ++m) {
@@ -207,7 +209,8 @@ static hp_status finish_trace(hp_ctx* ctx, const SolveResult& res, int L, int do
     HP_CUDA(cudaMemcpyAsync(qprev, q_inout, sizeof(double2) * (size_t)first, cudaMemcpyHostToDevice, ctx->stream));
   {
     ProfScope ps(ctx, "k_trace_prefix");
-    k_trace_prefix<<<1, 32, 0, ctx->stream>>>(qj, dof, qprev, (int)first, (int)s_max, qout, T, lam_dev, nlam);
+    k_trace_prefix<<<1, 32, 0, ctx->stream>>>(qj, dof, qprev, (int)first, (int)s_max, qout, T, lam_dev, nlam,
+                                              nullptr);
   }
   HP_LAUNCH_CHECK();
   if (q_inout)
@@ -404,9 +407,68 @@ extern "C" hp_status hp_trace_prefix(hp_ctx* ctx, int64_t s_max, const double* q
   HP_CUDA(cudaMemcpyAsync(qprev, q, sizeof(double2) * (size_t)s_max, cudaMemcpyDefault, ctx->stream));
   {
     ProfScope ps(ctx, "k_trace_prefix");
-    k_trace_prefix<<<1, 32, 0, ctx->stream>>>(nullptr, 0, qprev, (int)s_max, (int)s_max, qout, T, nullptr, 0);
+    k_trace_prefix<<<1, 32, 0, ctx->stream>>>(nullptr, 0, qprev, (int)s_max, (int)s_max, qout, T, nullptr, 0,
+                                              nullptr);
   }
   HP_LAUNCH_CHECK();
+  HP_CUDA(cudaMemcpyAsync(trace_prefix, T, sizeof(double2) * (size_t)s_max, cudaMemcpyDefault, ctx->stream));
+  HP_CUDA(cudaStreamSynchronize(ctx->stream));
+  return HP_OK;
+}
+
+// deflated probing of the Wilson matrix: the plain solves, then the deflation correction of each
+// quadrature and the exact part on the device (hp_wdefl.cu)
+static hp_status trace_deflated_wilson(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k,
+                                       const double* evecs, const double* evals, int64_t s_max, double tol,
+                                       const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
+                                       hp_solve_stats* stats) {
+  HP_TRY(check_ctx(ctx));
+  LatGeom g;
+  HP_TRY(operator_geom(ctx, op, lat, &g, nullptr));
+  if (!opts || !trace_prefix) {
+    hp_set_error("deflation: solver options and trace_prefix required");
+    return HP_EINVAL;
+  }
+  HP_TRY(set_probe_kind(opts, s_max, &g));
+  if (opts->probe_kind != HP_PROBE_HIERARCHICAL) {
+    hp_set_error("deflated Wilson probing uses the hierarchical vectors (probe_kind 0)");
+    return HP_EUNSUPPORTED;
+  }
+  if (k < 1 || (int64_t)k > 12LL * g.V || !evecs || !evals) {
+    hp_set_error("deflation: 1 <= k <= 12 V and non-NULL eigenvectors and eigenvalues required (k = %d)", k);
+    return HP_EINVAL;
+  }
+  for (int j = 0; j < k; ++j)
+    if (!(evals[j] != 0.0) || !std::isfinite(evals[j])) {
+      hp_set_error("deflation: eigenvalue %d of gamma_5 D is %g", j, evals[j]);
+      return HP_EINVAL;
+    }
+  std::vector<double> qraw(2 * (size_t)s_max, 0.0), Traw(2 * (size_t)s_max, 0.0);
+  HP_TRY(trace_common(ctx, op, lat, s_max, tol, opts, qraw.data(), Traw.data(), nullptr, nullptr, stats));
+  const void* p = nullptr;
+  HP_TRY(hp_device_view(ctx, evecs, sizeof(double2) * 12 * (size_t)k * g.V, "wdefl.W", &p));
+  const double2* W = (const double2*)p;
+  void* v = nullptr;
+  HP_TRY(hp_ws(ctx, "wdefl.lam", sizeof(double) * (size_t)k, &v));
+  double* lam = (double*)v;
+  HP_CUDA(cudaMemcpyAsync(lam, evals, sizeof(double) * (size_t)k, cudaMemcpyHostToDevice, ctx->stream));
+  HP_TRY(hp_ws(ctx, "wdefl.exact", sizeof(double), &v));
+  double* exact = (double*)v;
+  HP_TRY(hp_ws(ctx, "trace.qprev", sizeof(double2) * (size_t)s_max, &v));
+  double2* qprev = (double2*)v;
+  HP_TRY(hp_ws(ctx, "trace.qout", sizeof(double2) * (size_t)s_max, &v));
+  double2* qout = (double2*)v;
+  HP_TRY(hp_ws(ctx, "trace.T", sizeof(double2) * (size_t)s_max, &v));
+  double2* T = (double2*)v;
+  HP_CUDA(cudaMemcpyAsync(qprev, qraw.data(), sizeof(double2) * (size_t)s_max, cudaMemcpyHostToDevice, ctx->stream));
+  HP_TRY(hp_wilson_deflation(ctx, g, k, W, lam, s_max, qprev, exact));
+  {
+    ProfScope ps(ctx, "k_trace_prefix");
+    k_trace_prefix<<<1, 32, 0, ctx->stream>>>(nullptr, 0, qprev, (int)s_max, (int)s_max, qout, T, nullptr, 0, exact);
+  }
+  HP_LAUNCH_CHECK();
+  if (q_inout)
+    HP_CUDA(cudaMemcpyAsync(q_inout, qout, sizeof(double2) * (size_t)s_max, cudaMemcpyDefault, ctx->stream));
   HP_CUDA(cudaMemcpyAsync(trace_prefix, T, sizeof(double2) * (size_t)s_max, cudaMemcpyDefault, ctx->stream));
   HP_CUDA(cudaStreamSynchronize(ctx->stream));
   return HP_OK;
@@ -416,8 +478,15 @@ extern "C" hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, c
                                            const double* evecs, const double* evals, int64_t s_max, double tol,
                                            const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
                                            hp_solve_stats* stats) {
+  if (op && op->kind == HP_OP_WILSON) {
+    if (opts && opts->first != 0) {
+      hp_set_error("deflated probing needs first == 0");
+      return HP_EINVAL;
+    }
+    return trace_deflated_wilson(ctx, op, lat, k, evecs, evals, s_max, tol, opts, q_inout, trace_prefix, stats);
+  }
   if (!op || op->kind != HP_OP_LAPLACIAN) {
-    hp_set_error("deflated probing serves the (real symmetric) Laplacian");
+    hp_set_error("deflated probing needs a Laplacian or Wilson operator");
     return HP_EINVAL;
   }
   std::vector<int64_t> dims;

@@ -11,14 +11,24 @@
 // Everything on the device is FP64: the Laplacian stencil (hp_apply_laplace), the recurrence, the
 // Gram matrices (32 x 32 tiles of X^T Y over site chunks, partial sums added in a fixed order) and
 // the block rotations X W; the host works on b x b matrices only.
+//
+// The Wilson operator's counterpart (hp_wilson_eigs) runs the same iteration on complex spinor
+// blocks for Q = gamma_5 D, Hermitian by gamma_5-hermiticity: the filter and the first
+// Rayleigh-Ritz step act on Q^2 = D^H D (positive semidefinite, the same eigenvectors; Q itself is
+// indefinite, and its Ritz values on an unconverged block can fall anywhere), a second Rayleigh-Ritz
+// step with Q inside the span of the k lowest Q^2 Ritz vectors gives the pairs with their signed
+// eigenvalues, ordered by |lambda| (the singular values of D).
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <vector>
 
 #include "hp_internal.h"
 
 hp_status hp_apply_laplace(hp_ctx* ctx, LatGeom g, int nrhs, const double* in, double* out);
+hp_status hp_apply_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrhs, int prec, const double* in,
+                          double* out);
 
 namespace {
 
@@ -255,6 +265,271 @@ struct EigWork {
   }
 };
 
+// ---------------------------------------------------------------- complex blocks (gamma_5 D)
+constexpr int ZCH = 16;         // complex entries per shared-memory chunk of the complex Gram
+constexpr int ZJ = 8;           // outputs per thread of the complex block rotation
+typedef std::complex<double> zd;
+
+__device__ __forceinline__ double2 zacc_conj(double2 x, double2 y, double2 acc) {   // acc + conj(x) y
+  acc.x = fma(x.x, y.x, acc.x);
+  acc.x = fma(x.y, y.y, acc.x);
+  acc.y = fma(x.x, y.y, acc.y);
+  acc.y = fma(-x.y, y.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ double2 zacc(double2 x, double2 w, double2 acc) {   // acc + x w
+  acc.x = fma(x.x, w.x, acc.x);
+  acc.x = fma(-x.y, w.y, acc.x);
+  acc.y = fma(x.x, w.y, acc.y);
+  acc.y = fma(x.y, w.x, acc.y);
+  return acc;
+}
+
+// partial complex Gram matrices: part[bx][i][j] = sum over the entries of chunk bx of conj(X[i][e]) Y[j][e]
+// (vectors of n complex entries); 16 x 16 threads, 2 x 2 entries each
+__global__ void __launch_bounds__(256) k_zeig_gram(const double2* __restrict__ X, const double2* __restrict__ Y,
+                                                   long long n, int b, long long per_block, double2* __restrict__ part) {
+  __shared__ double2 xs[GT][ZCH + 1], ys[GT][ZCH + 1];
+  const int ntj = (b + GT - 1) / GT;
+  const int i0 = (blockIdx.y / ntj) * GT, j0 = (blockIdx.y % ntj) * GT;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double2 acc[2][2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) acc[u][v] = make_double2(0.0, 0.0);
+  const long long e_begin = (long long)blockIdx.x * per_block;
+  const long long e_end = std::min<long long>(n, e_begin + per_block);
+  for (long long e0 = e_begin; e0 < e_end; e0 += ZCH) {
+    for (int t = threadIdx.x; t < GT * ZCH; t += 256) {
+      const int r = t / ZCH, c = t % ZCH;
+      const long long e = e0 + c;
+      xs[r][c] = (i0 + r < b && e < e_end) ? X[(size_t)(i0 + r) * n + e] : make_double2(0.0, 0.0);
+      ys[r][c] = (j0 + r < b && e < e_end) ? Y[(size_t)(j0 + r) * n + e] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int c = 0; c < ZCH; ++c) {
+      const double2 x0 = xs[2 * ty][c], x1 = xs[2 * ty + 1][c];
+      const double2 y0 = ys[2 * tx][c], y1 = ys[2 * tx + 1][c];
+      acc[0][0] = zacc_conj(x0, y0, acc[0][0]);
+      acc[0][1] = zacc_conj(x0, y1, acc[0][1]);
+      acc[1][0] = zacc_conj(x1, y0, acc[1][0]);
+      acc[1][1] = zacc_conj(x1, y1, acc[1][1]);
+    }
+    __syncthreads();
+  }
+  double2* p = part + (size_t)blockIdx.x * b * b;
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int i = i0 + 2 * ty + u, j = j0 + 2 * tx + v;
+      if (i < b && j < b) p[(size_t)i * b + j] = acc[u][v];
+    }
+}
+
+// Z[j][e] = sum_i X[i][e] W[i][j] for the ZJ outputs j of blockIdx.y (W complex, row-major b x b)
+__global__ void k_zeig_rotate(const double2* __restrict__ X, const double2* __restrict__ W, long long n, int b,
+                              double2* __restrict__ Z) {
+  const int j0 = blockIdx.y * ZJ;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    double2 acc[ZJ];
+#pragma unroll
+    for (int j = 0; j < ZJ; ++j) acc[j] = make_double2(0.0, 0.0);
+    for (int i = 0; i < b; ++i) {
+      const double2 x = X[(size_t)i * n + e];
+      const double2* w = W + (size_t)i * b + j0;
+#pragma unroll
+      for (int j = 0; j < ZJ; ++j)
+        if (j0 + j < b) acc[j] = zacc(x, __ldg(w + j), acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < ZJ; ++j)
+      if (j0 + j < b) Z[(size_t)(j0 + j) * n + e] = acc[j];
+  }
+}
+
+// X <- gamma_5 X on spinor fields [..][V][4][3]: gamma_5 = diag(1, 1, -1, -1) on the spins (chiral basis)
+__global__ void k_gamma5(double2* __restrict__ X, long long total) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x)
+    if ((t % 12) >= 6) X[t] = make_double2(-X[t].x, -X[t].y);
+}
+
+// Cholesky G = R^H R of a Hermitian G (upper R, row-major); false if a pivot is not positive
+bool cholesky_upper_z(std::vector<zd>& G, int b) {
+  for (int j = 0; j < b; ++j) {
+    double d = G[(size_t)j * b + j].real();
+    for (int k = 0; k < j; ++k) d -= std::norm(G[(size_t)k * b + j]);
+    if (!(d > 0.0) || !std::isfinite(d)) return false;
+    const double r = std::sqrt(d);
+    G[(size_t)j * b + j] = r;
+    for (int i = j + 1; i < b; ++i) {
+      zd v = G[(size_t)j * b + i];
+      for (int k = 0; k < j; ++k) v -= std::conj(G[(size_t)k * b + j]) * G[(size_t)k * b + i];
+      G[(size_t)j * b + i] = v / r;
+    }
+    for (int i = 0; i < j; ++i) G[(size_t)j * b + i] = 0.0;
+  }
+  return true;
+}
+
+void invert_upper_z(std::vector<zd>& R, int b) {
+  std::vector<zd> Ri((size_t)b * b, 0.0);
+  for (int j = 0; j < b; ++j) {
+    Ri[(size_t)j * b + j] = 1.0 / R[(size_t)j * b + j];
+    for (int i = j - 1; i >= 0; --i) {
+      zd v = 0.0;
+      for (int k = i + 1; k <= j; ++k) v += R[(size_t)i * b + k] * Ri[(size_t)k * b + j];
+      Ri[(size_t)i * b + j] = -v / R[(size_t)i * b + i];
+    }
+  }
+  R.swap(Ri);
+}
+
+// cyclic Jacobi for a Hermitian H (row-major): H = W diag(theta) W^H, ordered by |theta|.  Each
+// rotation first turns h_pq real (column q times e^{-i phi}, row q times e^{i phi}, phi = arg h_pq),
+// then applies the real Jacobi rotation of the symmetric case.
+void jacobi_eigh_z(std::vector<zd> H, int b, std::vector<double>& theta, std::vector<zd>& W) {
+  W.assign((size_t)b * b, 0.0);
+  for (int i = 0; i < b; ++i) W[(size_t)i * b + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < b; ++i)
+      for (int j = 0; j < b; ++j) {
+        const double v = std::norm(H[(size_t)i * b + j]);
+        tot += v;
+        if (i != j) off += v;
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < b - 1; ++p)
+      for (int q = p + 1; q < b; ++q) {
+        const zd hpq = H[(size_t)p * b + q];
+        const double apq = std::abs(hpq);
+        if (apq == 0.0) continue;
+        const zd ph = std::conj(hpq) / apq;   // e^{-i phi}
+        for (int k = 0; k < b; ++k) {
+          H[(size_t)k * b + q] *= ph;
+          W[(size_t)k * b + q] *= ph;
+        }
+        for (int k = 0; k < b; ++k) H[(size_t)q * b + k] *= std::conj(ph);
+        const double app = H[(size_t)p * b + p].real(), aqq = H[(size_t)q * b + q].real();
+        const double tau = (aqq - app) / (2.0 * apq);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+        for (int k = 0; k < b; ++k) {   // columns p, q
+          const zd hkp = H[(size_t)k * b + p], hkq = H[(size_t)k * b + q];
+          H[(size_t)k * b + p] = c * hkp - s * hkq;
+          H[(size_t)k * b + q] = s * hkp + c * hkq;
+        }
+        for (int k = 0; k < b; ++k) {   // rows p, q
+          const zd hpk = H[(size_t)p * b + k], hqk = H[(size_t)q * b + k];
+          H[(size_t)p * b + k] = c * hpk - s * hqk;
+          H[(size_t)q * b + k] = s * hpk + c * hqk;
+        }
+        for (int k = 0; k < b; ++k) {
+          const zd wkp = W[(size_t)k * b + p], wkq = W[(size_t)k * b + q];
+          W[(size_t)k * b + p] = c * wkp - s * wkq;
+          W[(size_t)k * b + q] = s * wkp + c * wkq;
+        }
+      }
+  }
+  std::vector<int> order(b);
+  for (int i = 0; i < b; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    return std::fabs(H[(size_t)a * b + a].real()) < std::fabs(H[(size_t)c * b + c].real());
+  });
+  theta.resize(b);
+  std::vector<zd> Ws((size_t)b * b);
+  for (int j = 0; j < b; ++j) {
+    theta[j] = H[(size_t)order[j] * b + order[j]].real();
+    for (int i = 0; i < b; ++i) Ws[(size_t)i * b + j] = W[(size_t)i * b + order[j]];
+  }
+  W.swap(Ws);
+}
+
+struct ZEigWork {
+  hp_ctx* ctx;
+  const hp_operator* op;
+  LatGeom g;
+  long long n;   // complex entries per vector (12 V)
+  int b;
+  double2 *X, *Y, *Z, *T, *part, *Gd, *Wd;
+  int nbx;
+  long long epb;
+
+  // out = Q in = gamma_5 D in for the b vectors (FP64 stencil)
+  hp_status apply_q(const double2* in, double2* out) {
+    HP_TRY(hp_apply_wilson(ctx, op, g, b, HP_PREC_FP64, (const double*)in, (double*)out));
+    const long long tot = n * b;
+    k_gamma5<<<blocks_for(ctx, tot, 256), 256, 0, ctx->stream>>>(out, tot);
+    HP_LAUNCH_CHECK();
+    return HP_OK;
+  }
+  hp_status apply_q2(const double2* in, double2* out) {   // out = Q^2 in (T scratch)
+    HP_TRY(apply_q(in, T));
+    return apply_q(T, out);
+  }
+  hp_status gram(const double2* A, const double2* B, std::vector<zd>& G) {
+    const int nt = (b + GT - 1) / GT;
+    {
+      ProfScope ps(ctx, "k_zeig_gram");
+      k_zeig_gram<<<dim3(nbx, nt * nt), 256, 0, ctx->stream>>>(A, B, n, b, epb, part);
+    }
+    HP_LAUNCH_CHECK();
+    // the complex sum of the partials: the real kernel over both parts
+    k_eig_gram_sum<<<std::max(1, std::min(1024, (2 * b * b + 255) / 256)), 256, 0, ctx->stream>>>(
+        (const double*)part, nbx, 2 * b * b, (double*)Gd);
+    HP_LAUNCH_CHECK();
+    std::vector<double2> raw((size_t)b * b);
+    HP_CUDA(cudaMemcpyAsync(raw.data(), Gd, sizeof(double2) * b * b, cudaMemcpyDeviceToHost, ctx->stream));
+    HP_CUDA(cudaStreamSynchronize(ctx->stream));
+    G.resize((size_t)b * b);
+    for (size_t e = 0; e < G.size(); ++e) G[e] = zd(raw[e].x, raw[e].y);
+    return HP_OK;
+  }
+  hp_status rotate(const double2* in, const std::vector<zd>& W, double2* out) {
+    std::vector<double2> raw((size_t)b * b);
+    for (size_t e = 0; e < raw.size(); ++e) raw[e] = make_double2(W[e].real(), W[e].imag());
+    HP_CUDA(cudaMemcpyAsync(Wd, raw.data(), sizeof(double2) * b * b, cudaMemcpyHostToDevice, ctx->stream));
+    {
+      ProfScope ps(ctx, "k_zeig_rotate");
+      k_zeig_rotate<<<dim3(blocks_for(ctx, n, 256), (b + ZJ - 1) / ZJ), 256, 0, ctx->stream>>>(in, Wd, n, b, out);
+    }
+    HP_LAUNCH_CHECK();
+    HP_CUDA(cudaStreamSynchronize(ctx->stream));   // raw (host) must outlive the copy
+    return HP_OK;
+  }
+  // out = a P + c Q + e R on the real and imaginary parts (real coefficients)
+  hp_status lincomb(double2* out, const double2* P, const double2* Q, const double2* R, double a, double c, double e) {
+    const long long m = 2 * n * b;
+    k_eig_lincomb<<<blocks_for(ctx, m, 256), 256, 0, ctx->stream>>>((double*)out, (const double*)P, (const double*)Q,
+                                                                     (const double*)R, a, c, e, m);
+    HP_LAUNCH_CHECK();
+    return HP_OK;
+  }
+  hp_status orthonormalise() {
+    std::vector<zd> G;
+    for (int pass = 0; pass < 3; ++pass) {
+      HP_TRY(gram(X, X, G));
+      if (pass == 0) {
+        double nrm = 0.0;
+        for (int i = 0; i < b; ++i) nrm = std::max(nrm, G[(size_t)i * b + i].real());
+        const double sh = 11.0 * ((double)n * b + (double)b * (b + 1)) * 2.220446049250313e-16 * nrm;
+        for (int i = 0; i < b; ++i) G[(size_t)i * b + i] += sh;
+      }
+      if (!cholesky_upper_z(G, b)) {
+        hp_set_error("hp_wilson_eigs: the block lost rank (Cholesky QR failed)");
+        return HP_ENOCONV;
+      }
+      invert_upper_z(G, b);
+      HP_TRY(rotate(X, G, Y));
+      std::swap(X, Y);
+    }
+    return HP_OK;
+  }
+};
+
 }  // namespace
 
 extern "C" hp_status hp_laplacian_eigs(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k,
@@ -382,6 +657,169 @@ extern "C" hp_status hp_laplacian_eigs(hp_ctx* ctx, const hp_operator* op, const
   }
   if (!converged) {
     hp_set_error("hp_laplacian_eigs: %d sweeps without reaching tol", sweeps);
+    return HP_ENOCONV;
+  }
+  return HP_OK;
+}
+
+extern "C" hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k, double tol,
+                                    int32_t max_sweeps, double* evecs, double* evals, double* resid) {
+  if (!ctx) {
+    hp_set_error("NULL context");
+    return HP_EINVAL;
+  }
+  HP_CUDA(cudaSetDevice(ctx->device));
+  std::vector<int64_t> dims;
+  HP_TRY(hp_validate_lattice(lat, 4, &dims));
+  if (!op || op->kind != HP_OP_WILSON || !op->links) {
+    hp_set_error("hp_wilson_eigs: a Wilson operator with links is required");
+    return HP_EINVAL;
+  }
+  if (!std::isfinite(op->mass) || !std::isfinite(op->kappa) || !std::isfinite(op->csw)) {
+    hp_set_error("hp_wilson_eigs: mass / kappa / csw not finite");
+    return HP_EINVAL;
+  }
+  LatticeSetup* ls = nullptr;
+  HP_TRY(hp_get_lattice(ctx, dims, &ls));
+  LatGeom g = ls->g;
+  g.nd = 4;
+  for (int j = (int)dims.size(); j < 8; ++j) g.L[j] = 1;
+  g.op_kind = HP_OP_WILSON;
+  g.dof = 12;
+  const int V = g.V;
+  const long long n = 12LL * V;
+  if (k < 1 || 2LL * k > n || !(tol > 0.0) || !evecs || !evals) {
+    hp_set_error("hp_wilson_eigs: k in [1, 6 V], tol > 0 and output arrays required");
+    return HP_EINVAL;
+  }
+  // spectrum bound of Q^2 = D^H D: ||D|| <= |1 + m| + max |mu| + 16 kappa (eight hops of norm 2 kappa)
+  // + 12 csw kappa (six clover planes, ||sigma F|| <= 2)
+  double mu_abs = 0.0;
+  if (op->mass_field) {
+    LatGeom gm = g;
+    HP_TRY(hp_prepare_mass(ctx, op, &gm, "zeigs"));
+    std::vector<double> mf((size_t)V);
+    HP_CUDA(cudaMemcpyAsync(mf.data(), gm.mass_field, sizeof(double) * V, cudaMemcpyDeviceToHost, ctx->stream));
+    HP_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (double v : mf) mu_abs = std::max(mu_abs, std::fabs(v));
+  }
+  const double dnorm = std::fabs(1.0 + op->mass) + mu_abs + 16.0 * std::fabs(op->kappa) +
+                       12.0 * std::fabs(op->csw * op->kappa);
+  const double l_max = dnorm * dnorm, l_low = 0.0;
+  const int b = (int)std::min<long long>(n, k + std::max(8, k / 2));
+  const int m = 12;
+  ZEigWork w;
+  w.ctx = ctx;
+  w.op = op;
+  w.g = g;
+  w.n = n;
+  w.b = b;
+  w.nbx = (int)std::max<long long>(1, std::min<long long>(256, (n + 4095) / 4096));
+  w.epb = (n + w.nbx - 1) / w.nbx;
+  const size_t blk = sizeof(double2) * (size_t)n * b;
+  void* p = nullptr;
+  HP_TRY(hp_ws(ctx, "zeigs.X", blk, &p));
+  w.X = (double2*)p;
+  HP_TRY(hp_ws(ctx, "zeigs.Y", blk, &p));
+  w.Y = (double2*)p;
+  HP_TRY(hp_ws(ctx, "zeigs.Z", blk, &p));
+  w.Z = (double2*)p;
+  HP_TRY(hp_ws(ctx, "zeigs.T", blk, &p));
+  w.T = (double2*)p;
+  HP_TRY(hp_ws(ctx, "zeigs.part", sizeof(double2) * (size_t)w.nbx * b * b, &p));
+  w.part = (double2*)p;
+  HP_TRY(hp_ws(ctx, "zeigs.G", sizeof(double2) * (size_t)b * b, &p));
+  w.Gd = (double2*)p;
+  HP_TRY(hp_ws(ctx, "zeigs.W", sizeof(double2) * (size_t)b * b, &p));
+  w.Wd = (double2*)p;
+  k_eig_fill<<<blocks_for(ctx, 2 * n * b, 256), 256, 0, ctx->stream>>>((double*)w.X, 2 * n * b, 0x5eed5ULL + k);
+  HP_LAUNCH_CHECK();
+  HP_TRY(w.orthonormalise());
+  std::vector<double> theta, rn(k, 0.0);
+  std::vector<zd> W, H;
+  const int sweeps = max_sweeps > 0 ? max_sweeps : 200;
+  bool converged = false;
+  double top2 = 0.0;   // the largest Rayleigh-Ritz value of Q^2 on the block (the filter's damping bound)
+  for (int it = 0; it <= sweeps; ++it) {
+    // Rayleigh-Ritz with Q^2 = (Q X)^H (Q X) on the orthonormal block: the subspace and its order
+    // (Q is indefinite, so its own Ritz values on a block mixing both ends of the spectrum can fall
+    // anywhere, near 0 included; those of Q^2 are bounded by its spectrum)
+    HP_TRY(w.apply_q(w.X, w.Z));
+    HP_TRY(w.gram(w.Z, w.Z, H));
+    for (int i = 0; i < b; ++i) {   // Hermitian part (the rounding)
+      H[(size_t)i * b + i] = H[(size_t)i * b + i].real();
+      for (int j = i + 1; j < b; ++j) {
+        const zd v = 0.5 * (H[(size_t)i * b + j] + std::conj(H[(size_t)j * b + i]));
+        H[(size_t)i * b + j] = v;
+        H[(size_t)j * b + i] = std::conj(v);
+      }
+    }
+    std::vector<double> theta2;
+    jacobi_eigh_z(H, b, theta2, W);   // ascending (theta2 >= 0)
+    top2 = *std::max_element(theta2.begin(), theta2.end());
+    HP_TRY(w.rotate(w.X, W, w.Y));
+    std::swap(w.X, w.Y);
+    HP_TRY(w.rotate(w.Z, W, w.Y));
+    std::swap(w.Z, w.Y);             // Z = Q X in the rotated basis
+    // the eigenpairs of Q inside the span of the k lowest Q^2 Ritz vectors: Rayleigh-Ritz with Q there
+    HP_TRY(w.gram(w.X, w.Z, H));
+    std::vector<zd> Hk((size_t)k * k), W1;
+    for (int i = 0; i < k; ++i) {
+      Hk[(size_t)i * k + i] = H[(size_t)i * b + i].real();
+      for (int j = i + 1; j < k; ++j) {
+        const zd v = 0.5 * (H[(size_t)i * b + j] + std::conj(H[(size_t)j * b + i]));
+        Hk[(size_t)i * k + j] = v;
+        Hk[(size_t)j * k + i] = std::conj(v);
+      }
+    }
+    jacobi_eigh_z(Hk, k, theta, W1);   // ordered by |theta|
+    std::vector<zd> Wb((size_t)b * b, 0.0);
+    for (int i = 0; i < b; ++i) Wb[(size_t)i * b + i] = 1.0;
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) Wb[(size_t)i * b + j] = W1[(size_t)i * k + j];
+    HP_TRY(w.rotate(w.X, Wb, w.Y));
+    std::swap(w.X, w.Y);
+    HP_TRY(w.rotate(w.Z, Wb, w.Y));   // Y = Q X, its first k columns the pairs' Q w_j
+    {
+      std::vector<zd> Dg((size_t)b * b, 0.0);
+      for (int j = 0; j < k; ++j) Dg[(size_t)j * b + j] = -theta[j];
+      HP_TRY(w.rotate(w.X, Dg, w.Z));                                   // Z = -X diag(theta, 0)
+      HP_TRY(w.lincomb(w.Z, w.Y, w.Z, nullptr, 1.0, 1.0, 0.0));         // Z = Q X - X diag(theta)
+      std::vector<zd> RR;
+      HP_TRY(w.gram(w.Z, w.Z, RR));
+      converged = true;
+      for (int j = 0; j < k; ++j) {
+        rn[j] = std::sqrt(std::max(0.0, RR[(size_t)j * b + j].real())) / std::max(std::fabs(theta[j]), 1e-300);
+        if (!(rn[j] <= tol)) converged = false;
+      }
+    }
+    if (converged || it == sweeps) break;
+    // Chebyshev filter of degree m on Q^2 damping [largest Q^2 Ritz value of the block, l_max], scaled at 0
+    const double a = std::min(top2, 0.99 * l_max);
+    const double c0 = 0.5 * (l_max + a), e = 0.5 * (l_max - a);
+    double sigma = e / (l_low - c0);
+    const double tau = 2.0 / sigma;
+    HP_TRY(w.apply_q2(w.X, w.Y));
+    HP_TRY(w.lincomb(w.Y, w.Y, w.X, nullptr, sigma / e, -c0 * sigma / e, 0.0));
+    for (int i = 2; i <= m; ++i) {
+      const double sigma1 = 1.0 / (tau - sigma);
+      HP_TRY(w.apply_q2(w.Y, w.Z));
+      HP_TRY(w.lincomb(w.Z, w.Z, w.Y, w.X, 2.0 * sigma1 / e, -2.0 * sigma1 * c0 / e, -sigma * sigma1));
+      std::swap(w.X, w.Y);
+      std::swap(w.Y, w.Z);
+      sigma = sigma1;
+    }
+    std::swap(w.X, w.Y);
+    HP_TRY(w.orthonormalise());
+  }
+  HP_CUDA(cudaMemcpyAsync(evecs, w.X, sizeof(double2) * (size_t)k * n, cudaMemcpyDefault, ctx->stream));
+  HP_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (int j = 0; j < k; ++j) {
+    evals[j] = theta[j];
+    if (resid) resid[j] = rn[j];
+  }
+  if (!converged) {
+    hp_set_error("hp_wilson_eigs: %d sweeps without reaching tol", sweeps);
     return HP_ENOCONV;
   }
   return HP_OK;

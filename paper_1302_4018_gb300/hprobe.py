@@ -45,7 +45,7 @@ EXPORTED = ["hp_ctx_create", "hp_ctx_destroy", "hp_last_error", "hp_ctx_synchron
             "hp_operator_apply", "hp_dslash_bench", "hp_profile_enable", "hp_profile_report",
             "hp_launch_count", "hp_operator_apply_noalloc", "hp_probe_sequence", "hp_trace_inv_bounds",
             "hp_sparse_coloring", "hp_sparse_ordering", "hp_sparse_probe_vectors", "hp_trace_inv_sparse", "hp_trace_inv_deflated",
-            "hp_trace_inv_solutions", "hp_trace_prefix", "hp_schur_apply", "hp_laplacian_eigs"]
+            "hp_trace_inv_solutions", "hp_trace_prefix", "hp_schur_apply", "hp_laplacian_eigs", "hp_wilson_eigs"]
 
 
 class Lattice(C.Structure):
@@ -122,6 +122,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hp_trace_prefix": (C.c_int, [P, I64, P, P]),
         "hp_schur_apply": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I64, I32, I32, P, P]),
         "hp_laplacian_eigs": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I32, D, I32, P, P, P]),
+        "hp_wilson_eigs": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I32, D, I32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -303,6 +304,19 @@ class Context:
                                        int(max_sweeps), _ptr(evecs), _ptr(evals), _ptr(resid)))
         return evals, evecs, resid
 
+    def wilson_eigs(self, op: Operator, dims, k: int, tol: float = 1e-10, max_sweeps: int = 0, evecs=None):
+        """The k eigenpairs of gamma_5 D (Hermitian) with the smallest |lambda|: (evals [k] signed,
+        ordered by |lambda|, evecs complex [k, V, 4, 3] (host array by default, or the given
+        complex128 array / tensor), resid [k])."""
+        V = int(np.prod(dims))
+        if evecs is None:
+            evecs = np.zeros((k, V, 4, 3), dtype=np.complex128)
+        evals = np.zeros(k)
+        resid = np.zeros(k)
+        _check(lib().hp_wilson_eigs(self._h, C.byref(op), C.byref(make_lattice(dims)), int(k), float(tol),
+                                    int(max_sweeps), _ptr(evecs), _ptr(evals), _ptr(resid)))
+        return evals, evecs, resid
+
     def trace_inv(self, op: Operator, dims, s_max: int, tol: float, opts: SolverOpts, q_inout=None):
         """Returns (T [s_max] complex, q [s_max] complex or None, stats dict).  ``q_inout``: host
         complex128 array of s_max (entries < opts.first are inputs)."""
@@ -412,10 +426,19 @@ class Context:
 
     def trace_inv_deflated(self, op: Operator, dims, evecs, evals, s_max: int, tol: float, opts: SolverOpts,
                            q_inout=None):
-        """Laplacian with k eigenvectors deflated: evecs float64 [k, V] (host array or device
-        tensor), evals float64 [k] (host).  Returns (T [s_max] complex, q, stats)."""
+        """Deflated probing.  Laplacian: evecs float64 [k, V] orthonormal eigenvectors; Wilson: evecs
+        complex128 [k, V, 4, 3] eigenvectors of gamma_5 D (host array or device tensor); evals float64
+        [k] (host) their eigenvalues.  Returns (T [s_max] complex, q (deflated), stats)."""
         ev = np.ascontiguousarray(np.asarray(evals, dtype=np.float64))
         k = int(ev.shape[0])
+        V = int(np.prod(dims))
+        wilson = op.kind == OP_WILSON
+        n_el = int(np.prod(evecs.shape))
+        dt = str(evecs.dtype)   # numpy or torch dtype name
+        if (wilson and not (dt.endswith("complex128") and n_el == 12 * k * V)) or \
+                (not wilson and not (dt.endswith("float64") and n_el == k * V)):
+            raise ValueError("eigenvectors must be %s of %d x %d values" % ("complex" if wilson else "real", k,
+                                                                            (12 if wilson else 1) * V))
         T = np.zeros(s_max, dtype=np.complex128)
         st = SolveStats()
         if q_inout is not None:

@@ -150,3 +150,15 @@ def test_sparse_entry_points_reject_a_missing_context_without_gpu():
                                    rad.ctypes.data, 1, 1, 1e-10, ctypes.byref(opts), None, T.ctypes.data,
                                    None) == hprobe.HP_EINVAL
     assert "context" in lib.hp_last_error().decode().lower()
+
+
+def test_eigensolvers_reject_a_missing_context_without_gpu():
+    from paper_1302_4018_gb300 import hprobe
+
+    lib = hprobe.lib()
+    lat = hprobe.make_lattice((4, 4, 4, 4))
+    op = hprobe.Operator(kind=hprobe.OP_WILSON, kappa=0.12)
+    ev = np.zeros(8)
+    for fn in (lib.hp_wilson_eigs, lib.hp_laplacian_eigs):
+        assert fn(None, ctypes.byref(op), ctypes.byref(lat), 2, 1e-10, 0, ev.ctypes.data, ev.ctypes.data,
+                  None) == hprobe.HP_EINVAL
