@@ -773,6 +773,72 @@ def run_variance(args):
     print(json.dumps(out), flush=True)
 
 
+def run_wilson_deflation(args):
+    """Deflated probing of the Wilson matrix (the conclusions' next step, on the Wilson operator):
+    8^4, kappa 0.124, eps 0.4 (link seed 1004), the k eigenpairs of gamma_5 D with the smallest
+    |lambda| from hp_wilson_eigs, then per z_0 seed S probing vectors with full dilution, plain and
+    deflated (the same FP16 even-odd solves, the deflated quadratures corrected on the device).
+    One step = one seed, both estimates; value = probing solves/s; the JSON carries the spread of
+    T_s over the seeds for both and the eigensolver's time and residuals."""
+    import torch
+
+    from paper_1302_4018_gb300 import hprobe, synth
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    ctx = hprobe.Context(0, stream=stream.cuda_stream)
+    dims = (8, 8, 8, 8)
+    kappa, k, S = 0.124, args.defl_k, args.defl_vectors
+    U = synth.gauge_links(dims, 0.4, 1004, device="cuda:0")
+    links = torch.from_numpy(U.view(np.float64).reshape(-1)).to("cuda:0")
+    op = ctx.make_operator(hprobe.OP_WILSON, 0.0, kappa, links, None)
+    V = int(np.prod(dims))
+    ev = torch.zeros((k, V, 4, 3), dtype=torch.complex128, device="cuda:0")
+    torch.cuda.synchronize()
+    t_e = time.perf_counter()
+    lam, ev, res = ctx.wilson_eigs(op, dims, k, tol=1e-10, evecs=ev)
+    torch.cuda.synchronize()
+    t_e = time.perf_counter() - t_e
+
+    def step(seed):
+        opts = ctx.make_opts(args.precision, z0_seed=seed, rhs_block=96, even_odd=1)
+        T0, _, s0 = ctx.trace_inv(op, dims, S, 1e-10, opts)
+        T1, _, s1 = ctx.trace_inv_deflated(op, dims, ev, lam, S, 1e-10, opts)
+        return T0.real, T1.real, s0["rhs_solved"] + s1["rhs_solved"]
+
+    for w in range(args.warmup):
+        step(5000 + w)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    runs = [step(1 + i) for i in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    solves = sum(r[2] for r in runs)
+    points = [s for s in (1, 2, 4, 8, 16, 32, 64, 128, 256, 512) if s <= S]
+    T0 = np.array([r[0] for r in runs])
+    T1 = np.array([r[1] for r in runs])
+    spread = {"s": points,
+              "std_plain": [float(T0[:, s - 1].std(ddof=1)) if len(runs) > 1 else None for s in points],
+              "std_deflated": [float(T1[:, s - 1].std(ddof=1)) if len(runs) > 1 else None for s in points],
+              "mean_plain": [float(T0[:, s - 1].mean()) for s in points],
+              "mean_deflated": [float(T1[:, s - 1].mean()) for s in points]}
+    out = {"metric": "probing solves/s, deflated Wilson probing (8^4, kappa 0.124, %d modes of gamma_5 D)" % k,
+           "value": solves / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f16-storage/f32-math + f64 reliable updates" if args.precision == "fp16" else args.precision,
+           "data": "synthetic: SU(3) links exp(i eps H), seeded (no gauge ensemble available)",
+           "config": {"workload": "8^4 Wilson-Dirac, kappa 0.124, eps 0.4, link seed 1004; %d vectors x 12 "
+                                  "dilutions per z_0 seed, plain and with the %d smallest |lambda| of gamma_5 D "
+                                  "deflated; %d seeds" % (S, k, args.steps),
+                      "precision": args.precision, "even_odd": True},
+           "wilson_eigs": {"k": k, "seconds": t_e, "abs_lambda_min": float(np.abs(lam).min()),
+                           "abs_lambda_max": float(np.abs(lam).max()), "max_rel_residual": float(res.max())},
+           "spread_over_seeds": spread}
+    print(json.dumps(out), flush=True)
+
+
 def _laplacian_exact_trace(dims, mass):
     """Tr A^-1 of the shifted periodic Laplacian: A is diagonal in Fourier space."""
     k = [2 * np.pi * np.arange(L) / L for L in dims]
@@ -1124,7 +1190,10 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "batch", "grad", "variance", "sparse", "study", "config2"])
+                    choices=["headline", "batch", "grad", "variance", "sparse", "study", "config2",
+                             "wilson_deflation"])
+    ap.add_argument("--defl-k", type=int, default=48, help="modes of gamma_5 D deflated (wilson_deflation)")
+    ap.add_argument("--defl-vectors", type=int, default=64, help="probing vectors per seed (wilson_deflation)")
     ap.add_argument("--config2-vectors", type=int, default=512)
     ap.add_argument("--study-seeds", type=int, default=32, help="z_0 draws of the Wilson speed-up ratio")
     ap.add_argument("--study-wilson-vectors", type=int, default=512)
@@ -1170,6 +1239,8 @@ def main():
         run_study(args)
     elif args.workload == "config2":
         run_config2(args)
+    elif args.workload == "wilson_deflation":
+        run_wilson_deflation(args)
     else:
         run_ours(args)
 

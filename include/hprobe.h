@@ -315,9 +315,11 @@ hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, const hp_lat
  * |lambda| -- the smallest singular values of D, the modes hp_trace_inv_deflated
  * removes from the Wilson trace.  Chebyshev-filtered subspace iteration on
  * complex spinor blocks of b = k + max(8, k/2) vectors: each sweep filters the
- * block with a degree-12 Chebyshev polynomial of Q^2 = D^H D (positive
+ * block with a degree-16 Chebyshev polynomial of Q^2 = D^H D (positive
  * semidefinite, the same eigenvectors) damping [largest Ritz value of Q^2 on
- * the block, ||D||^2 bound], orthonormalises it (Cholesky QR), and takes the
+ * the block, top of the spectrum of Q^2: 24 Lanczos steps, the largest Ritz
+ * value plus the last off-diagonal element, capped by ||D||^2 <= (|1 + m| +
+ * max |mu| + 16 kappa + 12 csw kappa)^2], orthonormalises it (Cholesky QR), and takes the
  * Rayleigh-Ritz pairs of Q^2 on the block, then those of Q inside the span of
  * the k lowest (Q is indefinite: its Ritz values on a block that mixes both
  * ends of the spectrum can fall anywhere, near 0 included); k should sit at a

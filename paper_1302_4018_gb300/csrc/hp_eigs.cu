@@ -705,9 +705,10 @@ extern "C" hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp
   }
   const double dnorm = std::fabs(1.0 + op->mass) + mu_abs + 16.0 * std::fabs(op->kappa) +
                        12.0 * std::fabs(op->csw * op->kappa);
-  const double l_max = dnorm * dnorm, l_low = 0.0;
+  double l_max = dnorm * dnorm;
+  const double l_low = 0.0;
   const int b = (int)std::min<long long>(n, k + std::max(8, k / 2));
-  const int m = 12;
+  const int m = 16;
   ZEigWork w;
   w.ctx = ctx;
   w.op = op;
@@ -732,6 +733,46 @@ extern "C" hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp
   w.Gd = (double2*)p;
   HP_TRY(hp_ws(ctx, "zeigs.W", sizeof(double2) * (size_t)b * b, &p));
   w.Wd = (double2*)p;
+  {
+    // the top of the spectrum of Q^2 for the filter: 24 Lanczos steps from one random vector, the
+    // largest Ritz value plus the last off-diagonal element (the safeguard of Zhou and Saad's
+    // filtered subspace iteration), capped by the norm bound above
+    ZEigWork v = w;
+    v.b = 1;
+    double2 *prev = w.Y, *cur = w.X, *nxt = w.Z;
+    k_eig_fill<<<blocks_for(ctx, 2 * n, 256), 256, 0, ctx->stream>>>((double*)cur, 2 * n, 0x1a2c05ULL);
+    HP_LAUNCH_CHECK();
+    HP_CUDA(cudaMemsetAsync(prev, 0, sizeof(double2) * (size_t)n, ctx->stream));
+    std::vector<zd> G;
+    HP_TRY(v.gram(cur, cur, G));
+    HP_TRY(v.lincomb(cur, cur, cur, nullptr, 1.0 / std::sqrt(G[0].real()), 0.0, 0.0));
+    std::vector<double> alpha, beta;
+    double bprev = 0.0;
+    for (int j = 0; j < 24; ++j) {
+      HP_TRY(v.apply_q2(cur, nxt));
+      HP_TRY(v.lincomb(nxt, nxt, prev, nullptr, 1.0, -bprev, 0.0));
+      HP_TRY(v.gram(cur, nxt, G));
+      const double al = G[0].real();
+      HP_TRY(v.lincomb(nxt, nxt, cur, nullptr, 1.0, -al, 0.0));
+      HP_TRY(v.gram(nxt, nxt, G));
+      const double be = std::sqrt(std::max(0.0, G[0].real()));
+      alpha.push_back(al);
+      beta.push_back(be);
+      if (!(be > 1e-12 * std::fabs(al))) break;
+      HP_TRY(v.lincomb(nxt, nxt, nxt, nullptr, 1.0 / be, 0.0, 0.0));
+      std::swap(prev, cur);   // prev <- v_j, cur <- v_{j+1}, nxt <- free
+      std::swap(cur, nxt);
+      bprev = be;
+    }
+    const int L = (int)alpha.size();
+    std::vector<double> Tm((size_t)L * L, 0.0), tth, tW;
+    for (int i = 0; i < L; ++i) {
+      Tm[(size_t)i * L + i] = alpha[i];
+      if (i + 1 < L) Tm[(size_t)i * L + i + 1] = Tm[(size_t)(i + 1) * L + i] = beta[i];
+    }
+    jacobi_eigh(Tm, L, tth, tW);
+    l_max = std::min(l_max, 1.01 * (tth[L - 1] + beta[L - 1]));
+  }
   k_eig_fill<<<blocks_for(ctx, 2 * n * b, 256), 256, 0, ctx->stream>>>((double*)w.X, 2 * n * b, 0x5eed5ULL + k);
   HP_LAUNCH_CHECK();
   HP_TRY(w.orthonormalise());
