@@ -52,18 +52,15 @@ struct RawHalf {
   __device__ __forceinline__ float im_sub(int idx, float b) const;
 };
 
-// binary16: cvt.f32.f16 and add / sub.rn.f32.f16 on the halves of the 32-bit word
+// binary16: conversion as h + 0 and add / sub.rn.f32.f16 on the halves of the 32-bit word (all at the
+// full FP32 rate)
 template <>
 __device__ __forceinline__ float RawHalf<PR16>::re(int idx) const {
-  float r;
-  asm("{.reg .f16 l, h; mov.b32 {l, h}, %1; cvt.f32.f16 %0, l;}" : "=f"(r) : "r"(word(idx)));
-  return r;
+  return h16lo_to_f32(word(idx));
 }
 template <>
 __device__ __forceinline__ float RawHalf<PR16>::im(int idx) const {
-  float r;
-  asm("{.reg .f16 l, h; mov.b32 {l, h}, %1; cvt.f32.f16 %0, h;}" : "=f"(r) : "r"(word(idx)));
-  return r;
+  return h16hi_to_f32(word(idx));
 }
 template <>
 __device__ __forceinline__ float RawHalf<PR16>::re_add(int idx, float b) const {
@@ -289,9 +286,8 @@ struct Link2<PR16> {   // binary16: 2 uint4 + 1 word per link
   }
   __device__ __forceinline__ void elem(int k, float& x, float& y) const {
     const unsigned w = word(k);
-    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w));
-    x = f.x;
-    y = f.y;
+    x = h16lo_to_f32(w);
+    y = h16hi_to_f32(w);
   }
 };
 template <>

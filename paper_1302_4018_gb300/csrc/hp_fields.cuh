@@ -222,12 +222,22 @@ struct SpinorIO<PRFF> {
 
 template <int PR>
 struct Half2Ops;
+// binary16 -> FP32 as the mixed-precision add h + 0.0f (add.rn.f32.f16): exact, since every binary16
+// value is an FP32 value (a negative zero comes out positive), and on sm_100+ it issues at the full
+// FP32 rate, where cvt.f32.f16 takes two slots of the FP32 pipe
+__device__ __forceinline__ float h16lo_to_f32(unsigned int u) {
+  float r;
+  asm("{.reg .f16 l, h; mov.b32 {l, h}, %1; add.rn.f32.f16 %0, l, %2;}" : "=f"(r) : "r"(u), "f"(0.0f));
+  return r;
+}
+__device__ __forceinline__ float h16hi_to_f32(unsigned int u) {
+  float r;
+  asm("{.reg .f16 l, h; mov.b32 {l, h}, %1; add.rn.f32.f16 %0, h, %2;}" : "=f"(r) : "r"(u), "f"(0.0f));
+  return r;
+}
 template <>
 struct Half2Ops<PR16> {
-  __device__ static __forceinline__ float2 to_f2(unsigned int u) {
-    __half2 h = *reinterpret_cast<__half2*>(&u);
-    return __half22float2(h);
-  }
+  __device__ static __forceinline__ float2 to_f2(unsigned int u) { return make_float2(h16lo_to_f32(u), h16hi_to_f32(u)); }
   __device__ static __forceinline__ unsigned int from_f2(float a, float b) {
     __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<unsigned int*>(&h);

@@ -1047,8 +1047,11 @@ __global__ void __launch_bounds__(NT, EO_ODD_MINB(SIN, REC)) k_eo_odd(WArgs a, F
   EO_SLOTS_END
 }
 
-// the exact steps: at least EO_X_MINB resident blocks of 128 threads (register cap)
+// the exact steps: resident blocks of 128 threads (register caps, chosen by timing on 32^3x64):
+// step 1 at 3 (168 registers), the float-float step 2 at 2 (its hop plus the residual epilogue
+// spills at 168; without spills it runs 13% faster)
 #define EO_X_MINB 3
+#define EO_X2_MINB 2
 // ---- exact step 1: x_e = d_e^-1 (b_e + k hop(x_o))   (FP64 or float-float)
 template <int PX, int NT>
 __global__ void __launch_bounds__(NT, EO_X_MINB) k_eo_x1(WArgs a, int nslots) {
@@ -1093,7 +1096,7 @@ __global__ void __launch_bounds__(NT, EO_X_MINB) k_eo_x1(WArgs a, int nslots) {
 
 // ---- exact step 2: r_o = b_o - d_o x_o + k hop(x_e); a fresh slot also sets r^ = p = r
 template <int SPR, int PX, int NT>
-__global__ void __launch_bounds__(NT, EO_X_MINB) k_eo_x2(WArgs a, int nslots) {
+__global__ void __launch_bounds__(NT, PX == PR64 ? EO_X_MINB : EO_X2_MINB) k_eo_x2(WArgs a, int nslots) {
   EO_SLOTS_BEGIN(MASK_EXACT, true)
   typedef typename Real_of<PX>::T R;
   typedef typename Real_of<SPR>::T RS;
