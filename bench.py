@@ -70,10 +70,10 @@ def source_hash(kernel):
 
 # DRAM traffic of the dominant kernel per byte of algorithmic work, from one ncu capture of the
 # same kernel (k_eo2_even, the two-right-hand-side even-site stencil, eo_kernel 4) on 32^3x16 with
-# 12 slots: 278.3 MB read + 142.6 MB written per launch against 377.5 MB algorithmic (12-real links;
+# 12 slots: 282.3 MB read + 143.3 MB written per launch against 377.5 MB algorithmic (12-real links;
 # both parts of the launch -- spinors and links -- grow with the units processed, so the ratio
 # carries over to the 32^3x64 launch); valid only for the kernel source it was taken on
-NCU_TRAFFIC = {("k_eo_even", "2cd1ee671099"): {"bytes_all_slots": 278.3e6 + 142.6e6,
+NCU_TRAFFIC = {("k_eo_even", "f7f32fc9b7f5"): {"bytes_all_slots": 282.3e6 + 143.3e6,
                                       "alg_bytes_all_slots": 262144 * 104 * 12 + 4 * 524288 * 24}}
 
 
