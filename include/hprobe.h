@@ -302,7 +302,7 @@ hp_status hp_trace_inv_bounds(hp_ctx* ctx, const hp_operator* op, const hp_latti
  *
  * q_inout (the deflated quadratures), trace_prefix, stats as hp_trace_inv;
  * opts->first must be 0.  Errors: HP_EINVAL for k outside [1, V] (Laplacian)
- * or [1, 12 V] (Wilson), NULL arrays, a Laplacian eigenvalue <= 0 or a Wilson
+ * or [1, min(12 V, 65535)] (Wilson), NULL arrays, a Laplacian eigenvalue <= 0 or a Wilson
  * eigenvalue 0; HP_EUNSUPPORTED for another probe kind (Wilson); as
  * hp_trace_inv otherwise. */
 hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k,

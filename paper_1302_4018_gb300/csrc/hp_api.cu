@@ -434,8 +434,9 @@ static hp_status trace_deflated_wilson(hp_ctx* ctx, const hp_operator* op, const
     hp_set_error("deflated Wilson probing uses the hierarchical vectors (probe_kind 0)");
     return HP_EUNSUPPORTED;
   }
-  if (k < 1 || (int64_t)k > 12LL * g.V || !evecs || !evals) {
-    hp_set_error("deflation: 1 <= k <= 12 V and non-NULL eigenvectors and eigenvalues required (k = %d)", k);
+  if (k < 1 || (int64_t)k > std::min<int64_t>(12LL * g.V, 65535) || !evecs || !evals) {
+    hp_set_error("deflation: 1 <= k <= min(12 V, 65535) and non-NULL eigenvectors and eigenvalues required (k = %d)",
+                 k);
     return HP_EINVAL;
   }
   for (int j = 0; j < k; ++j)
