@@ -324,9 +324,13 @@ hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, const hp_lat
  * the k lowest (Q is indefinite: its Ritz values on a block that mixes both
  * ends of the spectrum can fall anywhere, near 0 included); k should sit at a
  * gap of |lambda| (a +-pair of nearly equal |lambda| split by k converges
- * slowly).  FP64 throughout (the FP64 Wilson stencil, complex Gram
- * matrices and block rotations on the device; b x b Hermitian Cholesky and
- * Jacobi on the host).  Stops when ||Q w_j - lambda_j w_j|| <= tol |lambda_j|
+ * slowly).  FP64 Rayleigh-Ritz steps and residuals (the FP64 Wilson stencil,
+ * complex Gram matrices and block rotations on the device; b x b Hermitian
+ * Cholesky and Jacobi on the host); the filter runs the FP32 stencil while the
+ * largest residual exceeds max(1e-5, 100 tol), the FP64 one after.  Sized for
+ * small lattices: on 16^4 and larger the lowest modes are too dense for the
+ * degree-16 filter to separate in a reasonable number of sweeps (HP_ENOCONV;
+ * measured: 16^4, k = 24, residual 1e-2 after 400 sweeps).  Stops when ||Q w_j - lambda_j w_j|| <= tol |lambda_j|
  * for j < k, or after max_sweeps (0: 200; then HP_ENOCONV, outputs hold the
  * last iterate).  evecs: complex double[k][V][4][3] (host or device), w_j
  * orthonormal; evals (host double[k]): lambda_j ordered by |lambda_j|; resid

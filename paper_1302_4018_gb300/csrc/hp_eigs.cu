@@ -12,7 +12,8 @@
 // Gram matrices (32 x 32 tiles of X^T Y over site chunks, partial sums added in a fixed order) and
 // the block rotations X W; the host works on b x b matrices only.
 //
-// The Wilson operator's counterpart (hp_wilson_eigs) runs the same iteration on complex spinor
+// The Wilson operator's counterpart (hp_wilson_eigs; its filter runs the FP32 stencil while the
+// residuals are above 1e-5, the FP64 one after) runs the same iteration on complex spinor
 // blocks for Q = gamma_5 D, Hermitian by gamma_5-hermiticity: the filter and the first
 // Rayleigh-Ritz step act on Q^2 = D^H D (positive semidefinite, the same eigenvectors; Q itself is
 // indefinite, and its Ritz values on an unconverged block can fall anywhere), a second Rayleigh-Ritz
@@ -457,10 +458,11 @@ struct ZEigWork {
   double2 *X, *Y, *Z, *T, *part, *Gd, *Wd;
   int nbx;
   long long epb;
+  int prec = HP_PREC_FP64;   // stencil precision of apply_q (the filter may run the FP32 one)
 
-  // out = Q in = gamma_5 D in for the b vectors (FP64 stencil)
+  // out = Q in = gamma_5 D in for the b vectors (FP64 or FP32 stencil, FP64 in and out)
   hp_status apply_q(const double2* in, double2* out) {
-    HP_TRY(hp_apply_wilson(ctx, op, g, b, HP_PREC_FP64, (const double*)in, (double*)out));
+    HP_TRY(hp_apply_wilson(ctx, op, g, b, prec, (const double*)in, (double*)out));
     const long long tot = n * b;
     k_gamma5<<<blocks_for(ctx, tot, 256), 256, 0, ctx->stream>>>(out, tot);
     HP_LAUNCH_CHECK();
@@ -739,6 +741,7 @@ extern "C" hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp
     // filtered subspace iteration), capped by the norm bound above
     ZEigWork v = w;
     v.b = 1;
+    v.prec = HP_PREC_MIXED_FP32;   // a bound with a 1% margin: FP32 rounding is far inside it
     double2 *prev = w.Y, *cur = w.X, *nxt = w.Z;
     k_eig_fill<<<blocks_for(ctx, 2 * n, 256), 256, 0, ctx->stream>>>((double*)cur, 2 * n, 0x1a2c05ULL);
     HP_LAUNCH_CHECK();
@@ -784,7 +787,8 @@ extern "C" hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp
   for (int it = 0; it <= sweeps; ++it) {
     // Rayleigh-Ritz with Q^2 = (Q X)^H (Q X) on the orthonormal block: the subspace and its order
     // (Q is indefinite, so its own Ritz values on a block mixing both ends of the spectrum can fall
-    // anywhere, near 0 included; those of Q^2 are bounded by its spectrum)
+    // anywhere, near 0 included; those of Q^2 are bounded by its spectrum); always the FP64 stencil
+    w.prec = HP_PREC_FP64;
     HP_TRY(w.apply_q(w.X, w.Z));
     HP_TRY(w.gram(w.Z, w.Z, H));
     for (int i = 0; i < b; ++i) {   // Hermitian part (the rounding)
@@ -835,6 +839,11 @@ extern "C" hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp
       }
     }
     if (converged || it == sweeps) break;
+    // the filter only has to raise the wanted directions: while the pairs are far from converged
+    // the FP32 stencil does (its rounding, ~1e-7 of each vector, stays below what a sweep removes),
+    // the last decades take the FP64 one
+    const double worst = *std::max_element(rn.begin(), rn.end());
+    w.prec = worst > std::max(1e-5, 100.0 * tol) ? HP_PREC_MIXED_FP32 : HP_PREC_FP64;
     // Chebyshev filter of degree m on Q^2 damping [largest Q^2 Ritz value of the block, l_max], scaled at 0
     const double a = std::min(top2, 0.99 * l_max);
     const double c0 = 0.5 * (l_max + a), e = 0.5 * (l_max - a);
