@@ -314,7 +314,7 @@ hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, const hp_lat
  * gamma_5-hermiticity, real eigenvalues of either sign) with the smallest
  * |lambda| -- the smallest singular values of D, the modes hp_trace_inv_deflated
  * removes from the Wilson trace.  Chebyshev-filtered subspace iteration on
- * complex spinor blocks of b = k + max(8, k/2) vectors: each sweep filters the
+ * complex spinor blocks of b = 2k + 8 vectors: each sweep filters the
  * block with a degree-16 Chebyshev polynomial of Q^2 = D^H D (positive
  * semidefinite, the same eigenvectors) damping [largest Ritz value of Q^2 on
  * the block, top of the spectrum of Q^2: 24 Lanczos steps, the largest Ritz
@@ -330,7 +330,7 @@ hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, const hp_lat
  * largest residual exceeds max(1e-5, 100 tol), the FP64 one after.  Sized for
  * small lattices: on 16^4 and larger the lowest modes are too dense for the
  * degree-16 filter to separate in a reasonable number of sweeps (HP_ENOCONV;
- * measured: 16^4, k = 24, residual 1e-2 after 400 sweeps).  Stops when ||Q w_j - lambda_j w_j|| <= tol |lambda_j|
+ * measured: 16^4, k = 24, residual 3.3e-3 after 200 sweeps).  Stops when ||Q w_j - lambda_j w_j|| <= tol |lambda_j|
  * for j < k, or after max_sweeps (0: 200; then HP_ENOCONV, outputs hold the
  * last iterate).  evecs: complex double[k][V][4][3] (host or device), w_j
  * orthonormal; evals (host double[k]): lambda_j ordered by |lambda_j|; resid

@@ -709,7 +709,11 @@ extern "C" hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp
                        12.0 * std::fabs(op->csw * op->kappa);
   double l_max = dnorm * dnorm;
   const double l_low = 0.0;
-  const int b = (int)std::min<long long>(n, k + std::max(8, k / 2));
+  // guard vectors: the low spectrum of gamma_5 D is dense, and the k-th pair converges at the rate
+  // set by the gap between the k-th and the (b+1)-th values of Q^2, so the block is twice k (with
+  // k + 8 the k-th and b-th values of a 16^4 problem lay within 0.7% and the modes near k never
+  // separated)
+  const int b = (int)std::min<long long>(n, 2LL * k + 8);
   const int m = 16;
   ZEigWork w;
   w.ctx = ctx;
