@@ -44,6 +44,24 @@ def test_ring_gives_bit_reversal():
     assert offsets[0] == (0, n - 1, 1)
 
 
+def test_ring_color_offsets_are_the_dyadic_intervals():
+    """On the ring of 2^K sites every block splits into its two colours down to blocks of two
+    (which the distance-2^(K-1) graph joins: dense, so the recursion stops there), so colorOffsets
+    is the list of dyadic intervals of sizes 2^K .. 2 in pre-order, interval j of size n / 2^(l-1)
+    at level l."""
+    K = 5
+    n = 1 << K
+    _, offsets, _ = SP.hierarchical_coloring(ring_laplacian(n))
+
+    def dyadic(start, size, level):
+        out = [(start, start + size - 1, level)]
+        if size > 2:
+            out += dyadic(start, size // 2, level + 1) + dyadic(start + size // 2, size // 2, level + 1)
+        return out
+
+    assert offsets == dyadic(0, n, 1)
+
+
 def test_torus_first_level_is_red_black():
     dims = (8, 6)
     A = sp.csr_matrix(O.laplacian_dense(dims, 0.1))
