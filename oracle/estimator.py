@@ -281,6 +281,45 @@ def wilson_deflated_quadratures(dims, U, kappa, evals, evecs, first, count, z0_s
     return q, complex(exact)
 
 
+def wilson_smallest_singular_triplets(dims, U, kappa, k, mass=0.0, mass_field=None, csw=0.0):
+    """The k smallest singular triplets D v_j = sigma_j u_j of the Wilson matrix (numpy's dense SVD):
+    returns (sigma [k] ascending, right [k][V][4][3], left [k][V][4][3]), both sets orthonormal."""
+    clover = ops.clover_term(U, dims, kappa, csw) if csw else None
+    D = ops.wilson_dense(U, dims, kappa, mass, mass_field, clover=clover)
+    Ul, s, Vh = np.linalg.svd(D)
+    order = np.argsort(s, kind="stable")[:k]
+    V = int(np.prod(dims))
+    right = np.conj(Vh[order]).reshape(k, V, 4, 3)
+    left = Ul[:, order].T.reshape(k, V, 4, 3)
+    return s[order], np.ascontiguousarray(right), np.ascontiguousarray(left)
+
+
+def wilson_deflated_quadratures_svd(dims, U, kappa, sigma, right, left, first, count, z0_seed, mass=0.0,
+                                    mass_field=None, csw=0.0):
+    """Deflated probing of the Wilson matrix with singular triplets D v_j = sigma_j u_j (right
+    vectors v_j, left vectors u_j, each set orthonormal), written out literally:
+        D^-1 u_j = v_j / sigma_j,  D^-1 = sum_j v_j u_j^H / sigma_j + D^-1 (I - U U^H),
+        Tr D^-1 = sum_j (u_j^H v_j) / sigma_j + Tr(D^-1 (I - U U^H)),
+    the second term probed: q_m = sum_a v_{m,a}^H D^-1 (I - U U^H) v_{m,a} (dense solves).
+    Returns (q [count], the exact part)."""
+    W = probe_vectors(dims, first, count, z0_seed)
+    V = W.shape[1]
+    k = len(sigma)
+    clover = ops.clover_term(U, dims, kappa, csw) if csw else None
+    D = ops.wilson_dense(U, dims, kappa, mass, mass_field, clover=clover)
+    Rv = np.asarray(right).reshape(k, 12 * V).T
+    Lv = np.asarray(left).reshape(k, 12 * V).T
+    B = np.zeros((12 * V, 12 * count), dtype=complex)
+    for m in range(count):
+        for a in range(12):
+            B[:, 12 * m + a] = _dilute(W[m], a).reshape(-1)
+    Bp = B - Lv @ (np.conj(Lv).T @ B)
+    X = solvers.dense_solve(D, Bp)
+    q = np.array([sum(np.vdot(B[:, 12 * m + a], X[:, 12 * m + a]) for a in range(12)) for m in range(count)])
+    exact = sum(np.vdot(Lv[:, j], Rv[:, j]) / sigma[j] for j in range(k))
+    return q, complex(exact)
+
+
 def wilson_grad_mass_field(dims, U, kappa, s, z0_seed, tol=1e-13, mass=0.0, mass_field=None,
                            method="bicgstab", csw=0.0):
     """dT_s/dmu(x) = -(1/s) sum_{m<s,a} sum_c conj(y(x,c)) x(x,c), y = D^-H v solved explicitly."""

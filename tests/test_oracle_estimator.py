@@ -415,3 +415,47 @@ def test_wilson_deflation_reduces_the_z0_variance():
     Z = 1 - 2 * ph
     for s in (4, 8, 16):
         assert E.z0_variance(block_traces(Bd), Z, s) < 0.7 * E.z0_variance(block_traces(B), Z, s)
+
+
+# ------------------------------------------------------------------ Wilson deflation with singular triplets
+def test_wilson_singular_triplets_are_the_gamma5_eigenpairs():
+    """D v = sigma u with v = w_j, u = sign(lambda_j) gamma_5 w_j, sigma = |lambda_j| for the
+    eigenpairs of gamma_5 D: the same smallest singular values, and D v_j = sigma_j u_j."""
+    dims, kappa = (2, 4, 2, 2), 0.12
+    U = synth.gauge_links(dims, 0.4, 11)
+    sig, R, L = E.wilson_smallest_singular_triplets(dims, U, kappa, 8, mass=0.02)
+    lam, _ = E.wilson_lowest_eigenpairs(dims, U, kappa, 8, mass=0.02)
+    assert np.allclose(sig, np.abs(lam), rtol=1e-12, atol=0)
+    for j in range(8):
+        assert np.linalg.norm(O.wilson_apply(R[j], U, dims, kappa, 0.02) - sig[j] * L[j]) <= 1e-12
+        assert abs(np.vdot(R[j], R[j]) - 1) <= 1e-12 and abs(np.vdot(L[j], L[j]) - 1) <= 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 6, 25])
+def test_wilson_svd_deflated_full_sequence_is_exact(k):
+    """T_N = sum_j u_j^H v_j / sigma_j + Tr(D^-1 (I - U U^H)) = Tr D^-1 (dense inverse) for any k."""
+    dims, kappa = (2, 2, 4, 2), 0.12
+    U = synth.gauge_links(dims, 0.4, 12)
+    sig, R, L = E.wilson_smallest_singular_triplets(dims, U, kappa, k)
+    q, exact = E.wilson_deflated_quadratures_svd(dims, U, kappa, sig, R, L, 0, 32, z0_seed=6)
+    T = exact + E.trace_prefix(q)
+    ref = np.trace(np.linalg.inv(O.wilson_dense(U, dims, kappa)))
+    assert abs(T[-1] - ref) <= 1e-11 * abs(ref)
+
+
+def test_wilson_svd_deflated_quadrature_is_the_plain_one_minus_a_projection_sum():
+    """q'_m = q_m - sum_{a,j} (v_{m,a}^H v_j)(u_j^H v_{m,a}) / sigma_j, and the gamma_5 eigenpair form
+    gives the same deflated quadratures (its triplets are the same modes)."""
+    dims, kappa = (2, 2, 2, 4), 0.115
+    U = synth.gauge_links(dims, 0.3, 13)
+    sig, R, L = E.wilson_smallest_singular_triplets(dims, U, kappa, 7)
+    qd, ex = E.wilson_deflated_quadratures_svd(dims, U, kappa, sig, R, L, 0, 8, z0_seed=3)
+    q0 = E.wilson_quadratures(dims, U, kappa, 0, 8, 3, method="dense")
+    P = E.probe_vectors(dims, 0, 8, 3)
+    Rf, Lf = R.reshape(7, -1, 12), L.reshape(7, -1, 12)
+    corr = np.array([sum(np.vdot(P[m], Rf[j, :, a]) * np.vdot(Lf[j, :, a], P[m]) / sig[j]
+                         for a in range(12) for j in range(7)) for m in range(8)])
+    assert np.allclose(qd, q0 - corr, rtol=0, atol=1e-11 * np.abs(q0).max())
+    lam, Wq = E.wilson_lowest_eigenpairs(dims, U, kappa, 7)
+    qg, exg = E.wilson_deflated_quadratures(dims, U, kappa, lam, Wq, 0, 8, z0_seed=3)
+    assert np.allclose(qd, qg, rtol=0, atol=1e-11 * np.abs(q0).max()) and abs(ex - exg) <= 1e-11 * abs(exg)
