@@ -310,6 +310,24 @@ hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, const hp_lat
                                 const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
                                 hp_solve_stats* stats);
 
+/* Deflated probing of the Wilson matrix with singular triplets D v_j = sigma_j
+ * u_j (right vectors v_j and left vectors u_j, each set orthonormal, complex
+ * double[k][V][4][3], host or device; sigma host double[k], all > 0;
+ * hp_wilson_svd computes them): D^-1 u_j = v_j / sigma_j, so
+ *   Tr D^-1 = sum_j (u_j^H v_j) / sigma_j + Tr(D^-1 (I - U U^H)),
+ * the second term probed with the plain solves and the correction
+ *   - sum_a sum_j (v_{m,a}^H v_j) (u_j^H v_{m,a}) / sigma_j
+ * of each quadrature, as in hp_trace_inv_deflated (whose gamma_5 eigenpairs are
+ * the triplets v = w, u = sign(lambda) gamma_5 w, sigma = |lambda|).  The
+ * identity holds for any singular triplets, so the k smallest need not sit at a
+ * gap of the spectrum.  Arguments and errors as hp_trace_inv_deflated for the
+ * Wilson operator (HP_EINVAL also for a Laplacian, NULL left vectors or a
+ * sigma <= 0). */
+hp_status hp_trace_inv_deflated_svd(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k,
+                                    const double* right, const double* left, const double* sigma, int64_t s_max,
+                                    double tol, const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
+                                    hp_solve_stats* stats);
+
 /* The k eigenpairs of Q = gamma_5 D (Wilson or Clover-Wilson; Hermitian by
  * gamma_5-hermiticity, real eigenvalues of either sign) with the smallest
  * |lambda| -- the smallest singular values of D, the modes hp_trace_inv_deflated
@@ -326,8 +344,9 @@ hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, const hp_lat
  * gap of |lambda| (a +-pair of nearly equal |lambda| split by k converges
  * slowly).  FP64 Rayleigh-Ritz steps and residuals (the FP64 Wilson stencil,
  * complex Gram matrices and block rotations on the device; b x b Hermitian
- * Cholesky and Jacobi on the host); the filter runs the FP32 stencil while the
- * largest residual exceeds max(1e-5, 100 tol), the FP64 one after.  Sized for
+ * Cholesky and Jacobi on the host); the filter runs the FP32 stencil until the
+ * largest residual falls to max(1e-5, 100 tol) or stops falling (less than 10%
+ * per sweep once below 1e-2), the FP64 one after.  Sized for
  * small lattices: on 16^4 and larger the lowest modes are too dense for the
  * degree-16 filter to separate in a reasonable number of sweeps (HP_ENOCONV;
  * measured: 16^4, k = 24, residual 3.3e-3 after 200 sweeps).  Stops when ||Q w_j - lambda_j w_j|| <= tol |lambda_j|
@@ -338,6 +357,20 @@ hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, const hp_lat
  * Laplacian, k outside [1, 6 V], tol <= 0, NULL outputs. */
 hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k, double tol,
                          int32_t max_sweeps, double* evecs, double* evals, double* resid);
+
+/* The k smallest singular triplets D v_j = sigma_j u_j of the Wilson matrix
+ * (Wilson or Clover-Wilson) from the same iteration as hp_wilson_eigs without
+ * its second step: the Rayleigh-Ritz pairs of Q^2 = D^H D on the block are the
+ * right vectors v_j and sigma_j^2, converged when ||Q^2 v_j - sigma_j^2 v_j|| <=
+ * tol sigma_j^2 (about ||D|| / sigma_j times the relative residual of a pair of
+ * Q, so a tol near 1e-9 is the counterpart of 1e-11 there and the FP64 floor is
+ * reached sooner), and u_j = D v_j / sigma_j = gamma_5 (Q v_j) / sigma_j.  No +-pair
+ * of gamma_5 D needs resolving, so this converges where the eigenpairs of Q do
+ * not separate.  right, left: complex double[k][V][4][3] (host or device);
+ * sigma (host double[k]) ascending; resid (host double[k], nullable).  Errors as
+ * hp_wilson_eigs (NULL left included). */
+hp_status hp_wilson_svd(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k, double tol,
+                        int32_t max_sweeps, double* right, double* left, double* sigma, double* resid);
 
 /* The k lowest eigenpairs of the shifted Laplacian (real symmetric positive
  * definite; mass field allowed): the eigenvectors hp_trace_inv_deflated removes

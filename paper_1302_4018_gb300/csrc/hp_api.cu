@@ -12,8 +12,10 @@
 hp_status hp_apply_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrhs, int prec, const double* in,
                           double* out);
 hp_status hp_apply_laplace(hp_ctx* ctx, LatGeom g, int nrhs, const double* in, double* out);
-hp_status hp_wilson_deflation(hp_ctx* ctx, const LatGeom& g, int k, const double2* W, const double* lam,
-                              int64_t s_max, double2* q, double* exact_dev);
+hp_status hp_wilson_deflation(hp_ctx* ctx, const LatGeom& g, int k, const double2* R, const double2* L,
+                              const double* sigma, int64_t s_max, double2* q, double* exact_dev);
+hp_status hp_wilson_deflation_gamma5(hp_ctx* ctx, const LatGeom& g, int k, const double2* W, const double* lam,
+                                     int64_t s_max, double2* q, double* exact_dev);
 hp_status hp_schur_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrhs, int prec, int eo_kernel,
                           const double* in, double* out);
 hp_status hp_bench_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int prec, int nrhs, int iters, double* ms,
@@ -26,7 +28,8 @@ __global__ void k_trace_prefix(const double2* __restrict__ qj, int dof, const do
                                int first, int s_max, double2* __restrict__ q_out, double2* __restrict__ T,
                                const double* __restrict__ lam, int nlam, const double* __restrict__ exact0) {
   if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  double exact = exact0 ? *exact0 : 0.0;
+  double exact = exact0 ? exact0[0] : 0.0;   // exact0: (re, im) of an exact part, or null
+  const double exact_im = exact0 ? exact0[1] : 0.0;
   for (int j = 0; j < nlam; ++j) exact += 1.0 / lam[j];
   double2 acc = make_double2(0.0, 0.0);
   for (int m = 0; m < s_max; ++m) {
@@ -44,7 +47,7 @@ __global__ void k_trace_prefix(const double2* __restrict__ qj, int dof, const do
     q_out[m] = q;
     acc.x += q.x;
     acc.y += q.y;
-    T[m] = make_double2(exact + acc.x / (m + 1), acc.y / (m + 1));
+    T[m] = make_double2(exact + acc.x / (m + 1), exact_im + acc.y / (m + 1));
   }
 }
 
@@ -417,10 +420,11 @@ extern "C" hp_status hp_trace_prefix(hp_ctx* ctx, int64_t s_max, const double* q
 }
 
 // deflated probing of the Wilson matrix: the plain solves, then the deflation correction of each
-// quadrature and the exact part on the device (hp_wdefl.cu)
+// quadrature and the exact part on the device (hp_wdefl.cu).  left = NULL: evecs / evals are
+// eigenpairs of gamma_5 D; else evecs / left / evals are singular triplets D v = sigma u.
 static hp_status trace_deflated_wilson(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k,
-                                       const double* evecs, const double* evals, int64_t s_max, double tol,
-                                       const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
+                                       const double* evecs, const double* left, const double* evals, int64_t s_max,
+                                       double tol, const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
                                        hp_solve_stats* stats) {
   HP_TRY(check_ctx(ctx));
   LatGeom g;
@@ -440,8 +444,9 @@ static hp_status trace_deflated_wilson(hp_ctx* ctx, const hp_operator* op, const
     return HP_EINVAL;
   }
   for (int j = 0; j < k; ++j)
-    if (!(evals[j] != 0.0) || !std::isfinite(evals[j])) {
-      hp_set_error("deflation: eigenvalue %d of gamma_5 D is %g", j, evals[j]);
+    if ((left ? !(evals[j] > 0.0) : !(evals[j] != 0.0)) || !std::isfinite(evals[j])) {
+      hp_set_error(left ? "deflation: singular value %d is %g" : "deflation: eigenvalue %d of gamma_5 D is %g", j,
+                   evals[j]);
       return HP_EINVAL;
     }
   std::vector<double> qraw(2 * (size_t)s_max, 0.0), Traw(2 * (size_t)s_max, 0.0);
@@ -449,11 +454,16 @@ static hp_status trace_deflated_wilson(hp_ctx* ctx, const hp_operator* op, const
   const void* p = nullptr;
   HP_TRY(hp_device_view(ctx, evecs, sizeof(double2) * 12 * (size_t)k * g.V, "wdefl.W", &p));
   const double2* W = (const double2*)p;
+  const double2* Ld = nullptr;
+  if (left) {
+    HP_TRY(hp_device_view(ctx, left, sizeof(double2) * 12 * (size_t)k * g.V, "wdefl.Lin", &p));
+    Ld = (const double2*)p;
+  }
   void* v = nullptr;
   HP_TRY(hp_ws(ctx, "wdefl.lam", sizeof(double) * (size_t)k, &v));
   double* lam = (double*)v;
   HP_CUDA(cudaMemcpyAsync(lam, evals, sizeof(double) * (size_t)k, cudaMemcpyHostToDevice, ctx->stream));
-  HP_TRY(hp_ws(ctx, "wdefl.exact", sizeof(double), &v));
+  HP_TRY(hp_ws(ctx, "wdefl.exact", 2 * sizeof(double), &v));
   double* exact = (double*)v;
   HP_TRY(hp_ws(ctx, "trace.qprev", sizeof(double2) * (size_t)s_max, &v));
   double2* qprev = (double2*)v;
@@ -462,7 +472,8 @@ static hp_status trace_deflated_wilson(hp_ctx* ctx, const hp_operator* op, const
   HP_TRY(hp_ws(ctx, "trace.T", sizeof(double2) * (size_t)s_max, &v));
   double2* T = (double2*)v;
   HP_CUDA(cudaMemcpyAsync(qprev, qraw.data(), sizeof(double2) * (size_t)s_max, cudaMemcpyHostToDevice, ctx->stream));
-  HP_TRY(hp_wilson_deflation(ctx, g, k, W, lam, s_max, qprev, exact));
+  if (left) HP_TRY(hp_wilson_deflation(ctx, g, k, W, Ld, lam, s_max, qprev, exact));
+  else HP_TRY(hp_wilson_deflation_gamma5(ctx, g, k, W, lam, s_max, qprev, exact));
   {
     ProfScope ps(ctx, "k_trace_prefix");
     k_trace_prefix<<<1, 32, 0, ctx->stream>>>(nullptr, 0, qprev, (int)s_max, (int)s_max, qout, T, nullptr, 0, exact);
@@ -484,7 +495,8 @@ extern "C" hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, c
       hp_set_error("deflated probing needs first == 0");
       return HP_EINVAL;
     }
-    return trace_deflated_wilson(ctx, op, lat, k, evecs, evals, s_max, tol, opts, q_inout, trace_prefix, stats);
+    return trace_deflated_wilson(ctx, op, lat, k, evecs, nullptr, evals, s_max, tol, opts, q_inout, trace_prefix,
+                                 stats);
   }
   if (!op || op->kind != HP_OP_LAPLACIAN) {
     hp_set_error("deflated probing needs a Laplacian or Wilson operator");
@@ -509,6 +521,25 @@ extern "C" hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, c
   }
   const DeflReq d{k, evecs, evals};
   return trace_common(ctx, op, lat, s_max, tol, opts, q_inout, trace_prefix, nullptr, nullptr, stats, nullptr, &d);
+}
+
+extern "C" hp_status hp_trace_inv_deflated_svd(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k,
+                                               const double* right, const double* left, const double* sigma,
+                                               int64_t s_max, double tol, const hp_solver_opts* opts, double* q_inout,
+                                               double* trace_prefix, hp_solve_stats* stats) {
+  if (!op || op->kind != HP_OP_WILSON) {
+    hp_set_error("deflation with singular triplets serves the Wilson operator");
+    return HP_EINVAL;
+  }
+  if (!left) {
+    hp_set_error("deflation with singular triplets: left vectors required");
+    return HP_EINVAL;
+  }
+  if (opts && opts->first != 0) {
+    hp_set_error("deflated probing needs first == 0");
+    return HP_EINVAL;
+  }
+  return trace_deflated_wilson(ctx, op, lat, k, right, left, sigma, s_max, tol, opts, q_inout, trace_prefix, stats);
 }
 
 extern "C" hp_status hp_trace_inv_sparse(hp_ctx* ctx, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,

@@ -12,8 +12,8 @@
 // Gram matrices (32 x 32 tiles of X^T Y over site chunks, partial sums added in a fixed order) and
 // the block rotations X W; the host works on b x b matrices only.
 //
-// The Wilson operator's counterpart (hp_wilson_eigs; its filter runs the FP32 stencil while the
-// residuals are above 1e-5, the FP64 one after) runs the same iteration on complex spinor
+// The Wilson operator's counterpart (hp_wilson_eigs; its filter runs the FP32 stencil until the
+// residuals fall below 1e-5 or stop falling, the FP64 one after) runs the same iteration on complex spinor
 // blocks for Q = gamma_5 D, Hermitian by gamma_5-hermiticity: the filter and the first
 // Rayleigh-Ritz step act on Q^2 = D^H D (positive semidefinite, the same eigenvectors; Q itself is
 // indefinite, and its Ritz values on an unconverged block can fall anywhere), a second Rayleigh-Ritz
@@ -357,6 +357,17 @@ __global__ void k_gamma5(double2* __restrict__ X, long long total) {
     if ((t % 12) >= 6) X[t] = make_double2(-X[t].x, -X[t].y);
 }
 
+// out[j] = inv[j] gamma_5 Z[j] for the first k vectors (the left singular vectors u_j = D v_j / sigma_j
+// from Z = Q X = gamma_5 D X)
+__global__ void k_left_vectors(const double2* __restrict__ Z, const double* __restrict__ inv, long long n, int k,
+                               double2* __restrict__ out) {
+  const long long total = n * k;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const double s = inv[t / n] * ((t % 12) >= 6 ? -1.0 : 1.0);
+    out[t] = make_double2(s * Z[t].x, s * Z[t].y);
+  }
+}
+
 // Cholesky G = R^H R of a Hermitian G (upper R, row-major); false if a pivot is not positive
 bool cholesky_upper_z(std::vector<zd>& G, int b) {
   for (int j = 0; j < b; ++j) {
@@ -664,8 +675,13 @@ extern "C" hp_status hp_laplacian_eigs(hp_ctx* ctx, const hp_operator* op, const
   return HP_OK;
 }
 
-extern "C" hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k, double tol,
-                                    int32_t max_sweeps, double* evecs, double* evals, double* resid) {
+// the eigenpairs of Q = gamma_5 D with the smallest |lambda| (svd = false: evecs, evals signed), or the
+// smallest singular triplets D v = sigma u (svd = true: evecs = v, left = u, evals = sigma), from the
+// same filtered block iteration
+static hp_status wilson_block_eigs(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k, double tol,
+                                   int32_t max_sweeps, bool svd, double* evecs, double* left, double* evals,
+                                   double* resid) {
+  const char* fn = svd ? "hp_wilson_svd" : "hp_wilson_eigs";
   if (!ctx) {
     hp_set_error("NULL context");
     return HP_EINVAL;
@@ -674,11 +690,11 @@ extern "C" hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp
   std::vector<int64_t> dims;
   HP_TRY(hp_validate_lattice(lat, 4, &dims));
   if (!op || op->kind != HP_OP_WILSON || !op->links) {
-    hp_set_error("hp_wilson_eigs: a Wilson operator with links is required");
+    hp_set_error("%s: a Wilson operator with links is required", fn);
     return HP_EINVAL;
   }
   if (!std::isfinite(op->mass) || !std::isfinite(op->kappa) || !std::isfinite(op->csw)) {
-    hp_set_error("hp_wilson_eigs: mass / kappa / csw not finite");
+    hp_set_error("%s: mass / kappa / csw not finite", fn);
     return HP_EINVAL;
   }
   LatticeSetup* ls = nullptr;
@@ -690,8 +706,8 @@ extern "C" hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp
   g.dof = 12;
   const int V = g.V;
   const long long n = 12LL * V;
-  if (k < 1 || 2LL * k > n || !(tol > 0.0) || !evecs || !evals) {
-    hp_set_error("hp_wilson_eigs: k in [1, 6 V], tol > 0 and output arrays required");
+  if (k < 1 || 2LL * k > n || !(tol > 0.0) || !evecs || !evals || (svd && !left)) {
+    hp_set_error("%s: k in [1, 6 V], tol > 0 and output arrays required", fn);
     return HP_EINVAL;
   }
   // spectrum bound of Q^2 = D^H D: ||D|| <= |1 + m| + max |mu| + 16 kappa (eight hops of norm 2 kappa)
@@ -788,6 +804,18 @@ extern "C" hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp
   const int sweeps = max_sweeps > 0 ? max_sweeps : 200;
   bool converged = false;
   double top2 = 0.0;   // the largest Rayleigh-Ritz value of Q^2 on the block (the filter's damping bound)
+  // the filter only has to raise the wanted directions: while the pairs are far from converged the
+  // FP32 stencil does (its rounding stays below what a sweep removes), the last decades take the FP64
+  // one.  Where the FP32 rounding floor of the residual lies depends on the operator (clover, the
+  // spread of the spectrum, the residual's scale), so the switch is latched both at a fixed level and
+  // as soon as the worst residual stops falling (less than 10% per sweep once below 1e-2).
+  bool fp64_filter = false;
+  double prev_worst = HUGE_VAL;
+  auto pick_filter_precision = [&](double worst) {
+    if (worst <= std::max(1e-5, 100.0 * tol) || (worst < 1e-2 && worst > 0.9 * prev_worst)) fp64_filter = true;
+    prev_worst = worst;
+    return fp64_filter ? HP_PREC_FP64 : HP_PREC_MIXED_FP32;
+  };
   for (int it = 0; it <= sweeps; ++it) {
     // Rayleigh-Ritz with Q^2 = (Q X)^H (Q X) on the orthonormal block: the subspace and its order
     // (Q is indefinite, so its own Ritz values on a block mixing both ends of the spectrum can fall
@@ -810,6 +838,42 @@ extern "C" hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp
     std::swap(w.X, w.Y);
     HP_TRY(w.rotate(w.Z, W, w.Y));
     std::swap(w.Z, w.Y);             // Z = Q X in the rotated basis
+    if (svd) {
+      // singular triplets: the Q^2 Ritz pairs themselves, v_j = X_j, sigma_j = sqrt(theta2_j);
+      // residual ||Q^2 v_j - sigma_j^2 v_j|| / sigma_j^2, Y = Q^2 X (FP64) serving the filter as well
+      HP_TRY(w.apply_q(w.Z, w.Y));
+      std::vector<zd> Dg((size_t)b * b, 0.0);
+      for (int j = 0; j < k; ++j) Dg[(size_t)j * b + j] = -theta2[j];
+      HP_TRY(w.rotate(w.X, Dg, w.T));
+      HP_TRY(w.lincomb(w.T, w.Y, w.T, nullptr, 1.0, 1.0, 0.0));
+      std::vector<zd> RR;
+      HP_TRY(w.gram(w.T, w.T, RR));
+      converged = true;
+      theta.assign(k, 0.0);
+      for (int j = 0; j < k; ++j) {
+        theta[j] = std::sqrt(std::max(0.0, theta2[j]));
+        rn[j] = std::sqrt(std::max(0.0, RR[(size_t)j * b + j].real())) / std::max(theta2[j], 1e-300);
+        if (!(rn[j] <= tol)) converged = false;
+      }
+      if (converged || it == sweeps) break;
+      w.prec = pick_filter_precision(*std::max_element(rn.begin(), rn.end()));
+      const double a = std::min(top2, 0.99 * l_max);
+      const double c0 = 0.5 * (l_max + a), e = 0.5 * (l_max - a);
+      double sigma = e / (l_low - c0);
+      const double tau = 2.0 / sigma;
+      HP_TRY(w.lincomb(w.Y, w.Y, w.X, nullptr, sigma / e, -c0 * sigma / e, 0.0));   // Y = Q^2 X from above
+      for (int i = 2; i <= m; ++i) {
+        const double sigma1 = 1.0 / (tau - sigma);
+        HP_TRY(w.apply_q2(w.Y, w.Z));
+        HP_TRY(w.lincomb(w.Z, w.Z, w.Y, w.X, 2.0 * sigma1 / e, -2.0 * sigma1 * c0 / e, -sigma * sigma1));
+        std::swap(w.X, w.Y);
+        std::swap(w.Y, w.Z);
+        sigma = sigma1;
+      }
+      std::swap(w.X, w.Y);
+      HP_TRY(w.orthonormalise());
+      continue;
+    }
     // the eigenpairs of Q inside the span of the k lowest Q^2 Ritz vectors: Rayleigh-Ritz with Q there
     HP_TRY(w.gram(w.X, w.Z, H));
     std::vector<zd> Hk((size_t)k * k), W1;
@@ -843,11 +907,7 @@ extern "C" hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp
       }
     }
     if (converged || it == sweeps) break;
-    // the filter only has to raise the wanted directions: while the pairs are far from converged
-    // the FP32 stencil does (its rounding, ~1e-7 of each vector, stays below what a sweep removes),
-    // the last decades take the FP64 one
-    const double worst = *std::max_element(rn.begin(), rn.end());
-    w.prec = worst > std::max(1e-5, 100.0 * tol) ? HP_PREC_MIXED_FP32 : HP_PREC_FP64;
+    w.prec = pick_filter_precision(*std::max_element(rn.begin(), rn.end()));
     // Chebyshev filter of degree m on Q^2 damping [largest Q^2 Ritz value of the block, l_max], scaled at 0
     const double a = std::min(top2, 0.99 * l_max);
     const double c0 = 0.5 * (l_max + a), e = 0.5 * (l_max - a);
@@ -867,14 +927,34 @@ extern "C" hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp
     HP_TRY(w.orthonormalise());
   }
   HP_CUDA(cudaMemcpyAsync(evecs, w.X, sizeof(double2) * (size_t)k * n, cudaMemcpyDefault, ctx->stream));
+  if (svd) {   // u_j = D v_j / sigma_j = gamma_5 (Q v_j) / sigma_j, Q X in Z
+    std::vector<double> inv(k);
+    for (int j = 0; j < k; ++j) inv[j] = theta[j] > 0.0 ? 1.0 / theta[j] : 0.0;
+    double* invd = nullptr;
+    HP_TRY(hp_ws(ctx, "zeigs.inv", sizeof(double) * (size_t)k, (void**)&invd));
+    HP_CUDA(cudaMemcpyAsync(invd, inv.data(), sizeof(double) * k, cudaMemcpyHostToDevice, ctx->stream));
+    k_left_vectors<<<blocks_for(ctx, n * k, 256), 256, 0, ctx->stream>>>(w.Z, invd, n, k, w.T);
+    HP_LAUNCH_CHECK();
+    HP_CUDA(cudaMemcpyAsync(left, w.T, sizeof(double2) * (size_t)k * n, cudaMemcpyDefault, ctx->stream));
+  }
   HP_CUDA(cudaStreamSynchronize(ctx->stream));
   for (int j = 0; j < k; ++j) {
     evals[j] = theta[j];
     if (resid) resid[j] = rn[j];
   }
   if (!converged) {
-    hp_set_error("hp_wilson_eigs: %d sweeps without reaching tol", sweeps);
+    hp_set_error("%s: %d sweeps without reaching tol", fn, sweeps);
     return HP_ENOCONV;
   }
   return HP_OK;
+}
+
+extern "C" hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k, double tol,
+                                    int32_t max_sweeps, double* evecs, double* evals, double* resid) {
+  return wilson_block_eigs(ctx, op, lat, k, tol, max_sweeps, false, evecs, nullptr, evals, resid);
+}
+
+extern "C" hp_status hp_wilson_svd(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k, double tol,
+                                   int32_t max_sweeps, double* right, double* left, double* sigma, double* resid) {
+  return wilson_block_eigs(ctx, op, lat, k, tol, max_sweeps, true, right, left, sigma, resid);
 }

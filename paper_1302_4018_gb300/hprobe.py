@@ -45,7 +45,8 @@ EXPORTED = ["hp_ctx_create", "hp_ctx_destroy", "hp_last_error", "hp_ctx_synchron
             "hp_operator_apply", "hp_dslash_bench", "hp_profile_enable", "hp_profile_report",
             "hp_launch_count", "hp_operator_apply_noalloc", "hp_probe_sequence", "hp_trace_inv_bounds",
             "hp_sparse_coloring", "hp_sparse_ordering", "hp_sparse_probe_vectors", "hp_trace_inv_sparse", "hp_trace_inv_deflated",
-            "hp_trace_inv_solutions", "hp_trace_prefix", "hp_schur_apply", "hp_laplacian_eigs", "hp_wilson_eigs"]
+            "hp_trace_inv_solutions", "hp_trace_prefix", "hp_schur_apply", "hp_laplacian_eigs", "hp_wilson_eigs", "hp_wilson_svd",
+            "hp_trace_inv_deflated_svd"]
 
 
 class Lattice(C.Structure):
@@ -123,6 +124,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hp_schur_apply": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I64, I32, I32, P, P]),
         "hp_laplacian_eigs": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I32, D, I32, P, P, P]),
         "hp_wilson_eigs": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I32, D, I32, P, P, P]),
+        "hp_wilson_svd": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I32, D, I32, P, P, P, P]),
+        "hp_trace_inv_deflated_svd": (C.c_int, [P, C.POINTER(Operator), C.POINTER(Lattice), I32, P, P, P, I64, D,
+                                                C.POINTER(SolverOpts), P, P, C.POINTER(SolveStats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -316,6 +320,39 @@ class Context:
         _check(lib().hp_wilson_eigs(self._h, C.byref(op), C.byref(make_lattice(dims)), int(k), float(tol),
                                     int(max_sweeps), _ptr(evecs), _ptr(evals), _ptr(resid)))
         return evals, evecs, resid
+
+    def wilson_svd(self, op: Operator, dims, k: int, tol: float = 1e-10, max_sweeps: int = 0, right=None, left=None):
+        """The k smallest singular triplets D v = sigma u: (sigma [k] ascending, right, left complex
+        [k, V, 4, 3] (host arrays by default, or the given complex128 arrays / tensors), resid [k])."""
+        V = int(np.prod(dims))
+        if right is None:
+            right = np.zeros((k, V, 4, 3), dtype=np.complex128)
+        if left is None:
+            left = np.zeros((k, V, 4, 3), dtype=np.complex128)
+        sigma = np.zeros(k)
+        resid = np.zeros(k)
+        _check(lib().hp_wilson_svd(self._h, C.byref(op), C.byref(make_lattice(dims)), int(k), float(tol),
+                                   int(max_sweeps), _ptr(right), _ptr(left), _ptr(sigma), _ptr(resid)))
+        return sigma, right, left, resid
+
+    def trace_inv_deflated_svd(self, op: Operator, dims, right, left, sigma, s_max: int, tol: float,
+                               opts: SolverOpts, q_inout=None):
+        """Wilson deflation with singular triplets D v_j = sigma_j u_j: right, left complex128
+        [k, V, 4, 3] (host arrays or device tensors), sigma float64 [k] (host).  Returns (T, q, stats)."""
+        sg = np.ascontiguousarray(np.asarray(sigma, dtype=np.float64))
+        k = int(sg.shape[0])
+        V = int(np.prod(dims))
+        for a in (right, left):
+            if not (str(a.dtype).endswith("complex128") and int(np.prod(a.shape)) == 12 * k * V):
+                raise ValueError("singular vectors must be complex of %d x %d values" % (k, 12 * V))
+        T = np.zeros(s_max, dtype=np.complex128)
+        st = SolveStats()
+        if q_inout is not None:
+            assert q_inout.dtype == np.complex128 and q_inout.shape == (s_max,)
+        _check(lib().hp_trace_inv_deflated_svd(self._h, C.byref(op), C.byref(make_lattice(dims)), k, _ptr(right),
+                                               _ptr(left), _ptr(sg), int(s_max), float(tol), C.byref(opts),
+                                               _ptr(q_inout), _ptr(T), C.byref(st)))
+        return T, q_inout, st.as_dict()
 
     def trace_inv(self, op: Operator, dims, s_max: int, tol: float, opts: SolverOpts, q_inout=None):
         """Returns (T [s_max] complex, q [s_max] complex or None, stats dict).  ``q_inout``: host

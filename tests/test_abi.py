@@ -162,3 +162,5 @@ def test_eigensolvers_reject_a_missing_context_without_gpu():
     for fn in (lib.hp_wilson_eigs, lib.hp_laplacian_eigs):
         assert fn(None, ctypes.byref(op), ctypes.byref(lat), 2, 1e-10, 0, ev.ctypes.data, ev.ctypes.data,
                   None) == hprobe.HP_EINVAL
+    assert lib.hp_wilson_svd(None, ctypes.byref(op), ctypes.byref(lat), 2, 1e-10, 0, ev.ctypes.data, ev.ctypes.data,
+                             ev.ctypes.data, None) == hprobe.HP_EINVAL

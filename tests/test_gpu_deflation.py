@@ -236,3 +236,83 @@ def test_wilson_deflation_and_eigs_errors(ctx, hp):
         with pytest.raises(hp.HProbeError) as e:
             ctx.wilson_eigs(o, dims, k)
         assert e.value.status == hp.HP_EINVAL
+
+
+# ------------------------------------------------------------------ Wilson: singular triplets
+@pytest.mark.parametrize("dims,k,mfs,csw", [((4, 4, 2, 4), 8, 0.0, 0.0), ((4, 2, 4, 2), 12, 0.02, 0.0),
+                                            ((2, 4, 2, 4), 6, 0.0, 1.0)])
+def test_wilson_svd_matches_the_oracle(ctx, hp, dims, k, mfs, csw):
+    """Singular values within 1e-9 of the oracle's dense SVD; D v_j = sigma_j u_j by the oracle's
+    stencil; both sets orthonormal.  (The residual is measured on Q^2 relative to sigma^2, about
+    ||Q|| / sigma times the relative residual of the same pair of Q: 1e-9 here is ~3e-11 there.)"""
+    mf = synth.mass_field(dims, mfs, 41) if mfs else None
+    U, op = _wilson_op(ctx, hp, dims, 40, mass=0.01, mf=mf, csw=csw)
+    sig, R, L, res = ctx.wilson_svd(op, dims, k, 1e-9)
+    sig_o, _, _ = E.wilson_smallest_singular_triplets(dims, U, 0.12, k, mass=0.01, mass_field=mf, csw=csw)
+    assert np.all(res <= 1e-9)
+    assert np.allclose(sig, sig_o, rtol=1e-9, atol=0), (sig, sig_o)
+    C = O.clover_term(U, dims, 0.12, csw) if csw else None
+    for j in range(k):
+        Dv = O.wilson_apply(R[j], U, dims, 0.12, 0.01, mf, clover=C)
+        assert np.linalg.norm(Dv - sig[j] * L[j]) <= 1e-9 * sig[j], j
+    for X in (R, L):
+        G = np.einsum("ixsc,jxsc->ij", np.conj(X), X)
+        assert np.allclose(G, np.eye(k), atol=1e-10)
+
+
+@pytest.mark.parametrize("dims,k,s,prec,eo,device", [((4, 4, 2, 4), 8, 16, "fp64", 0, False),
+                                                     ((4, 4, 2, 4), 20, 32, "fp16", 1, True),
+                                                     ((6, 2, 2, 2), 6, 24, "fp64", 0, False)])
+def test_wilson_svd_deflated_trace_matches_oracle(ctx, hp, dims, k, s, prec, eo, device):
+    """T_s = sum_j u_j^H v_j / sigma_j + (1/s) sum_m q'_m against the oracle's dense solves with the
+    left projector on the sources, within 1e-9 (complex exact part included)."""
+    mf = synth.mass_field(dims, 0.01, 43)
+    U, op = _wilson_op(ctx, hp, dims, 42, mf=mf)
+    sig, R, L = E.wilson_smallest_singular_triplets(dims, U, 0.12, k, mass_field=mf)
+    q = np.zeros(s, dtype=np.complex128)
+    r, l = (_dev(R), _dev(L)) if device else (R, L)
+    T, q, st = ctx.trace_inv_deflated_svd(op, dims, r, l, sig, s, 1e-12,
+                                          ctx.make_opts(prec, z0_seed=5, even_odd=eo, rhs_block=24), q_inout=q)
+    qo, exact = E.wilson_deflated_quadratures_svd(dims, U, 0.12, sig, R, L, 0, s, 5, mass_field=mf)
+    To = exact + E.trace_prefix(qo)
+    assert np.abs(q - qo).max() <= 1e-9 * np.abs(qo).max()
+    assert np.abs(T - To).max() <= 1e-9 * np.abs(To).max()
+
+
+def test_wilson_svd_deflation_with_library_triplets(ctx, hp):
+    """hp_wilson_svd feeding hp_trace_inv_deflated_svd gives the oracle's deflated estimate, and
+    the full set of triplets leaves nothing to probe."""
+    dims = (4, 4, 2, 4)
+    U, op = _wilson_op(ctx, hp, dims, 45)
+    R = torch.zeros((10, 128, 4, 3), dtype=torch.complex128, device="cuda:0")
+    L = torch.zeros_like(R)
+    sig, R, L, _ = ctx.wilson_svd(op, dims, 10, 1e-10, right=R, left=L)
+    T, _, _ = ctx.trace_inv_deflated_svd(op, dims, R, L, sig, 16, 1e-12, ctx.make_opts("fp64", z0_seed=6))
+    s_o, R_o, L_o = E.wilson_smallest_singular_triplets(dims, U, 0.12, 10)
+    qo, exact = E.wilson_deflated_quadratures_svd(dims, U, 0.12, s_o, R_o, L_o, 0, 16, 6)
+    To = exact + E.trace_prefix(qo)
+    assert np.abs(T - To).max() <= 1e-8 * np.abs(To).max()
+    d2 = (2, 2, 2, 2)
+    U2, op2 = _wilson_op(ctx, hp, d2, 46)
+    s2, R2, L2 = E.wilson_smallest_singular_triplets(d2, U2, 0.12, 192)
+    T2, q2, _ = ctx.trace_inv_deflated_svd(op2, d2, R2, L2, s2, 8, 1e-12, ctx.make_opts("fp64", z0_seed=2),
+                                           q_inout=np.zeros(8, dtype=np.complex128))
+    ref = np.trace(np.linalg.inv(O.wilson_dense(U2, d2, 0.12)))
+    assert np.abs(q2).max() <= 1e-9 * abs(ref) and np.allclose(T2, ref, rtol=1e-10, atol=0)
+
+
+def test_wilson_svd_errors(ctx, hp):
+    dims = (4, 4, 2, 4)
+    U, op = _wilson_op(ctx, hp, dims, 47)
+    sig, R, L = E.wilson_smallest_singular_triplets(dims, U, 0.12, 4)
+    bad = sig.copy()
+    bad[2] = 0.0
+    with pytest.raises(hp.HProbeError) as e:
+        ctx.trace_inv_deflated_svd(op, dims, R, L, bad, 8, 1e-10, ctx.make_opts("fp64"))
+    assert e.value.status == hp.HP_EINVAL
+    with pytest.raises(ValueError):
+        ctx.trace_inv_deflated_svd(op, dims, R, L[:2], sig, 8, 1e-10, ctx.make_opts("fp64"))
+    lap = ctx.make_operator(hp.OP_LAPLACIAN, 0.3)
+    with pytest.raises(hp.HProbeError) as e:
+        ctx.wilson_svd(lap, dims, 2)
+    assert e.value.status == hp.HP_EINVAL
