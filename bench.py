@@ -775,11 +775,13 @@ def run_variance(args):
 
 def run_wilson_deflation(args):
     """Deflated probing of the Wilson matrix (the conclusions' next step, on the Wilson operator):
-    8^4, kappa 0.124, eps 0.4 (link seed 1004), the k eigenpairs of gamma_5 D with the smallest
-    |lambda| from hp_wilson_eigs, then per z_0 seed S probing vectors with full dilution, plain and
-    deflated (the same FP16 even-odd solves, the deflated quadratures corrected on the device).
-    One step = one seed, both estimates; value = probing solves/s; the JSON carries the spread of
-    T_s over the seeds for both and the eigensolver's time and residuals."""
+    8^4, kappa 0.124, eps 0.4 (link seed 1004), or 16^4, kappa 0.115, eps 0.3 (link seed 1002);
+    the k eigenpairs of gamma_5 D with the smallest |lambda| from hp_wilson_eigs (or, with
+    --defl-svd, the k smallest singular triplets of D from hp_wilson_svd), then per z_0 seed S
+    probing vectors with full dilution, plain and deflated (the same FP16 even-odd solves, the
+    deflated quadratures corrected on the device).  One step = one seed, both estimates; value =
+    probing solves/s; the JSON carries the spread of T_s over the seeds for both and the
+    eigensolver's time and residuals."""
     import torch
 
     from paper_1302_4018_gb300 import hprobe, synth
@@ -787,23 +789,33 @@ def run_wilson_deflation(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     ctx = hprobe.Context(0, stream=stream.cuda_stream)
-    dims = (8, 8, 8, 8)
-    kappa, k, S = 0.124, args.defl_k, args.defl_vectors
-    U = synth.gauge_links(dims, 0.4, 1004, device="cuda:0")
+    L = args.defl_lattice
+    dims = (L, L, L, L)
+    kappa, eps, link_seed = (0.124, 0.4, 1004) if L == 8 else (0.115, 0.3, 1002)
+    k, S, svd = args.defl_k, args.defl_vectors, args.defl_svd
+    U = synth.gauge_links(dims, eps, link_seed, device="cuda:0")
     links = torch.from_numpy(U.view(np.float64).reshape(-1)).to("cuda:0")
+    del U
     op = ctx.make_operator(hprobe.OP_WILSON, 0.0, kappa, links, None)
     V = int(np.prod(dims))
     ev = torch.zeros((k, V, 4, 3), dtype=torch.complex128, device="cuda:0")
+    lv = torch.zeros_like(ev) if svd else None
     torch.cuda.synchronize()
     t_e = time.perf_counter()
-    lam, ev, res = ctx.wilson_eigs(op, dims, k, tol=1e-10, evecs=ev)
+    if svd:   # the triplets' residual is relative to sigma^2: 1e-9 there is about 1e-10 / sigma on Q
+        lam, ev, lv, res = ctx.wilson_svd(op, dims, k, tol=1e-9, right=ev, left=lv)
+    else:
+        lam, ev, res = ctx.wilson_eigs(op, dims, k, tol=1e-10, evecs=ev)
     torch.cuda.synchronize()
     t_e = time.perf_counter() - t_e
 
     def step(seed):
         opts = ctx.make_opts(args.precision, z0_seed=seed, rhs_block=96, even_odd=1)
         T0, _, s0 = ctx.trace_inv(op, dims, S, 1e-10, opts)
-        T1, _, s1 = ctx.trace_inv_deflated(op, dims, ev, lam, S, 1e-10, opts)
+        if svd:
+            T1, _, s1 = ctx.trace_inv_deflated_svd(op, dims, ev, lv, lam, S, 1e-10, opts)
+        else:
+            T1, _, s1 = ctx.trace_inv_deflated(op, dims, ev, lam, S, 1e-10, opts)
         return T0.real, T1.real, s0["rhs_solved"] + s1["rhs_solved"]
 
     for w in range(args.warmup):
@@ -824,17 +836,21 @@ def run_wilson_deflation(args):
               "std_deflated": [float(T1[:, s - 1].std(ddof=1)) if len(runs) > 1 else None for s in points],
               "mean_plain": [float(T0[:, s - 1].mean()) for s in points],
               "mean_deflated": [float(T1[:, s - 1].mean()) for s in points]}
-    out = {"metric": "probing solves/s, deflated Wilson probing (8^4, kappa 0.124, %d modes of gamma_5 D)" % k,
+    modes = "%d singular triplets of D" % k if svd else "%d modes of gamma_5 D" % k
+    out = {"metric": "probing solves/s, deflated Wilson probing (%d^4, kappa %g, %s)" % (L, kappa, modes),
            "value": solves / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f16-storage/f32-math + f64 reliable updates" if args.precision == "fp16" else args.precision,
            "data": "synthetic: SU(3) links exp(i eps H), seeded (no gauge ensemble available)",
-           "config": {"workload": "8^4 Wilson-Dirac, kappa 0.124, eps 0.4, link seed 1004; %d vectors x 12 "
-                                  "dilutions per z_0 seed, plain and with the %d smallest |lambda| of gamma_5 D "
-                                  "deflated; %d seeds" % (S, k, args.steps),
+           "config": {"workload": "%d^4 Wilson-Dirac, kappa %g, eps %g, link seed %d; %d vectors x 12 "
+                                  "dilutions per z_0 seed, plain and with the %s deflated; %d seeds"
+                                  % (L, kappa, eps, link_seed, S,
+                                     ("%d smallest singular triplets of D" if svd else
+                                      "%d smallest |lambda| of gamma_5 D") % k, args.steps),
                       "precision": args.precision, "even_odd": True},
-           "wilson_eigs": {"k": k, "seconds": t_e, "abs_lambda_min": float(np.abs(lam).min()),
-                           "abs_lambda_max": float(np.abs(lam).max()), "max_rel_residual": float(res.max())},
+           ("wilson_svd" if svd else "wilson_eigs"): {
+               "k": k, "seconds": t_e, "abs_lambda_min": float(np.abs(lam).min()),
+               "abs_lambda_max": float(np.abs(lam).max()), "max_rel_residual": float(res.max())},
            "spread_over_seeds": spread}
     print(json.dumps(out), flush=True)
 
@@ -1194,6 +1210,11 @@ def main():
                              "wilson_deflation"])
     ap.add_argument("--defl-k", type=int, default=48, help="modes of gamma_5 D deflated (wilson_deflation)")
     ap.add_argument("--defl-vectors", type=int, default=64, help="probing vectors per seed (wilson_deflation)")
+    ap.add_argument("--defl-lattice", type=int, choices=(8, 16), default=8,
+                    help="wilson_deflation lattice: 8 (8^4, kappa 0.124) or 16 (16^4, kappa 0.115)")
+    ap.add_argument("--defl-svd", action="store_true",
+                    help="wilson_deflation: deflate singular triplets of D (hp_wilson_svd) instead of the "
+                         "eigenpairs of gamma_5 D")
     ap.add_argument("--config2-vectors", type=int, default=512)
     ap.add_argument("--study-seeds", type=int, default=32, help="z_0 draws of the Wilson speed-up ratio")
     ap.add_argument("--study-wilson-vectors", type=int, default=512)

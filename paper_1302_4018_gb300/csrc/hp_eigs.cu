@@ -368,6 +368,36 @@ __global__ void k_left_vectors(const double2* __restrict__ Z, const double* __re
   }
 }
 
+// residual norms: part[j][bx] = sum over the entries of chunk bx of |AX[j][e] - th[j] X[j][e]|^2 for
+// the first k vectors (one block per chunk and vector; a fixed-order tree in shared memory)
+__global__ void __launch_bounds__(256) k_zresid(const double2* __restrict__ AX, const double2* __restrict__ X,
+                                                const double* __restrict__ th, long long n, int k, long long per_block,
+                                                double* __restrict__ part) {
+  __shared__ double sh[256];
+  const long long e_begin = (long long)blockIdx.x * per_block;
+  const long long e_end = std::min<long long>(n, e_begin + per_block);
+  for (int j = blockIdx.y; j < k; j += gridDim.y) {
+    const double t = th[j];
+    const double2* a = AX + (size_t)j * n;
+    const double2* x = X + (size_t)j * n;
+    double acc = 0.0;
+    for (long long e = e_begin + threadIdx.x; e < e_end; e += 256) {
+      const double2 av = a[e], xv = x[e];
+      const double rx = fma(-t, xv.x, av.x), ry = fma(-t, xv.y, av.y);
+      acc = fma(rx, rx, acc);
+      acc = fma(ry, ry, acc);
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(size_t)j * gridDim.x + blockIdx.x] = sh[0];
+    __syncthreads();
+  }
+}
+
 // Cholesky G = R^H R of a Hermitian G (upper R, row-major); false if a pivot is not positive
 bool cholesky_upper_z(std::vector<zd>& G, int b) {
   for (int j = 0; j < b; ++j) {
@@ -519,6 +549,24 @@ struct ZEigWork {
     k_eig_lincomb<<<blocks_for(ctx, m, 256), 256, 0, ctx->stream>>>((double*)out, (const double*)P, (const double*)Q,
                                                                      (const double*)R, a, c, e, m);
     HP_LAUNCH_CHECK();
+    return HP_OK;
+  }
+  // r2[j] = ||AX_j - th_j X_j||^2 for j < k (th real); the partials summed on the host in chunk order
+  hp_status resid_norms(const double2* AX, const double2* X, const std::vector<double>& th, int k,
+                        std::vector<double>& r2) {
+    HP_CUDA(cudaMemcpyAsync(Wd, th.data(), sizeof(double) * k, cudaMemcpyHostToDevice, ctx->stream));
+    {
+      ProfScope ps(ctx, "k_zresid");
+      k_zresid<<<dim3(nbx, std::min(k, 65535)), 256, 0, ctx->stream>>>(AX, X, (const double*)Wd, n, k, epb,
+                                                                        (double*)part);
+    }
+    HP_LAUNCH_CHECK();
+    std::vector<double> raw((size_t)nbx * k);
+    HP_CUDA(cudaMemcpyAsync(raw.data(), part, sizeof(double) * raw.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    HP_CUDA(cudaStreamSynchronize(ctx->stream));   // th and raw (host) outlive the copies
+    r2.assign(k, 0.0);
+    for (int j = 0; j < k; ++j)
+      for (int bx = 0; bx < nbx; ++bx) r2[j] += raw[(size_t)j * nbx + bx];
     return HP_OK;
   }
   hp_status orthonormalise() {
@@ -842,17 +890,13 @@ static hp_status wilson_block_eigs(hp_ctx* ctx, const hp_operator* op, const hp_
       // singular triplets: the Q^2 Ritz pairs themselves, v_j = X_j, sigma_j = sqrt(theta2_j);
       // residual ||Q^2 v_j - sigma_j^2 v_j|| / sigma_j^2, Y = Q^2 X (FP64) serving the filter as well
       HP_TRY(w.apply_q(w.Z, w.Y));
-      std::vector<zd> Dg((size_t)b * b, 0.0);
-      for (int j = 0; j < k; ++j) Dg[(size_t)j * b + j] = -theta2[j];
-      HP_TRY(w.rotate(w.X, Dg, w.T));
-      HP_TRY(w.lincomb(w.T, w.Y, w.T, nullptr, 1.0, 1.0, 0.0));
-      std::vector<zd> RR;
-      HP_TRY(w.gram(w.T, w.T, RR));
+      std::vector<double> r2;
+      HP_TRY(w.resid_norms(w.Y, w.X, theta2, k, r2));
       converged = true;
       theta.assign(k, 0.0);
       for (int j = 0; j < k; ++j) {
         theta[j] = std::sqrt(std::max(0.0, theta2[j]));
-        rn[j] = std::sqrt(std::max(0.0, RR[(size_t)j * b + j].real())) / std::max(theta2[j], 1e-300);
+        rn[j] = std::sqrt(std::max(0.0, r2[j])) / std::max(theta2[j], 1e-300);
         if (!(rn[j] <= tol)) converged = false;
       }
       if (converged || it == sweeps) break;
@@ -894,15 +938,11 @@ static hp_status wilson_block_eigs(hp_ctx* ctx, const hp_operator* op, const hp_
     std::swap(w.X, w.Y);
     HP_TRY(w.rotate(w.Z, Wb, w.Y));   // Y = Q X, its first k columns the pairs' Q w_j
     {
-      std::vector<zd> Dg((size_t)b * b, 0.0);
-      for (int j = 0; j < k; ++j) Dg[(size_t)j * b + j] = -theta[j];
-      HP_TRY(w.rotate(w.X, Dg, w.Z));                                   // Z = -X diag(theta, 0)
-      HP_TRY(w.lincomb(w.Z, w.Y, w.Z, nullptr, 1.0, 1.0, 0.0));         // Z = Q X - X diag(theta)
-      std::vector<zd> RR;
-      HP_TRY(w.gram(w.Z, w.Z, RR));
+      std::vector<double> r2;                                           // ||Q w_j - theta_j w_j||^2
+      HP_TRY(w.resid_norms(w.Y, w.X, theta, k, r2));
       converged = true;
       for (int j = 0; j < k; ++j) {
-        rn[j] = std::sqrt(std::max(0.0, RR[(size_t)j * b + j].real())) / std::max(std::fabs(theta[j]), 1e-300);
+        rn[j] = std::sqrt(std::max(0.0, r2[j])) / std::max(std::fabs(theta[j]), 1e-300);
         if (!(rn[j] <= tol)) converged = false;
       }
     }
