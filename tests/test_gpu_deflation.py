@@ -301,6 +301,26 @@ def test_wilson_svd_deflation_with_library_triplets(ctx, hp):
     assert np.abs(q2).max() <= 1e-9 * abs(ref) and np.allclose(T2, ref, rtol=1e-10, atol=0)
 
 
+def test_wilson_svd_at_8x8x8x8_by_the_oracle_stencil(ctx, hp):
+    """The 48 triplets of the 8^4 deflation workload (kappa 0.124, eps 0.4, link seed 1004): the
+    adjoint relation D^H u_j = sigma_j v_j, which the solver never forms (it returns u_j = D v_j /
+    sigma_j), holds to the residual bound tol sigma_j with D^H applied by the oracle's stencil;
+    D v_j = sigma_j u_j to rounding; both sets orthonormal; sigma ascending."""
+    dims, k, tol = (8, 8, 8, 8), 48, 1e-9
+    U = synth.gauge_links(dims, 0.4, 1004)
+    op = ctx.make_operator(hp.OP_WILSON, 0.0, 0.124, _dev(U.view(np.float64).reshape(-1)), None)
+    sig, R, L, res = ctx.wilson_svd(op, dims, k, tol)
+    assert np.all(res <= tol) and np.all(np.diff(sig) >= 0) and sig[0] > 0
+    for j in range(k):
+        Dv = O.wilson_apply(R[j], U, dims, 0.124)
+        assert np.linalg.norm(Dv - sig[j] * L[j]) <= 1e-12 * sig[j], j
+        DHu = O.wilson_apply(L[j], U, dims, 0.124, dagger=True)
+        assert np.linalg.norm(DHu - sig[j] * R[j]) <= 1.5 * tol * sig[j], j
+    for X, atol in ((R, 1e-10), (L, 1e-8)):
+        G = np.einsum("ixsc,jxsc->ij", np.conj(X), X)
+        assert np.abs(G - np.eye(k)).max() <= atol
+
+
 def test_wilson_svd_errors(ctx, hp):
     dims = (4, 4, 2, 4)
     U, op = _wilson_op(ctx, hp, dims, 47)
