@@ -802,10 +802,12 @@ def run_wilson_deflation(args):
     lv = torch.zeros_like(ev) if svd else None
     torch.cuda.synchronize()
     t_e = time.perf_counter()
-    if svd:   # the triplets' residual is relative to sigma^2: 1e-9 there is about 1e-10 / sigma on Q
-        lam, ev, lv, res = ctx.wilson_svd(op, dims, k, tol=1e-9, right=ev, left=lv)
+    # the triplets' residual is relative to sigma^2: 1e-9 there is about 1e-10 / sigma on Q
+    etol = args.defl_tol if args.defl_tol else (1e-9 if svd else 1e-10)
+    if svd:
+        lam, ev, lv, res = ctx.wilson_svd(op, dims, k, tol=etol, right=ev, left=lv)
     else:
-        lam, ev, res = ctx.wilson_eigs(op, dims, k, tol=1e-10, evecs=ev)
+        lam, ev, res = ctx.wilson_eigs(op, dims, k, tol=etol, evecs=ev)
     torch.cuda.synchronize()
     t_e = time.perf_counter() - t_e
 
@@ -849,7 +851,7 @@ def run_wilson_deflation(args):
                                       "%d smallest |lambda| of gamma_5 D") % k, args.steps),
                       "precision": args.precision, "even_odd": True},
            ("wilson_svd" if svd else "wilson_eigs"): {
-               "k": k, "seconds": t_e, "abs_lambda_min": float(np.abs(lam).min()),
+               "k": k, "tol": etol, "seconds": t_e, "abs_lambda_min": float(np.abs(lam).min()),
                "abs_lambda_max": float(np.abs(lam).max()), "max_rel_residual": float(res.max())},
            "spread_over_seeds": spread}
     print(json.dumps(out), flush=True)
@@ -1212,6 +1214,8 @@ def main():
     ap.add_argument("--defl-vectors", type=int, default=64, help="probing vectors per seed (wilson_deflation)")
     ap.add_argument("--defl-lattice", type=int, choices=(8, 16), default=8,
                     help="wilson_deflation lattice: 8 (8^4, kappa 0.124) or 16 (16^4, kappa 0.115)")
+    ap.add_argument("--defl-tol", type=float, default=0.0,
+                    help="wilson_deflation eigensolver tolerance (0: 1e-9 for triplets, 1e-10 for eigenpairs)")
     ap.add_argument("--defl-svd", action="store_true",
                     help="wilson_deflation: deflate singular triplets of D (hp_wilson_svd) instead of the "
                          "eigenpairs of gamma_5 D")

@@ -320,9 +320,10 @@ hp_status hp_trace_inv_deflated(hp_ctx* ctx, const hp_operator* op, const hp_lat
  * of each quadrature, as in hp_trace_inv_deflated (whose gamma_5 eigenpairs are
  * the triplets v = w, u = sign(lambda) gamma_5 w, sigma = |lambda|).  The
  * identity holds for any singular triplets, so the k smallest need not sit at a
- * gap of the spectrum.  Arguments and errors as hp_trace_inv_deflated for the
- * Wilson operator (HP_EINVAL also for a Laplacian, NULL left vectors or a
- * sigma <= 0). */
+ * gap of the spectrum; it needs only D^-1 u_j = v_j / sigma_j, so it also holds
+ * for the Rayleigh-Ritz triplets hp_wilson_svd returns before it converges.
+ * Arguments and errors as hp_trace_inv_deflated for the Wilson operator
+ * (HP_EINVAL also for a Laplacian, NULL left vectors or a sigma <= 0). */
 hp_status hp_trace_inv_deflated_svd(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k,
                                     const double* right, const double* left, const double* sigma, int64_t s_max,
                                     double tol, const hp_solver_opts* opts, double* q_inout, double* trace_prefix,
@@ -374,7 +375,12 @@ hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp_lattice* l
  * shells of 12 and 96: k = 12 in 3.6 s and k = 108 in 74 s to tol 1e-8, while
  * k = 24 stays near 1e-3).  right, left: complex double[k][V][4][3] (host or device);
  * sigma (host double[k]) ascending; resid (host double[k], nullable).  Errors as
- * hp_wilson_eigs (NULL left included). */
+ * hp_wilson_eigs (NULL left included).  On HP_ENOCONV the outputs hold the last
+ * Rayleigh-Ritz triplets: v orthonormal, sigma_j^2 their Ritz values of Q^2,
+ * u_j = D v_j / sigma_j (orthonormal as well, since V^H Q^2 V = diag(sigma^2));
+ * only D^H u_j = sigma_j v_j is off by the residual.  hp_trace_inv_deflated_svd
+ * needs no more than D v_j = sigma_j u_j, so deflation with an unconverged
+ * result stays exact and unbiased; it removes less variance. */
 hp_status hp_wilson_svd(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k, double tol,
                         int32_t max_sweeps, double* right, double* left, double* sigma, double* resid);
 

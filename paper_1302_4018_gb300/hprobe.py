@@ -321,9 +321,12 @@ class Context:
                                     int(max_sweeps), _ptr(evecs), _ptr(evals), _ptr(resid)))
         return evals, evecs, resid
 
-    def wilson_svd(self, op: Operator, dims, k: int, tol: float = 1e-10, max_sweeps: int = 0, right=None, left=None):
+    def wilson_svd(self, op: Operator, dims, k: int, tol: float = 1e-10, max_sweeps: int = 0, right=None, left=None,
+                   check: bool = True):
         """The k smallest singular triplets D v = sigma u: (sigma [k] ascending, right, left complex
-        [k, V, 4, 3] (host arrays by default, or the given complex128 arrays / tensors), resid [k])."""
+        [k, V, 4, 3] (host arrays by default, or the given complex128 arrays / tensors), resid [k]).
+        check=False returns the last Rayleigh-Ritz triplets when max_sweeps ends the iteration before
+        tol (HP_ENOCONV): D v_j = sigma_j u_j still holds, so deflation with them stays exact."""
         V = int(np.prod(dims))
         if right is None:
             right = np.zeros((k, V, 4, 3), dtype=np.complex128)
@@ -331,8 +334,10 @@ class Context:
             left = np.zeros((k, V, 4, 3), dtype=np.complex128)
         sigma = np.zeros(k)
         resid = np.zeros(k)
-        _check(lib().hp_wilson_svd(self._h, C.byref(op), C.byref(make_lattice(dims)), int(k), float(tol),
-                                   int(max_sweeps), _ptr(right), _ptr(left), _ptr(sigma), _ptr(resid)))
+        st = lib().hp_wilson_svd(self._h, C.byref(op), C.byref(make_lattice(dims)), int(k), float(tol),
+                                 int(max_sweeps), _ptr(right), _ptr(left), _ptr(sigma), _ptr(resid))
+        if check or st != HP_ENOCONV:
+            _check(st)
         return sigma, right, left, resid
 
     def trace_inv_deflated_svd(self, op: Operator, dims, right, left, sigma, s_max: int, tol: float,

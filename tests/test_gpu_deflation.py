@@ -321,6 +321,35 @@ def test_wilson_svd_at_8x8x8x8_by_the_oracle_stencil(ctx, hp):
         assert np.abs(G - np.eye(k)).max() <= atol
 
 
+def test_wilson_svd_unconverged_triplets_deflate_exactly(ctx, hp):
+    """After one sweep (far from tol) hp_wilson_svd's outputs are Rayleigh-Ritz triplets: D v_j =
+    sigma_j u_j by the oracle's stencil and both sets orthonormal, while D^H u_j = sigma_j v_j fails;
+    the deflated sequence with them matches the oracle's and reaches Tr D^-1 (dense inverse) at
+    s = N."""
+    dims, k, N = (4, 4, 2, 4), 8, 128
+    U, op = _wilson_op(ctx, hp, dims, 48)
+    with pytest.raises(hp.HProbeError) as e:
+        ctx.wilson_svd(op, dims, k, 1e-12, max_sweeps=1)
+    assert e.value.status == hp.HP_ENOCONV
+    sig, R, L, res = ctx.wilson_svd(op, dims, k, 1e-12, max_sweeps=1, check=False)
+    assert res.max() > 1e-6 and np.all(sig > 0)
+    off = 0.0
+    for j in range(k):
+        assert np.linalg.norm(O.wilson_apply(R[j], U, dims, 0.12) - sig[j] * L[j]) <= 1e-12 * sig[j], j
+        off = max(off, np.linalg.norm(O.wilson_apply(L[j], U, dims, 0.12, dagger=True) - sig[j] * R[j]))
+    assert off > 1e-6
+    for X in (R, L):
+        G = np.einsum("ixsc,jxsc->ij", np.conj(X), X)
+        assert np.abs(G - np.eye(k)).max() <= 1e-10
+    T, q, _ = ctx.trace_inv_deflated_svd(op, dims, R, L, sig, N, 1e-12, ctx.make_opts("fp64", z0_seed=8),
+                                         q_inout=np.zeros(N, dtype=np.complex128))
+    qo, exact = E.wilson_deflated_quadratures_svd(dims, U, 0.12, sig, R, L, 0, 16, 8)
+    To = exact + E.trace_prefix(qo)
+    assert np.abs(T[:16] - To).max() <= 1e-9 * np.abs(To).max()
+    ref = np.trace(np.linalg.inv(O.wilson_dense(U, dims, 0.12)))
+    assert abs(T[-1] - ref) <= 1e-9 * abs(ref)
+
+
 def test_wilson_svd_errors(ctx, hp):
     dims = (4, 4, 2, 4)
     U, op = _wilson_op(ctx, hp, dims, 47)

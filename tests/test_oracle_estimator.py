@@ -459,3 +459,29 @@ def test_wilson_svd_deflated_quadrature_is_the_plain_one_minus_a_projection_sum(
     lam, Wq = E.wilson_lowest_eigenpairs(dims, U, kappa, 7)
     qg, exg = E.wilson_deflated_quadratures(dims, U, kappa, lam, Wq, 0, 8, z0_seed=3)
     assert np.allclose(qd, qg, rtol=0, atol=1e-11 * np.abs(q0).max()) and abs(ex - exg) <= 1e-11 * abs(exg)
+
+
+def test_wilson_deflation_with_unconverged_ritz_triplets_is_exact():
+    """Rayleigh-Ritz triplets of Q^2 = D^H D on an arbitrary orthonormal block (v_j the Ritz vectors,
+    sigma_j^2 the Ritz values, u_j = D v_j / sigma_j) are not singular triplets (D^H u_j differs from
+    sigma_j v_j), but U is orthonormal and D^-1 u_j = v_j / sigma_j holds exactly, so the deflated
+    sequence still reaches Tr D^-1 at s = N: an unconverged eigensolver leaves the estimate exact."""
+    dims, kappa = (2, 2, 4, 2), 0.12
+    U = synth.gauge_links(dims, 0.4, 14)
+    D = O.wilson_dense(U, dims, kappa)
+    n, b, k = D.shape[0], 12, 6
+    rng = np.random.default_rng(5)
+    X, _ = np.linalg.qr(rng.standard_normal((n, b)) + 1j * rng.standard_normal((n, b)))
+    DX = D @ X
+    th2, W = np.linalg.eigh(DX.conj().T @ DX)
+    Vr = (X @ W)[:, :k]
+    sig = np.sqrt(th2[:k])
+    Ul = (DX @ W)[:, :k] / sig
+    assert np.allclose(Ul.conj().T @ Ul, np.eye(k), rtol=0, atol=1e-12)
+    assert np.linalg.norm(D.conj().T @ Ul - Vr * sig) > 1e-2
+    V = int(np.prod(dims))
+    R, L = Vr.T.reshape(k, V, 4, 3), Ul.T.reshape(k, V, 4, 3)
+    q, exact = E.wilson_deflated_quadratures_svd(dims, U, kappa, sig, R, L, 0, 32, z0_seed=6)
+    T = exact + E.trace_prefix(q)
+    ref = np.trace(np.linalg.inv(D))
+    assert abs(T[-1] - ref) <= 1e-11 * abs(ref)
