@@ -357,7 +357,8 @@ hp_status hp_trace_inv_deflated_svd(hp_ctx* ctx, const hp_operator* op, const hp
  * last iterate).  evecs: complex double[k][V][4][3] (host or device), w_j
  * orthonormal; evals (host double[k]): lambda_j ordered by |lambda_j|; resid
  * (host double[k], nullable): the relative residuals.  Errors: HP_EINVAL for a
- * Laplacian, k outside [1, 6 V], tol <= 0, NULL outputs. */
+ * Laplacian, k outside [1, min(6 V, 1024)] (the Rayleigh-Ritz steps diagonalise
+ * (2k + 8)^2 matrices on the host), tol <= 0, NULL outputs. */
 hp_status hp_wilson_eigs(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k, double tol,
                          int32_t max_sweeps, double* evecs, double* evals, double* resid);
 
@@ -399,7 +400,8 @@ hp_status hp_wilson_svd(hp_ctx* ctx, const hp_operator* op, const hp_lattice* la
  * evecs (host or device, double[k][V], lexicographic sites): orthonormal;
  * evals (host, double[k]): ascending; resid (host, nullable, double[k]): the
  * relative residuals reached.  max_sweeps <= 0: 200.
- * Errors: HP_EINVAL for a Wilson operator, k outside [1, V/2], tol <= 0, NULL
+ * Errors: HP_EINVAL for a Wilson operator, k outside [1, min(V/2, 1024)] (the
+ * Rayleigh-Ritz steps diagonalise b^2 matrices on the host), tol <= 0, NULL
  * outputs; HP_ENOCONV when max_sweeps pass first (outputs still written). */
 hp_status hp_laplacian_eigs(hp_ctx* ctx, const hp_operator* op, const hp_lattice* lat, int32_t k, double tol,
                             int32_t max_sweeps, double* evecs, double* evals, double* resid);

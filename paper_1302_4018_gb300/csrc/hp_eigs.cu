@@ -34,6 +34,9 @@ hp_status hp_apply_wilson(hp_ctx* ctx, const hp_operator* op, LatGeom g, int nrh
 namespace {
 
 constexpr int GT = 32;          // Gram tile (GT x GT entries per block)
+// the largest k: each Rayleigh-Ritz step diagonalises a b x b matrix (b <= 2k + 8) on the host by
+// cyclic Jacobi, O(b^3) per sweep, and the Gram launches take (b / GT)^2 blocks in grid y
+#define HP_EIGS_MAX_K 1024
 constexpr int GCH = 32;         // sites per shared-memory chunk
 constexpr int CJ = 16;          // outputs per thread of the block rotation
 
@@ -618,8 +621,8 @@ extern "C" hp_status hp_laplacian_eigs(hp_ctx* ctx, const hp_operator* op, const
   for (int j = (int)dims.size(); j < 8; ++j) g.L[j] = 1;
   g.op_kind = HP_OP_LAPLACIAN;
   const int V = g.V;
-  if (k < 1 || 2LL * k > V || !(tol > 0.0) || !evecs || !evals) {
-    hp_set_error("hp_laplacian_eigs: k in [1, V/2], tol > 0 and output arrays required");
+  if (k < 1 || 2LL * k > V || k > HP_EIGS_MAX_K || !(tol > 0.0) || !evecs || !evals) {
+    hp_set_error("hp_laplacian_eigs: k in [1, min(V/2, %d)], tol > 0 and output arrays required", HP_EIGS_MAX_K);
     return HP_EINVAL;
   }
   HP_TRY(hp_prepare_mass(ctx, op, &g, "eigs"));
@@ -754,8 +757,8 @@ static hp_status wilson_block_eigs(hp_ctx* ctx, const hp_operator* op, const hp_
   g.dof = 12;
   const int V = g.V;
   const long long n = 12LL * V;
-  if (k < 1 || 2LL * k > n || !(tol > 0.0) || !evecs || !evals || (svd && !left)) {
-    hp_set_error("%s: k in [1, 6 V], tol > 0 and output arrays required", fn);
+  if (k < 1 || 2LL * k > n || k > HP_EIGS_MAX_K || !(tol > 0.0) || !evecs || !evals || (svd && !left)) {
+    hp_set_error("%s: k in [1, min(6 V, %d)], tol > 0 and output arrays required", fn, HP_EIGS_MAX_K);
     return HP_EINVAL;
   }
   // spectrum bound of Q^2 = D^H D: ||D|| <= |1 + m| + max |mu| + 16 kappa (eight hops of norm 2 kappa)

@@ -142,6 +142,9 @@ def test_laplacian_eigs_errors(ctx, hp):
     with pytest.raises(hp.HProbeError) as e:
         ctx.laplacian_eigs(ctx.make_operator(hp.OP_WILSON, 0.0, 0.1, links), dims, 2)
     assert e.value.status == hp.HP_EINVAL
+    with pytest.raises(hp.HProbeError) as e:
+        ctx.laplacian_eigs(op, (8, 8, 8, 8), 1025)             # above the cap of 1024, below V / 2
+    assert e.value.status == hp.HP_EINVAL
 
 
 # ------------------------------------------------------------------ Wilson: eigenpairs of gamma_5 D, deflation
@@ -365,3 +368,9 @@ def test_wilson_svd_errors(ctx, hp):
     with pytest.raises(hp.HProbeError) as e:
         ctx.wilson_svd(lap, dims, 2)
     assert e.value.status == hp.HP_EINVAL
+    d4 = (4, 4, 4, 4)   # k above the cap of 1024, below 6 V = 1536 (rejected before the links are read)
+    op4 = ctx.make_operator(hp.OP_WILSON, 0.0, 0.12, torch.zeros(256 * 72, dtype=torch.float64, device="cuda:0"))
+    for fn in (ctx.wilson_svd, ctx.wilson_eigs):
+        with pytest.raises(hp.HProbeError) as e:
+            fn(op4, d4, 1025)
+        assert e.value.status == hp.HP_EINVAL
