@@ -23,12 +23,22 @@ probing      Section 2.2: Hadamard / Fourier matrices (Eqs. HadamardElements,
              (Eq. row-col-permutation) and bias removal (Section 4).
 operators    Section 1.1.1 / Section 5: shifted periodic Laplacian and the
              Wilson-Dirac matrix with explicit 4x4 gamma matrices and full
-             3x3 link products (no spin projection, no reconstruction).
+             3x3 link products (no spin projection, no reconstruction), the
+             clover term, the even-odd Schur complement.
 solvers      Textbook CG and BiCGStab in FP64 and dense solves (Section 1.1.2:
-             the quadrature z^H A^-1 z is computed through a linear solve).
+             the quadrature z^H A^-1 z is computed through a linear solve),
+             Gauss and Gauss-Radau bounds from the CG coefficients.
 estimator    Section 1 (Monte Carlo form of the estimator) and Section 2.2
-             (nesting): quadratures q_m, prefix estimates T_s, and the
-             derivative of T_s with respect to a per-site mass.
+             (nesting): quadratures q_m, prefix estimates T_s, the
+             derivative of T_s with respect to a per-site mass; the
+             statistics of Sections 5.2-5.3 (exact z_0-variance, speed-up
+             ratio R_s, jackknife); deflation (the conclusions' next step):
+             the lowest eigenpairs of the Laplacian and of gamma_5 D, the
+             smallest singular triplets of D (dense decompositions), and the
+             deflated quadratures written out as projected dense solves.
+sparse_probing  Section 2.1, Algorithm 1 on a general sparse matrix: greedy
+             colouring, Colors2Perm and the block-graph recursion, perm and
+             colorOffsets, and the probing vectors of the colour paths.
 
 Parity pins: every function here is pinned by ``tests/test_oracle_*.py``
 against worked examples printed in the paper (``tests/golden``), closed
